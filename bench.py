@@ -1,0 +1,331 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused HMLFC random-access decode + two-plane render.
+
+Workload (paper-scale plain method): a 17x17 grid of 512x512 RGB8 views of a
+seeded 6-plane synthetic scene (0-12 px disparity per camera step, 1/f
+textures), encoded with 4 SRV levels, 16x16 blocks, quarter-pel
+phase-shifted MC (+-4 px), quantiser step 4 and block thresholds
+(400, 800).  One step renders a 64-pose circular camera path of 512x512
+views with one call of hmlfc_render_views.  Metric: 512x512 views/s (and
+Mrays/s), with the render kernel's fraction of its gather roofline.
+
+One process per GPU.  The render shards by view with no exchange step, so
+N GPUs run N replicas of the step (weak scaling); under torchrun rank 0
+prints one JSON line with the whole-job rate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthlf  # noqa: E402
+
+WORKLOAD = dict(config="paper", qstep=4, t_ref=400, t_pred=800, poses=64, view=512)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="hmlfc", choices=["hmlfc", "reference"])
+    ap.add_argument("--config", default=WORKLOAD["config"], choices=list(synthlf.CONFIGS))
+    ap.add_argument("--qstep", type=int, default=WORKLOAD["qstep"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU baseline sample")
+    ap.add_argument("--traffic-json", default=os.path.join(ROOT, "profiles", "render_traffic.json"))
+    ap.add_argument("--path", type=int, default=0, help="render path: 0 staged, 1 direct")
+    return ap.parse_args()
+
+
+def make_workload(args):
+    c = synthlf.CONFIGS[args.config]
+    t0 = time.time()
+    lf = synthlf.make_lf(c.seed, c.nu, c.nv, c.width, c.height, c.n_planes, c.disp_max, c.texture)
+    t_gen = time.time() - t0
+    geo = synthlf.lf_geometry(c.nu, c.nv, c.width, c.height)
+    size = WORKLOAD["view"] if args.config == "paper" else c.width
+    views = synthlf.circle_path(geo, WORKLOAD["poses"], size, size)
+    arr = synthlf.views_to_array(views)
+    tr, tp = (WORKLOAD["t_ref"], WORKLOAD["t_pred"]) if args.config == "paper" else (0, 0)
+    return c, lf, arr, size, tr, tp, t_gen
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.proc = None
+        self.path = None
+        if shutil.which("nvidia-smi") is None:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                      "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for k, n in enumerate(names):
+                    if parts[5 + k].lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(data: bytes, arr, size: int, seconds: float):
+    """The oracle (plain C, FP64, random-access decode of every sample) on the
+    host cores, timed on a bounded sample of rays of the same 64 views."""
+    import oracle
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    st = oracle.Stream(data)
+    rng = np.random.default_rng(0)
+
+    def sample(n):
+        v = rng.integers(0, len(arr), n)
+        return np.stack([v, rng.integers(0, size, n), rng.integers(0, size, n)], -1).astype(np.int32)
+
+    pix = sample(2000)
+    t0 = time.perf_counter()
+    st.render_pixels(arr, pix)
+    dt = time.perf_counter() - t0
+    n = int(min(max(2000, 2000 * seconds / max(dt, 1e-6)), 50_000_000))
+    pix = sample(n)
+    t0 = time.perf_counter()
+    st.render_pixels(arr, pix)
+    dt = time.perf_counter() - t0
+    views_per_s = n / dt / (size * size)
+    return {"value": views_per_s, "unit": f"{size}x{size} views/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} random rays of the 64 views (FP64 render, random-access decode of 16 samples each), "
+                      f"{dt:.1f} s on {cores} threads"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the oracle, as it stands, on the host cores."""
+    c, lf, arr, size, tr, tp, _ = make_workload(args)
+    if rank != 0:
+        return
+    import oracle
+    data = oracle.encode(lf, c.levels, c.block, c.search, args.qstep, t_ref=tr, t_pred=tp).stream
+    oracle.set_threads(os.cpu_count() or 1)
+    st = oracle.Stream(data)
+    rng = np.random.default_rng(1)
+    per_step = max(1, int(size * size * len(arr) / 4096))     # 1/4096 of a step's rays
+    per_step = min(per_step, 200_000)
+    times = []
+    for k in range(args.warmup + args.steps):
+        v = rng.integers(0, len(arr), per_step)
+        pix = np.stack([v, rng.integers(0, size, per_step), rng.integers(0, size, per_step)], -1).astype(np.int32)
+        t0 = time.perf_counter()
+        st.render_pixels(arr, pix)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    rate = per_step * len(times) / sum(times) / (size * size)
+    unit = f"{size}x{size} views/s"
+    print(json.dumps({
+        "impl": "reference", "metric": f"{size}x{size} novel views/s (fused random-access decode + render)",
+        "value": rate, "unit": unit, "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * len(arr) / rate, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32 decode, f64 blend", "data": "synthetic",
+        "config": {"workload": f"{c.name}: {c.nu}x{c.nv}x{c.width}x{c.height} L={c.levels} B={c.block} "
+                               f"Ws={c.search} q={args.qstep}, {len(arr)}-pose path of {size}x{size} views"},
+        "cpu_baseline": {"value": rate, "unit": unit, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"{per_step} random rays per step of the {len(arr)} views"},
+        "e2e": {"value": rate, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import torch.distributed as dist
+    import paper_1902_09396_gb300 as H
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    H.lib()
+    c, lf, arr, size, tr, tp, t_gen = make_workload(args)
+    t0 = time.time()
+    data = H.encode(lf, c.levels, c.block, c.search, args.qstep, t_ref=tr, t_pred=tp)
+    t_enc = time.time() - t0
+    stream = torch.cuda.current_stream()
+    t0 = time.time()
+    st = H.Stream(data, device=local)
+    t_load = time.time() - t0
+    H.set_render_path(args.path)
+    n_out = H.out_size(arr)
+    out = torch.empty(n_out, dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > 129 MB L2
+
+    # quality of the stream (PSNR of all decoded samples vs the input, bpp)
+    psnr = None
+    if rank == 0:
+        ii, jj = np.meshgrid(np.arange(c.nu), np.arange(c.nv), indexing="ij")
+        se, cnt = 0.0, 0
+        for i, j in zip(ii.ravel(), jj.ravel()):
+            xx, yy = np.meshgrid(np.arange(c.width), np.arange(c.height))
+            co = np.stack([np.full(xx.size, i), np.full(xx.size, j), xx.ravel(), yy.ravel()], -1).astype(np.int32)
+            dec = st.decode_pixels(torch.from_numpy(co).cuda()).cpu().numpy().reshape(c.height, c.width, 3)
+            d = dec.astype(np.float64) - lf[i, j]
+            se += float(np.sum(d * d))
+            cnt += d.size
+        psnr = 10 * math.log10(255.0 ** 2 / (se / cnt)) if se > 0 else float("inf")
+    bpp = len(data) * 8.0 / (c.nu * c.nv * c.width * c.height)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        H.render_views([st], arr, out)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        H.render_views([st], arr, out)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+
+    # end to end through the public API: views from host memory, the rendered
+    # views copied back to pinned host memory inside the timed region
+    host_out = torch.empty(n_out, dtype=torch.float32, pin_memory=True)
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t_e0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        H.render_views([st], arr, out)
+        host_out.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t_e0
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    views_per_step = len(arr)
+    value = views_per_step * args.steps * world / (total_ms / 1000.0)
+    touched = H.touched_bytes([st], arr)
+    bytes_per_step = float(np.sum(touched))
+    avg_step_s = total_ms / 1000.0 / args.steps
+    peak, peak_kind = peaks()
+    achieved = bytes_per_step / avg_step_s / 1e9
+    traffic = None
+    try:
+        with open(args.traffic_json) as f:
+            tj = json.load(f)
+        if tj.get("kernel_version") == H.KERNEL_VERSION:
+            traffic = float(tj["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    res = {
+        "metric": f"{size}x{size} novel views/s (fused random-access decode + render)",
+        "value": value,
+        "unit": f"{size}x{size} views/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32 decode, fp32 blend",
+        "data": "synthetic",
+        "config": {
+            "workload": f"{c.name}: {c.nu}x{c.nv} grid of {c.width}x{c.height} RGB8 views, {c.n_planes} planes "
+                        f"0-{c.disp_max:g} px disparity, L={c.levels} B={c.block} quarter-pel MC Ws={c.search} "
+                        f"q={args.qstep} T=({tr},{tp}); step = {views_per_step}-pose circular path of "
+                        f"{size}x{size} views",
+            "views_per_step": views_per_step,
+            "l2": "flushed (256 MB write) before every timed step",
+            "render_path": "staged" if args.path == 0 else "direct",
+        },
+        "mrays_per_s": value * size * size / 1e6,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "note": f"peak {peak_kind}; achieved = compulsory bytes of the step "
+                             f"({bytes_per_step / 1e6:.1f} MB: FP32 output + distinct compressed blocks, "
+                             f"tiles and root pixels reached) / render time"},
+        "e2e": {"value": views_per_step * e2e_steps / e2e_s, "unit": f"{size}x{size} views/s",
+                "h2d_bytes_per_step": int(views_per_step * 96), "d2h_bytes_per_step": int(n_out * 4)},
+        "gpu_launches": args.steps,
+        "stream": {"bytes": len(data), "bpp": bpp, "psnr_db": psnr, "encode_s": t_enc, "load_s": t_load,
+                   "lf_gen_s": t_gen},
+    }
+    if clocks:
+        res["clocks"] = clocks
+    if not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(data, arr, size, args.cpu_seconds)
+    print(json.dumps(res), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

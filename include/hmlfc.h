@@ -1,0 +1,254 @@
+/*
+ * hmlfc.h -- C ABI of the GB300 HMLFC library: random-access decoding of a
+ * hierarchical motion-compensated light-field stream fused with two-plane
+ * novel-view rendering (Pratapa & Manocha, "HMLFC: Hierarchical
+ * Motion-Compensated Light Field Compression for Interactive Rendering",
+ * arXiv 1902.09396).
+ *
+ * Conventions
+ * -----------
+ * - Every entry point returns HMLFC_OK (0) or a negative HMLFC_E_* code;
+ *   hmlfc_last_error() gives a thread-local message for the last failure.
+ * - Arguments named d_* are device pointers owned by the caller; h_* are host
+ *   pointers owned by the caller.  The library never frees caller memory.
+ * - Calls that take a `cuda_stream` (a cudaStream_t passed as void*; NULL =
+ *   the legacy default stream) enqueue their work on it and return without
+ *   synchronising, except hmlfc_load_stream, hmlfc_encode,
+ *   hmlfc_check_status and hmlfc_touched_bytes, which are synchronous.
+ * - A stream object may be used from several CUDA streams at once for
+ *   reading (render, decode, backward); it must not be freed while work
+ *   that uses it is in flight.
+ *
+ * Stream format (little-endian; all offsets in bytes; sections 16-byte
+ * aligned).  The paper fixes the tree, the BISE coding and the breadth-first
+ * order (Sec. 4.3-4.7) but not the bit layout, the block index or the
+ * cluster shape; the readings fixed here are:
+ *
+ *   header: 32 x u32
+ *     [0] magic 0x464C4D48 ("HMLF")  [1] version 1
+ *     [2] nu  [3] nv   camera grid (u, v)      [4] W  [5] H   view size
+ *     [6] L   SRV levels (tree height; roots are the level-L RKVs)
+ *     [7] B   block size  [8] Ws search window (px)  [9] q quantiser step
+ *     [10] T_ref [11] T_pred block thresholds  [12] flags (bit 0: MC)
+ *     [13] mv_mode [14] mv_b  BISE alphabet of the motion-vector symbols
+ *     [15] n_nc node-channels  [16] groups per node-channel
+ *     [17] n_sig significant blocks  [18] record words  [19] MV symbols
+ *     [20] MV words  [21..25] offsets of roots, groups, block offsets,
+ *     records, MV words  [26] total bytes  [27..31] zero
+ *   tree: level l has ceil(nu/2^l) x ceil(nv/2^l) nodes; node (a, b) of
+ *     level l+1 is the RKV of the 2x2 cluster {2a, 2a+1} x {2b, 2b+1} of
+ *     level l (Sec. 4.3).  The cluster member with both coordinates even is
+ *     its reference SRV, the others are predictive SRVs (Sec. 4.4).  Camera
+ *     (i, j) lies under node (i >> l, j >> l) at level l.
+ *   node-channels: breadth-first from the top (Sec. 4.7): l = L-1 .. 0,
+ *     nodes row-major (a major), channels Y, Co, Cg (YCoCg-R, Sec. 4.5).
+ *   roots: int16 [roots][3][H][W], roots row-major.
+ *   blocks: B x B raster blocks of each node-channel, k = by * nbx + bx;
+ *     edge blocks are partial (bw x bh valid pixels, in-block index
+ *     (y - y0) * bw + (x - x0)).
+ *   groups: per node-channel and run of 32 blocks a {bitmap, record base
+ *     word, block-offset base, 0} quadruple; bit r marks block 32g+r
+ *     significant (Sec. 4.5 thresholds); its record starts at record word
+ *     base + offsets[offset base + popcount(bitmap & ((1 << r) - 1))]
+ *     (u16 offsets).  Insignificant blocks are zero.
+ *   records: u32 header (bits 0-15 int16 min level m, 16-20 b, 21-22
+ *     mode) followed by the BISE payload of the block's levels minus m
+ *     (Sec. 4.6): mode 0 = b bits per value; mode 1 = groups of 5 values
+ *     with an 8-bit trit byte t0+3t1+9t2+27t3+81t4 then 5 x b low bits;
+ *     mode 2 = groups of 3 values with a 7-bit field q0+5q1+25q2 then 3 x b
+ *     low bits; value = hi * 2^b + low; bit k is bit k%32 of word k/32.
+ *     The dequantised coefficient is q * (m + value).
+ *   motion vectors: one BISE sequence (mode, b of the header) with one
+ *     symbol per block of every predictive node-channel, in breadth-first
+ *     order: ((mvx + 4Ws)(8Ws + 1) + (mvy + 4Ws)) * 2 + (sign < 0), mv in
+ *     quarter pixels within [-4Ws, 4Ws].
+ *
+ * Decoding one sample (Sec. 4.8.1): value_c = root_c(x, y) + sum over l of
+ * SRV_l,c(x, y); a reference SRV is its dequantised coefficient R^; a
+ * predictive SRV is sign * P + r^ where r^ is its dequantised residual and
+ * P = (sum of 4 bilinear taps of its reference's R^ at (4x + mvx, 4y + mvy)
+ * quarter-pel, weights summing to 16, + 8) >> 4 with taps clamped to the
+ * image (Sec. 4.4; quarter-pel after the sub-pel extension of Sec. 6).  The
+ * inverse YCoCg-R then gives RGB, each clamped to [0, 255].
+ */
+#ifndef HMLFC_H
+#define HMLFC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HMLFC_OK 0
+#define HMLFC_E_INVALID_ARG -1
+#define HMLFC_E_CORRUPT -2
+#define HMLFC_E_OOM -3
+#define HMLFC_E_CUDA -4
+#define HMLFC_E_TIMEOUT -5
+#define HMLFC_E_UNSUPPORTED -6
+
+/* Largest number of views one render call takes, and of distinct streams. */
+#define HMLFC_MAX_VIEWS 1048576
+#define HMLFC_MAX_STREAMS 16
+
+typedef struct hmlfc_stream hmlfc_stream;
+
+/*
+ * One novel view (96 bytes).  Output pixel (px, py) is the ray whose
+ * two-plane coordinates (Sec. 2.1) are (u, v) = H_uv (px + .5, py + .5, 1)
+ * and (s, t) = H_st (px + .5, py + .5, 1) (projective, row-major 3x3).
+ * (u, v) is in camera-grid units (camera (i, j) at (u, v) = (i, j)); (s, t)
+ * is in pixels (sample x at s = x).  The 16 neighbouring samples
+ * (floor/ceil of each coordinate, clamped to the grid and image) are blended
+ * quadrilinearly.  The view's FP32 RGB output, in [0, 1] (= RGB8 / 255), is
+ * written as [height][width][3] starting at element out_offset of d_out.
+ * `lf` indexes the streams array of the call.
+ */
+typedef struct {
+    int32_t lf;
+    int32_t width;
+    int32_t height;
+    float H_uv[9];
+    float H_st[9];
+    int32_t reserved;
+    int64_t out_offset;
+} hmlfc_view;
+
+typedef struct {
+    int32_t nu, nv, width, height, levels, block, search, qstep, mc;
+    int32_t n_roots;
+    int64_t n_nc, n_blocks, n_sig, n_ref_tiles;
+    int64_t stream_bytes;   /* size of the compressed stream */
+    int64_t device_bytes;   /* device memory held by the stream object */
+} hmlfc_stream_info_t;
+
+/*
+ * Parse and validate a compressed stream (format above), copy it to device
+ * `device` and decode, once, its roots and every reference SRV into resident
+ * block-sparse tiles (Sec. 4.8.2: all reference SRVs are decoded at the start
+ * of decompression and kept in a sparse form).  The bytes are copied; the
+ * caller may free them on return.  Synchronous.  Errors: HMLFC_E_CORRUPT (the
+ * header, an index entry or a record points outside the stream),
+ * HMLFC_E_INVALID_ARG, HMLFC_E_OOM, HMLFC_E_CUDA.
+ */
+int hmlfc_load_stream(const void *h_bytes, size_t nbytes, int device, void *cuda_stream, hmlfc_stream **out);
+
+/* Release the stream object and its device memory (NULL is ignored). */
+void hmlfc_free_stream(hmlfc_stream *s);
+
+int hmlfc_stream_info(const hmlfc_stream *s, hmlfc_stream_info_t *out);
+
+/*
+ * Random-access decoding (Sec. 4.8.1, Sec. 4.8.4) of n samples.
+ * d_coords: int32 [n][4] = (i, j, x, y): camera (i, j), pixel (x, y).
+ * d_rgb: uint8 [n][3] output.  A coordinate outside the light field decodes
+ * to (0, 0, 0) and sets the stream's status word, which hmlfc_check_status
+ * reports as HMLFC_E_INVALID_ARG.  n = 0 is a no-op.
+ */
+int hmlfc_decode_pixels(const hmlfc_stream *s, const int32_t *d_coords, int64_t n, uint8_t *d_rgb,
+                        void *cuda_stream);
+
+/*
+ * Synchronise `cuda_stream` and report (then clear) the stream object's
+ * status word: HMLFC_OK, or HMLFC_E_INVALID_ARG if a decode on it met an
+ * out-of-range coordinate since the last check.
+ */
+int hmlfc_check_status(const hmlfc_stream *s, void *cuda_stream);
+
+/*
+ * Render n_views novel views (Sec. 5: ray-traced views decoded on the fly):
+ * per output ray, (u,v,s,t) from the view's homographies, the 16 neighbouring
+ * light-field samples decoded by random access from streams[view.lf], and
+ * their quadrilinear blend.  h_views is host memory.  Views of different
+ * sizes and streams may be mixed.  Coordinates outside the grid or image
+ * clamp to the edge.
+ */
+int hmlfc_render_views(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views, int n_views,
+                       float *d_out, void *cuda_stream);
+
+/*
+ * Differentiable relaxation (for gradient-based refinement of the residuals):
+ * the same render with real-valued coefficients -- exact bilinear weights
+ * instead of the >> 4 rounding, YCoCg-R inverse with /2 instead of >> 1, no
+ * clamp.  It is linear in the coefficients for the stream's fixed motion
+ * vectors and signs.
+ * d_coeff[k]: float [n_nc][H][W] per stream (breadth-first node-channel
+ * order; references hold R^, predictive nodes r^); d_root[k]: float
+ * [n_roots][3][H][W].
+ */
+int hmlfc_render_views_relaxed(const hmlfc_stream *const *streams, int n_streams, const float *const *d_coeff,
+                               const float *const *d_root, const hmlfc_view *h_views, int n_views, float *d_out,
+                               void *cuda_stream);
+
+/*
+ * Adjoint of hmlfc_render_views_relaxed: ACCUMULATES d(<out, grad_out>) into
+ * d_grad_coeff[k] (float [n_nc][H][W]) and d_grad_root[k] (float
+ * [n_roots][3][H][W]) for every stream k.  Decoded tiles are recomputed,
+ * nothing is stored between the passes.  Accumulation uses FP32 atomics, so
+ * the summation order (and the last bits) may vary between runs.
+ */
+int hmlfc_render_backward(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views, int n_views,
+                          const float *d_grad_out, float *const *d_grad_coeff, float *const *d_grad_root,
+                          void *cuda_stream);
+
+/*
+ * Write the stream's dequantised coefficients (float [n_nc][H][W]) and roots
+ * (float [n_roots][3][H][W]) to device memory: the starting point of the
+ * relaxation.
+ */
+int hmlfc_dequant(const hmlfc_stream *s, float *d_coeff, float *d_root, void *cuda_stream);
+
+/* Encoder parameters (Sec. 4.5: tree height, block size, two block
+ * thresholds, search window) plus the quantiser step and the MC mode
+ * (0 = none, 1 = phase-shifted with quarter-pel refinement, 2 = zero
+ * motion, 3 = phase-shifted integer-pel as in the paper). */
+typedef struct {
+    int32_t levels, block, search, qstep, t_ref, t_pred, mc, threads;
+} hmlfc_encode_params;
+
+/*
+ * Encode h_lf (uint8 [nu][nv][H][W][3], RGB) into a stream of the format
+ * above (Sec. 4.3-4.7).  *h_out is allocated by the library; release it with
+ * hmlfc_free_host.  Synchronous, host threads only.
+ */
+int hmlfc_encode(const uint8_t *h_lf, int nu, int nv, int width, int height, const hmlfc_encode_params *p,
+                 void **h_out, size_t *nbytes);
+
+/*
+ * Re-encode a stream with new coefficients (float [n_nc][H][W], host) and
+ * roots (float [n_roots][3][H][W], host) at the same quantiser step, motion
+ * vectors and signs: coefficients are rounded to the nearest multiple of q,
+ * roots to integers, and blocks whose levels are all zero become
+ * insignificant.  Synchronous.
+ */
+int hmlfc_requantize(const hmlfc_stream *s, const float *h_coeff, const float *h_root, void **h_out, size_t *nbytes);
+
+void hmlfc_free_host(void *p);
+
+/*
+ * Bytes that rendering the views must move at least once: the FP32 output
+ * plus every distinct root pixel (6 B), predictive block (group entry,
+ * offset, record, motion-vector bits) and significant reference tile
+ * (B * B * 2 + 4 B) the views' samples reach.  One value per view into
+ * h_bytes.  Synchronous, host threads only (a measurement aid).
+ */
+int hmlfc_touched_bytes(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views, int n_views,
+                        double *h_bytes);
+
+/*
+ * Diagnostic switch of the render kernels (process-wide): 0 (default) stages
+ * each tile's footprint in shared memory where it fits and decodes per ray
+ * otherwise; 1 decodes every ray's samples directly.  Both give identical
+ * results; the switch exists to test and time the two paths.
+ */
+int hmlfc_set_render_path(int path);
+
+const char *hmlfc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HMLFC_H */

@@ -1,0 +1,253 @@
+"""GB300-native HMLFC: random-access decoding of hierarchical
+motion-compensated light-field streams fused with two-plane rendering.
+
+This module is a thin ctypes binding of ``libhmlfc.so`` (C ABI declared in
+``include/hmlfc.h``): it marshals arguments -- device buffers are torch
+tensors, the CUDA stream is torch's current stream -- and every step of the
+decode and render runs in the library's CUDA kernels.  There is no CPU
+fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from pathlib import Path
+
+import numpy as np
+
+from .build import LIB, build  # noqa: F401
+
+# Identifies the render kernel's code; profile figures recorded for another
+# version are not reused.
+KERNEL_VERSION = "render-staged-v1"
+
+OK, E_INVALID_ARG, E_CORRUPT, E_OOM, E_CUDA, E_TIMEOUT, E_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+MC_OFF, MC_QPEL, MC_ZERO, MC_INTEGER = 0, 1, 2, 3
+
+
+class HmlfcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"hmlfc error {code}: {msg}")
+        self.code = code
+
+
+class View(C.Structure):
+    _fields_ = [("lf", C.c_int32), ("width", C.c_int32), ("height", C.c_int32),
+                ("H_uv", C.c_float * 9), ("H_st", C.c_float * 9), ("reserved", C.c_int32),
+                ("out_offset", C.c_int64)]
+
+
+assert C.sizeof(View) == 96
+
+
+class StreamInfo(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in ("nu", "nv", "width", "height", "levels", "block", "search",
+                                          "qstep", "mc", "n_roots")] + \
+               [(n, C.c_int64) for n in ("n_nc", "n_blocks", "n_sig", "n_ref_tiles", "stream_bytes",
+                                         "device_bytes")]
+
+
+class EncodeParams(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in ("levels", "block", "search", "qstep", "t_ref", "t_pred", "mc",
+                                          "threads")]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libhmlfc.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = Path(os.environ.get("HMLFC_LIB", str(LIB)))
+    if not path.exists() or path == LIB:
+        build()
+    L = C.CDLL(str(path))
+    P, I, I64, SZ = C.c_void_p, C.c_int, C.c_int64, C.c_size_t
+    L.hmlfc_last_error.restype = C.c_char_p
+    L.hmlfc_load_stream.argtypes = [P, SZ, I, P, C.POINTER(P)]
+    L.hmlfc_free_stream.argtypes = [P]
+    L.hmlfc_free_stream.restype = None
+    L.hmlfc_stream_info.argtypes = [P, C.POINTER(StreamInfo)]
+    L.hmlfc_decode_pixels.argtypes = [P, P, I64, P, P]
+    L.hmlfc_check_status.argtypes = [P, P]
+    L.hmlfc_render_views.argtypes = [P, I, P, I, P, P]
+    L.hmlfc_render_views_relaxed.argtypes = [P, I, P, P, P, I, P, P]
+    L.hmlfc_render_backward.argtypes = [P, I, P, I, P, P, P, P]
+    L.hmlfc_dequant.argtypes = [P, P, P, P]
+    L.hmlfc_encode.argtypes = [P, I, I, I, I, C.POINTER(EncodeParams), C.POINTER(P), C.POINTER(SZ)]
+    L.hmlfc_requantize.argtypes = [P, P, P, C.POINTER(P), C.POINTER(SZ)]
+    L.hmlfc_free_host.argtypes = [P]
+    L.hmlfc_free_host.restype = None
+    L.hmlfc_touched_bytes.argtypes = [P, I, P, I, P]
+    L.hmlfc_set_render_path.argtypes = [I]
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise HmlfcError(rc, lib().hmlfc_last_error().decode(errors="replace"))
+
+
+def _stream_handle(cuda_stream):
+    """Raw cudaStream_t of a torch stream (None -> torch's current stream)."""
+    import torch
+    if cuda_stream is None:
+        cuda_stream = torch.cuda.current_stream()
+    return C.c_void_p(int(cuda_stream.cuda_stream))
+
+
+def _ptr(t) -> C.c_void_p:
+    return C.c_void_p(int(t.data_ptr()))
+
+
+def _views_array(views) -> "C.Array":
+    """Accept a numpy record array of 96-byte views (see synthlf.VIEW_DTYPE)
+    or a sequence of View structures."""
+    if isinstance(views, np.ndarray):
+        arr = np.ascontiguousarray(views)
+        assert arr.dtype.itemsize == 96
+        buf = (View * len(arr)).from_buffer_copy(arr.tobytes())
+        return buf
+    buf = (View * len(views))()
+    for k, v in enumerate(views):
+        buf[k] = v
+    return buf
+
+
+class Stream:
+    """A compressed light field resident on the GPU (Sec. 4.8.2)."""
+
+    def __init__(self, data: bytes, device: int = 0, cuda_stream=None):
+        h = C.c_void_p()
+        raw = bytes(data)
+        _check(lib().hmlfc_load_stream(raw, len(raw), int(device), _stream_handle(cuda_stream), C.byref(h)))
+        self._h = h
+        self.device = device
+        inf = StreamInfo()
+        _check(lib().hmlfc_stream_info(self._h, C.byref(inf)))
+        self.info = {f: getattr(inf, f) for f, _ in StreamInfo._fields_}
+
+    @property
+    def handle(self) -> C.c_void_p:
+        if self._h is None:
+            raise HmlfcError(E_INVALID_ARG, "stream already freed")
+        return self._h
+
+    def free(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.hmlfc_free_stream(self._h)
+        self._h = None
+
+    __del__ = free
+
+    def decode_pixels(self, coords, out=None, cuda_stream=None):
+        """coords: int32 CUDA tensor [n, 4] = (i, j, x, y) -> uint8 [n, 3]."""
+        import torch
+        assert coords.dtype == torch.int32 and coords.is_cuda and coords.is_contiguous()
+        n = coords.shape[0]
+        if out is None:
+            out = torch.empty((n, 3), dtype=torch.uint8, device=coords.device)
+        _check(lib().hmlfc_decode_pixels(self.handle, _ptr(coords), n, _ptr(out), _stream_handle(cuda_stream)))
+        return out
+
+    def check_status(self, cuda_stream=None):
+        _check(lib().hmlfc_check_status(self.handle, _stream_handle(cuda_stream)))
+
+    def dequant(self, cuda_stream=None):
+        """Dequantised coefficients [n_nc, H, W] and roots [n_roots, 3, H, W] (float32 CUDA)."""
+        import torch
+        i = self.info
+        dev = torch.device("cuda", self.device)
+        co = torch.empty((i["n_nc"], i["height"], i["width"]), dtype=torch.float32, device=dev)
+        ro = torch.empty((i["n_roots"], 3, i["height"], i["width"]), dtype=torch.float32, device=dev)
+        _check(lib().hmlfc_dequant(self.handle, _ptr(co), _ptr(ro), _stream_handle(cuda_stream)))
+        return co, ro
+
+
+def _streams_array(streams):
+    arr = (C.c_void_p * len(streams))()
+    for k, s in enumerate(streams):
+        arr[k] = s.handle
+    return arr
+
+
+def out_size(views) -> int:
+    """Elements of the output buffer the views need (max of offset + size)."""
+    if isinstance(views, np.ndarray):
+        if len(views) == 0:
+            return 0
+        return int(np.max(views["out_offset"] + views["width"].astype(np.int64) * views["height"] * 3))
+    return max((v.out_offset + v.width * v.height * 3 for v in views), default=0)
+
+
+def render_views(streams, views, out=None, cuda_stream=None):
+    """Fused decode + render of novel views (float32 [sum H*W*3] CUDA tensor)."""
+    import torch
+    va = _views_array(views)
+    if out is None:
+        out = torch.empty(out_size(views), dtype=torch.float32, device=torch.device("cuda", streams[0].device))
+    _check(lib().hmlfc_render_views(_streams_array(streams), len(streams), va, len(va), _ptr(out),
+                                    _stream_handle(cuda_stream)))
+    return out
+
+
+def render_views_relaxed(streams, coeffs, roots, views, out=None, cuda_stream=None):
+    import torch
+    va = _views_array(views)
+    if out is None:
+        out = torch.empty(out_size(views), dtype=torch.float32, device=torch.device("cuda", streams[0].device))
+    cp = (C.c_void_p * len(streams))(*[int(t.data_ptr()) for t in coeffs])
+    rp = (C.c_void_p * len(streams))(*[int(t.data_ptr()) for t in roots])
+    _check(lib().hmlfc_render_views_relaxed(_streams_array(streams), len(streams), cp, rp, va, len(va), _ptr(out),
+                                            _stream_handle(cuda_stream)))
+    return out
+
+
+def render_backward(streams, views, grad_out, grad_coeffs, grad_roots, cuda_stream=None):
+    """Accumulates the adjoint of the relaxed render into the given buffers."""
+    va = _views_array(views)
+    gc = (C.c_void_p * len(streams))(*[int(t.data_ptr()) for t in grad_coeffs])
+    gr = (C.c_void_p * len(streams))(*[int(t.data_ptr()) for t in grad_roots])
+    _check(lib().hmlfc_render_backward(_streams_array(streams), len(streams), va, len(va), _ptr(grad_out), gc, gr,
+                                       _stream_handle(cuda_stream)))
+
+
+def set_render_path(path: int):
+    _check(lib().hmlfc_set_render_path(int(path)))
+
+
+def encode(lf: np.ndarray, levels: int, block: int, search: int, qstep: int, t_ref: int = 0, t_pred: int = 0,
+           mc: int = MC_QPEL, threads: int = 0) -> bytes:
+    """Encode uint8 [nu][nv][H][W][3] into an HMLFC stream (host threads)."""
+    lf = np.ascontiguousarray(lf, np.uint8)
+    nu, nv, H, W, _ = lf.shape
+    prm = EncodeParams(levels, block, search, qstep, t_ref, t_pred, mc, threads)
+    out = C.c_void_p()
+    n = C.c_size_t()
+    _check(lib().hmlfc_encode(lf.ctypes.data_as(C.c_void_p), nu, nv, W, H, C.byref(prm), C.byref(out), C.byref(n)))
+    data = C.string_at(out, n.value)
+    lib().hmlfc_free_host(out)
+    return data
+
+
+def requantize(stream: Stream, coeff: np.ndarray, root: np.ndarray) -> bytes:
+    co = np.ascontiguousarray(coeff, np.float32)
+    ro = np.ascontiguousarray(root, np.float32)
+    out = C.c_void_p()
+    n = C.c_size_t()
+    _check(lib().hmlfc_requantize(stream.handle, co.ctypes.data_as(C.c_void_p), ro.ctypes.data_as(C.c_void_p),
+                                  C.byref(out), C.byref(n)))
+    data = C.string_at(out, n.value)
+    lib().hmlfc_free_host(out)
+    return data
+
+
+def touched_bytes(streams, views) -> np.ndarray:
+    va = _views_array(views)
+    out = np.zeros(len(va), np.float64)
+    _check(lib().hmlfc_touched_bytes(_streams_array(streams), len(streams), va, len(va),
+                                     out.ctypes.data_as(C.c_void_p)))
+    return out

@@ -1,0 +1,470 @@
+// Host side of the HMLFC library: stream parsing and validation, device
+// residency (Sec. 4.8.2), and the C ABI entry points that launch the kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "hmlfc_host.h"
+
+using namespace hmlfc;
+
+namespace {
+
+thread_local std::string g_err;
+int g_render_path = 0;  // 0 = staged where the footprint fits, 1 = direct only
+
+}  // namespace
+
+int hmlfc::fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+namespace {
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(HMLFC_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+void hmlfc::parallel_for(int64_t n, int threads, const std::function<void(int64_t)> &fn) {
+    if (n <= 0) return;
+    int hw = (int)std::thread::hardware_concurrency();
+    if (threads <= 0) threads = hw > 0 ? hw : 1;
+    threads = (int)std::min<int64_t>(threads, n);
+    if (threads <= 1) {
+        for (int64_t i = 0; i < n; i++) fn(i);
+        return;
+    }
+    std::atomic<int64_t> next{0};
+    std::vector<std::thread> pool;
+    for (int t = 0; t < threads; t++)
+        pool.emplace_back([&] {
+            for (int64_t i = next.fetch_add(1); i < n; i = next.fetch_add(1)) fn(i);
+        });
+    for (auto &th : pool) th.join();
+}
+
+int hmlfc::parse_header(const uint8_t *p, size_t n, Geometry &g) {
+    if (!p || n < (size_t)kHeaderWords * 4) return fail(HMLFC_E_CORRUPT, "stream shorter than its header");
+    uint32_t h[kHeaderWords];
+    for (int i = 0; i < kHeaderWords; i++) h[i] = rd32(p + 4 * i);
+    if (h[0] != kMagic) return fail(HMLFC_E_CORRUPT, "bad magic");
+    if (h[1] != kVersion) return fail(HMLFC_E_UNSUPPORTED, "stream version %u", h[1]);
+    if (h[2] < 1 || h[2] > 65536 || h[3] < 1 || h[3] > 65536 || h[4] < 1 || h[4] > 65536 || h[5] < 1 ||
+        h[5] > 65536)
+        return fail(HMLFC_E_CORRUPT, "grid or image size out of range");
+    if (h[6] < 1 || h[6] > (uint32_t)kMaxLevels) return fail(HMLFC_E_UNSUPPORTED, "tree height %u", h[6]);
+    if (h[7] < 1 || h[7] > (uint32_t)kMaxBlock) return fail(HMLFC_E_UNSUPPORTED, "block size %u", h[7]);
+    if (h[8] > 64) return fail(HMLFC_E_UNSUPPORTED, "search window %u", h[8]);
+    if (h[9] < 1 || h[9] > (uint32_t)kCoefLimit) return fail(HMLFC_E_UNSUPPORTED, "quantiser step %u", h[9]);
+    if (h[12] > 1) return fail(HMLFC_E_CORRUPT, "flags");
+    g.nu = (int)h[2]; g.nv = (int)h[3]; g.W = (int)h[4]; g.H = (int)h[5]; g.L = (int)h[6]; g.B = (int)h[7];
+    g.Ws = (int)h[8]; g.q = (int)h[9]; g.t_ref = (int)h[10]; g.t_pred = (int)h[11]; g.mc = (int)h[12];
+    g.mv_mode = (int)h[13]; g.mv_b = (int)h[14];
+    g.nbx = (g.W + g.B - 1) / g.B;
+    g.nby = (g.H + g.B - 1) / g.B;
+    g.nblocks = g.nbx * g.nby;
+    g.ngroups = (g.nblocks + 31) / 32;
+    g.side = 8 * g.Ws + 1;
+    for (int l = 0; l <= g.L; l++) {
+        g.gu[l] = (g.nu + (1 << l) - 1) >> l;
+        g.gv[l] = (g.nv + (1 << l) - 1) >> l;
+    }
+    int64_t nc = 0, rr = 0, pr = 0;
+    for (int l = g.L - 1; l >= 0; l--) {
+        g.nc_base[l] = nc;
+        g.ref_base[l] = rr;
+        g.pred_base[l] = pr;
+        const int64_t nodes = (int64_t)g.gu[l] * g.gv[l];
+        const int64_t refs = (int64_t)((g.gu[l] + 1) / 2) * ((g.gv[l] + 1) / 2);
+        nc += 3 * nodes;
+        rr += 3 * refs;
+        pr += 3 * (nodes - refs);
+    }
+    g.n_nc = nc;
+    g.n_ref_nc = rr;
+    g.n_pred_nc = pr;
+    g.n_roots = (int64_t)g.gu[g.L] * g.gv[g.L];
+    if (nc * g.nblocks >= (int64_t)INT32_MAX || (int64_t)g.W * g.H * 3 * std::max<int64_t>(nc, g.n_roots) >= (1ll << 40))
+        return fail(HMLFC_E_UNSUPPORTED, "light field too large for one stream object");
+    if (h[15] != (uint32_t)nc || h[16] != (uint32_t)g.ngroups) return fail(HMLFC_E_CORRUPT, "node-channel count");
+    g.n_sig = h[17]; g.n_recw = h[18]; g.n_mv = h[19]; g.n_mvw = h[20];
+    g.off_roots = h[21]; g.off_groups = h[22]; g.off_offs = h[23]; g.off_recs = h[24]; g.off_mvs = h[25];
+    g.total = h[26];
+    if ((uint64_t)g.total != (uint64_t)n) return fail(HMLFC_E_CORRUPT, "stream length %zu, header says %u", n, g.total);
+    if (g.mc) {
+        int md, bb;
+        bise_choose(2ull * g.side * g.side, md, bb);
+        if (md != g.mv_mode || bb != g.mv_b) return fail(HMLFC_E_CORRUPT, "motion-vector alphabet");
+        if ((uint64_t)g.n_mv != (uint64_t)g.n_pred_nc * g.nblocks) return fail(HMLFC_E_CORRUPT, "motion-vector count");
+        if ((uint64_t)g.n_mvw != (bise_bits(md, bb, g.n_mv) + 31) / 32) return fail(HMLFC_E_CORRUPT, "motion-vector words");
+    } else if (g.n_mv != 0 || g.n_mvw != 0) {
+        return fail(HMLFC_E_CORRUPT, "motion vectors without motion compensation");
+    }
+    const uint64_t plane = (uint64_t)g.W * g.H;
+    struct Sec { uint64_t off, len; } secs[5] = {
+        {g.off_roots, (uint64_t)g.n_roots * 3 * plane * 2},
+        {g.off_groups, (uint64_t)nc * g.ngroups * 16},
+        {g.off_offs, (uint64_t)g.n_sig * 2},
+        {g.off_recs, (uint64_t)g.n_recw * 4},
+        {g.off_mvs, (uint64_t)g.n_mvw * 4}};
+    uint64_t prev_end = (uint64_t)kHeaderWords * 4;
+    for (auto &s : secs) {
+        if (s.off % 4 != 0 || s.off < prev_end || s.off + s.len > n) return fail(HMLFC_E_CORRUPT, "section layout");
+        prev_end = s.off + s.len;
+    }
+    return HMLFC_OK;
+}
+
+namespace {
+
+// Walk the block index; check every significant block's record against the
+// stream bounds and the coefficient limit; build the reference tile table.
+int validate_index(const uint8_t *p, const Geometry &g, std::vector<uint32_t> &ref_tab, std::vector<uint32_t> &tile_src) {
+    const uint8_t *groups = p + g.off_groups;
+    const uint8_t *offs = p + g.off_offs;
+    const uint8_t *recs = p + g.off_recs;
+    ref_tab.assign((size_t)g.n_ref_nc * g.nblocks, 0u);
+    tile_src.clear();
+    uint64_t sig = 0;
+    int64_t nc = 0, rr = 0;
+    for (int l = g.L - 1; l >= 0; l--)
+        for (int a = 0; a < g.gu[l]; a++)
+            for (int b = 0; b < g.gv[l]; b++) {
+                const bool ref = (a % 2 == 0) && (b % 2 == 0);
+                for (int c = 0; c < 3; c++, nc++) {
+                    for (int gi = 0; gi < g.ngroups; gi++) {
+                        const uint8_t *ge = groups + ((size_t)nc * g.ngroups + gi) * 16;
+                        const uint32_t bitmap = rd32(ge), rbase = rd32(ge + 4), obase = rd32(ge + 8);
+                        const int valid = std::min(32, g.nblocks - gi * 32);
+                        if (valid < 32 && (bitmap >> valid) != 0) return fail(HMLFC_E_CORRUPT, "bitmap past the last block");
+                        if ((uint64_t)obase != sig) return fail(HMLFC_E_CORRUPT, "block-offset base");
+                        for (int r = 0; r < valid; r++) {
+                            if (!((bitmap >> r) & 1u)) continue;
+                            if (sig >= g.n_sig) return fail(HMLFC_E_CORRUPT, "more significant blocks than offsets");
+                            uint16_t off;
+                            std::memcpy(&off, offs + 2 * sig, 2);
+                            sig++;
+                            const uint64_t rec = (uint64_t)rbase + off;
+                            if (rec >= g.n_recw) return fail(HMLFC_E_CORRUPT, "record outside the stream");
+                            const uint32_t hdr = rd32(recs + 4 * rec);
+                            const int mode = (int)((hdr >> 21) & 3u), bb = (int)((hdr >> 16) & 31u);
+                            if (mode == 3 || bb > 16 || (hdr >> 23) != 0) return fail(HMLFC_E_CORRUPT, "record header");
+                            const int k = gi * 32 + r;
+                            const int x0 = (k % g.nbx) * g.B, y0 = (k / g.nbx) * g.B;
+                            const int bw = std::min(g.B, g.W - x0), bh = std::min(g.B, g.H - y0);
+                            const uint64_t words = 1 + (bise_bits(mode, bb, (uint64_t)bw * bh) + 31) / 32;
+                            if (rec + words > g.n_recw) return fail(HMLFC_E_CORRUPT, "record overruns the stream");
+                            const int64_t m = (int16_t)(hdr & 0xFFFFu);
+                            const int64_t lo = (int64_t)g.q * m, hi = (int64_t)g.q * (m + (int64_t)bise_alphabet(mode, bb) - 1);
+                            if (lo < -kCoefLimit || hi > kCoefLimit)
+                                return fail(HMLFC_E_UNSUPPORTED, "coefficients beyond +-%d", kCoefLimit);
+                            if (ref) {
+                                tile_src.push_back((uint32_t)rec);
+                                tile_src.push_back((uint32_t)bw);
+                                tile_src.push_back((uint32_t)bh);
+                                tile_src.push_back(0u);
+                                ref_tab[(size_t)(rr + c) * g.nblocks + k] = (uint32_t)(tile_src.size() / 4);
+                            }
+                        }
+                    }
+                }
+                if (ref) rr += 3;
+            }
+    if (sig != g.n_sig) return fail(HMLFC_E_CORRUPT, "offset count");
+    return HMLFC_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int check_views(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *views, int n_views) {
+    if (n_streams < 1 || n_streams > HMLFC_MAX_STREAMS || !streams)
+        return fail(HMLFC_E_INVALID_ARG, "need 1..%d streams", HMLFC_MAX_STREAMS);
+    for (int k = 0; k < n_streams; k++) {
+        if (!streams[k]) return fail(HMLFC_E_INVALID_ARG, "stream %d is NULL", k);
+        if (streams[k]->device != streams[0]->device) return fail(HMLFC_E_INVALID_ARG, "streams on different devices");
+    }
+    if (n_views < 0 || n_views > HMLFC_MAX_VIEWS || (n_views > 0 && !views))
+        return fail(HMLFC_E_INVALID_ARG, "bad view count or view array");
+    for (int v = 0; v < n_views; v++) {
+        const hmlfc_view &V = views[v];
+        if (V.lf < 0 || V.lf >= n_streams) return fail(HMLFC_E_INVALID_ARG, "view %d: lf %d out of range", v, V.lf);
+        if (V.width < 0 || V.height < 0 || V.width > 65536 || V.height > 65536 || V.out_offset < 0)
+            return fail(HMLFC_E_INVALID_ARG, "view %d: bad size or offset", v);
+    }
+    return HMLFC_OK;
+}
+
+// Launch one kernel family over the views of each stream, in chunks that fit
+// the by-value view table.
+template <class F>
+int for_view_chunks(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *views, int n_views, F launch) {
+    std::vector<int> idx;
+    for (int lf = 0; lf < n_streams; lf++) {
+        idx.clear();
+        for (int v = 0; v < n_views; v++)
+            if (views[v].lf == lf && views[v].width > 0 && views[v].height > 0) idx.push_back(v);
+        for (size_t s = 0; s < idx.size(); s += kMaxViewsPerLaunch) {
+            LaunchViews lv;
+            std::memset(&lv, 0, sizeof lv);
+            lv.tile_w = 16;
+            lv.tile_h = 16;
+            const size_t e = std::min(idx.size(), s + kMaxViewsPerLaunch);
+            int64_t tiles = 0;
+            for (size_t t = s; t < e; t++) {
+                const hmlfc_view &V = views[idx[t]];
+                lv.tile_start[t - s] = (int)tiles;
+                lv.views[t - s] = V;
+                tiles += (int64_t)((V.width + 15) / 16) * ((V.height + 15) / 16);
+            }
+            lv.n_views = (int)(e - s);
+            lv.tile_start[lv.n_views] = (int)tiles;
+            if (tiles >= INT32_MAX) return fail(HMLFC_E_INVALID_ARG, "too many tiles in one launch");
+            const int rc = launch(streams[lf], lv, (int)tiles);
+            if (rc != HMLFC_OK) return rc;
+        }
+    }
+    return HMLFC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *hmlfc_last_error(void) { return g_err.c_str(); }
+
+int hmlfc_set_render_path(int path) {
+    if (path < 0 || path > 1) return fail(HMLFC_E_INVALID_ARG, "render path %d", path);
+    g_render_path = path;
+    return HMLFC_OK;
+}
+
+int hmlfc_load_stream(const void *h_bytes, size_t nbytes, int device, void *cuda_stream, hmlfc_stream **out) {
+    if (!out) return fail(HMLFC_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    const uint8_t *p = static_cast<const uint8_t *>(h_bytes);
+    Geometry g{};
+    int rc = parse_header(p, nbytes, g);
+    if (rc != HMLFC_OK) return rc;
+    std::vector<uint32_t> ref_tab, tile_src;
+    rc = validate_index(p, g, ref_tab, tile_src);
+    if (rc != HMLFC_OK) return rc;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return fail(HMLFC_E_INVALID_ARG, "device %d not available", device);
+    DeviceGuard guard(device);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+
+    auto *s = new (std::nothrow) hmlfc_stream();
+    if (!s) return fail(HMLFC_E_OOM, "host allocation");
+    s->device = device;
+    s->g = g;
+    s->bytes.assign(p, p + nbytes);
+    s->n_tiles = (int64_t)tile_src.size() / 4;
+    s->ref_tab = ref_tab;
+    const int B2 = g.B * g.B;
+    const uint64_t plane = (uint64_t)g.W * g.H;
+    // one device allocation, carved into 256-byte aligned sections
+    const size_t sz_roots = (size_t)g.n_roots * 3 * plane * 2;
+    const size_t sz_groups = (size_t)g.n_nc * g.ngroups * 16;
+    const size_t sz_offs = (size_t)g.n_sig * 2 + 4;
+    const size_t sz_recs = ((size_t)g.n_recw + 2) * 4;
+    const size_t sz_mvs = ((size_t)g.n_mvw + 2) * 4;
+    const size_t sz_tab = ref_tab.size() * 4 + 4;
+    const size_t sz_tiles = (size_t)(s->n_tiles + 1) * B2 * 2;
+    const size_t sz_src = tile_src.size() * 4 + 16;
+    size_t o_roots = 0, o_groups = up256(o_roots + sz_roots), o_offs = up256(o_groups + sz_groups),
+           o_recs = up256(o_offs + sz_offs), o_mvs = up256(o_recs + sz_recs), o_tab = up256(o_mvs + sz_mvs),
+           o_tiles = up256(o_tab + sz_tab), o_src = up256(o_tiles + sz_tiles), o_status = up256(o_src + sz_src),
+           total = up256(o_status + 256);
+    cudaError_t e = cudaMalloc(&s->d_mem, total);
+    if (e != cudaSuccess) {
+        delete s;
+        cudaGetLastError();
+        return fail(HMLFC_E_OOM, "device allocation of %zu bytes: %s", total, cudaGetErrorString(e));
+    }
+    s->d_bytes = total;
+    // staging image of the device layout, one copy
+    std::vector<uint8_t> img(o_tiles, 0);
+    std::memcpy(img.data() + o_roots, p + g.off_roots, sz_roots);
+    std::memcpy(img.data() + o_groups, p + g.off_groups, sz_groups);
+    std::memcpy(img.data() + o_offs, p + g.off_offs, (size_t)g.n_sig * 2);
+    std::memcpy(img.data() + o_recs, p + g.off_recs, (size_t)g.n_recw * 4);
+    std::memcpy(img.data() + o_mvs, p + g.off_mvs, (size_t)g.n_mvw * 4);
+    if (!ref_tab.empty()) std::memcpy(img.data() + o_tab, ref_tab.data(), ref_tab.size() * 4);
+    uint8_t *base = static_cast<uint8_t *>(s->d_mem);
+    DevStream &ds = s->ds;
+    ds.nu = g.nu; ds.nv = g.nv; ds.W = g.W; ds.H = g.H; ds.L = g.L; ds.B = g.B; ds.Ws = g.Ws; ds.q = g.q;
+    ds.mc = g.mc; ds.mv_mode = g.mv_mode; ds.mv_b = g.mv_b; ds.nbx = g.nbx; ds.nby = g.nby;
+    ds.nblocks = g.nblocks; ds.ngroups = g.ngroups; ds.side = g.side;
+    for (int l = 0; l <= kMaxLevels; l++) {
+        ds.gu[l] = l <= g.L ? g.gu[l] : 1;
+        ds.gv[l] = l <= g.L ? g.gv[l] : 1;
+    }
+    for (int l = 0; l < kMaxLevels; l++) {
+        ds.nc_base[l] = l < g.L ? (int)g.nc_base[l] : 0;
+        ds.ref_base[l] = l < g.L ? (int)g.ref_base[l] : 0;
+        ds.pred_base[l] = l < g.L ? (int)g.pred_base[l] : 0;
+    }
+    ds.roots = reinterpret_cast<const int16_t *>(base + o_roots);
+    ds.groups = reinterpret_cast<const uint4 *>(base + o_groups);
+    ds.offs = reinterpret_cast<const uint16_t *>(base + o_offs);
+    ds.recs = reinterpret_cast<const uint32_t *>(base + o_recs);
+    ds.mvs = reinterpret_cast<const uint32_t *>(base + o_mvs);
+    ds.ref_tab = reinterpret_cast<const uint32_t *>(base + o_tab);
+    ds.tiles = reinterpret_cast<const int16_t *>(base + o_tiles);
+    ds.status = reinterpret_cast<uint32_t *>(base + o_status);
+    e = cudaMemcpyAsync(base, img.data(), img.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !tile_src.empty())
+        e = cudaMemcpyAsync(base + o_src, tile_src.data(), tile_src.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_tiles, 0, (size_t)B2 * 2, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_status, 0, 256, st);
+    if (e == cudaSuccess)
+        e = launch_decode_tiles(ds, reinterpret_cast<const uint32_t *>(base + o_src), (int)s->n_tiles,
+                                reinterpret_cast<int16_t *>(base + o_tiles), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        hmlfc_free_stream(s);
+        return cuda_fail(e, "loading the stream");
+    }
+    *out = s;
+    return HMLFC_OK;
+}
+
+void hmlfc_free_stream(hmlfc_stream *s) {
+    if (!s) return;
+    if (s->d_mem) {
+        DeviceGuard guard(s->device);
+        cudaFree(s->d_mem);
+    }
+    delete s;
+}
+
+int hmlfc_stream_info(const hmlfc_stream *s, hmlfc_stream_info_t *out) {
+    if (!s || !out) return fail(HMLFC_E_INVALID_ARG, "NULL argument");
+    const Geometry &g = s->g;
+    out->nu = g.nu; out->nv = g.nv; out->width = g.W; out->height = g.H; out->levels = g.L; out->block = g.B;
+    out->search = g.Ws; out->qstep = g.q; out->mc = g.mc; out->n_roots = (int32_t)g.n_roots;
+    out->n_nc = g.n_nc; out->n_blocks = g.nblocks; out->n_sig = g.n_sig; out->n_ref_tiles = s->n_tiles;
+    out->stream_bytes = (int64_t)s->bytes.size();
+    out->device_bytes = (int64_t)s->d_bytes;
+    return HMLFC_OK;
+}
+
+int hmlfc_decode_pixels(const hmlfc_stream *s, const int32_t *d_coords, int64_t n, uint8_t *d_rgb, void *cuda_stream) {
+    if (!s) return fail(HMLFC_E_INVALID_ARG, "stream is NULL");
+    if (n < 0) return fail(HMLFC_E_INVALID_ARG, "negative count");
+    if (n == 0) return HMLFC_OK;
+    if (!d_coords || !d_rgb) return fail(HMLFC_E_INVALID_ARG, "NULL buffer");
+    DeviceGuard guard(s->device);
+    const cudaError_t e = launch_decode_pixels(s->ds, d_coords, n, d_rgb, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? HMLFC_OK : cuda_fail(e, "decode_pixels launch");
+}
+
+int hmlfc_check_status(const hmlfc_stream *s, void *cuda_stream) {
+    if (!s) return fail(HMLFC_E_INVALID_ARG, "stream is NULL");
+    DeviceGuard guard(s->device);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    uint32_t v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, s->ds.status, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && v) e = cudaMemsetAsync(s->ds.status, 0, 4, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (v & 1u) return fail(HMLFC_E_INVALID_ARG, "a decoded coordinate was outside the light field");
+    return HMLFC_OK;
+}
+
+int hmlfc_render_views(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views, int n_views,
+                       float *d_out, void *cuda_stream) {
+    int rc = check_views(streams, n_streams, h_views, n_views);
+    if (rc != HMLFC_OK) return rc;
+    if (n_views > 0 && !d_out) return fail(HMLFC_E_INVALID_ARG, "d_out is NULL");
+    if (n_views == 0) return HMLFC_OK;
+    DeviceGuard guard(streams[0]->device);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    return for_view_chunks(streams, n_streams, h_views, n_views,
+                           [&](const hmlfc_stream *s, const LaunchViews &lv, int tiles) {
+                               const cudaError_t e = launch_render(s->ds, lv, tiles, d_out, g_render_path, st);
+                               return e == cudaSuccess ? HMLFC_OK : cuda_fail(e, "render launch");
+                           });
+}
+
+int hmlfc_render_views_relaxed(const hmlfc_stream *const *streams, int n_streams, const float *const *d_coeff,
+                               const float *const *d_root, const hmlfc_view *h_views, int n_views, float *d_out,
+                               void *cuda_stream) {
+    int rc = check_views(streams, n_streams, h_views, n_views);
+    if (rc != HMLFC_OK) return rc;
+    if (n_views == 0) return HMLFC_OK;
+    if (!d_out || !d_coeff || !d_root) return fail(HMLFC_E_INVALID_ARG, "NULL buffer");
+    DeviceGuard guard(streams[0]->device);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const hmlfc_stream *s0 = streams[0];
+    (void)s0;
+    return for_view_chunks(streams, n_streams, h_views, n_views,
+                           [&](const hmlfc_stream *s, const LaunchViews &lv, int tiles) {
+                               const int k = lv.views[0].lf;
+                               if (!d_coeff[k] || !d_root[k]) return fail(HMLFC_E_INVALID_ARG, "NULL coefficients");
+                               const cudaError_t e =
+                                   launch_render_relaxed(s->ds, lv, tiles, d_coeff[k], d_root[k], d_out, st);
+                               return e == cudaSuccess ? HMLFC_OK : cuda_fail(e, "relaxed render launch");
+                           });
+}
+
+int hmlfc_render_backward(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views, int n_views,
+                          const float *d_grad_out, float *const *d_grad_coeff, float *const *d_grad_root,
+                          void *cuda_stream) {
+    int rc = check_views(streams, n_streams, h_views, n_views);
+    if (rc != HMLFC_OK) return rc;
+    if (n_views == 0) return HMLFC_OK;
+    if (!d_grad_out || !d_grad_coeff || !d_grad_root) return fail(HMLFC_E_INVALID_ARG, "NULL buffer");
+    DeviceGuard guard(streams[0]->device);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    return for_view_chunks(streams, n_streams, h_views, n_views,
+                           [&](const hmlfc_stream *s, const LaunchViews &lv, int tiles) {
+                               const int k = lv.views[0].lf;
+                               if (!d_grad_coeff[k] || !d_grad_root[k]) return fail(HMLFC_E_INVALID_ARG, "NULL gradient");
+                               const cudaError_t e = launch_render_backward(s->ds, lv, tiles, d_grad_out,
+                                                                            d_grad_coeff[k], d_grad_root[k], st);
+                               return e == cudaSuccess ? HMLFC_OK : cuda_fail(e, "backward launch");
+                           });
+}
+
+int hmlfc_dequant(const hmlfc_stream *s, float *d_coeff, float *d_root, void *cuda_stream) {
+    if (!s || !d_coeff || !d_root) return fail(HMLFC_E_INVALID_ARG, "NULL argument");
+    DeviceGuard guard(s->device);
+    const cudaError_t e = launch_dequant(s->ds, s->g.n_nc, d_coeff, d_root, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? HMLFC_OK : cuda_fail(e, "dequant launch");
+}
+
+void hmlfc_free_host(void *p) { std::free(p); }
+
+}  // extern "C"
+

@@ -1,0 +1,65 @@
+// Internal definitions shared by the host code and the CUDA kernels of the
+// product library (never by the CPU oracle).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "hmlfc.h"
+
+namespace hmlfc {
+
+constexpr int kMaxLevels = 16;      // tree height limit (grid up to 65536 per axis)
+constexpr int kMaxBlock = 64;       // block size limit
+constexpr int kCoefLimit = 16384;   // |dequantised coefficient| bound enforced at load
+constexpr uint32_t kMagic = 0x464C4D48u;
+constexpr uint32_t kVersion = 1u;
+constexpr int kHeaderWords = 32;
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+
+// Everything a kernel needs to decode samples of one stream.  Passed by value
+// as a kernel parameter (it lives in the constant bank while the kernel runs).
+struct DevStream {
+    int nu, nv, W, H, L, B, Ws, q, mc, mv_mode, mv_b;
+    int nbx, nby, nblocks, ngroups;
+    int side;                       // 8 * Ws + 1
+    int gu[kMaxLevels + 1], gv[kMaxLevels + 1];
+    int nc_base[kMaxLevels];        // breadth-first index of level l's first node-channel
+    int ref_base[kMaxLevels];       // rank of level l's first reference node-channel
+    int pred_base[kMaxLevels];      // rank of level l's first predictive node-channel
+    const int16_t *roots;           // [roots][3][H][W]
+    const uint4 *groups;            // [n_nc][ngroups] {bitmap, record base, offset base, 0}
+    const uint16_t *offs;           // [n_sig]
+    const uint32_t *recs;           // [n_rec_words + 2]
+    const uint32_t *mvs;            // [n_mv_words + 2]
+    const uint32_t *ref_tab;        // [n_ref_nc][nblocks] tile index, 0 = the zero tile
+    const int16_t *tiles;           // [n_tiles + 1][B * B]
+    uint32_t *status;               // bit 0: an out-of-range coordinate was seen
+};
+
+// Views of one launch, by value (kernel parameter space).
+constexpr int kMaxViewsPerLaunch = 128;
+
+struct LaunchViews {
+    int n_views;
+    int tile_w, tile_h;
+    int tile_start[kMaxViewsPerLaunch + 1];
+    hmlfc_view views[kMaxViewsPerLaunch];
+};
+
+// Launchers implemented in hmlfc_kernels.cu.
+cudaError_t launch_decode_tiles(const DevStream &ds, const uint32_t *d_src, int n_tiles, int16_t *d_tiles,
+                                cudaStream_t st);
+cudaError_t launch_decode_pixels(const DevStream &ds, const int32_t *d_coords, int64_t n, uint8_t *d_rgb,
+                                 cudaStream_t st);
+cudaError_t launch_render(const DevStream &ds, const LaunchViews &lv, int total_tiles, float *d_out, int mode,
+                          cudaStream_t st);
+cudaError_t launch_render_relaxed(const DevStream &ds, const LaunchViews &lv, int total_tiles, const float *coeff,
+                                  const float *root, float *d_out, cudaStream_t st);
+cudaError_t launch_render_backward(const DevStream &ds, const LaunchViews &lv, int total_tiles,
+                                   const float *grad_out, float *grad_coeff, float *grad_root, cudaStream_t st);
+cudaError_t launch_dequant(const DevStream &ds, int64_t n_nc, float *coeff, float *root, cudaStream_t st);
+
+}  // namespace hmlfc

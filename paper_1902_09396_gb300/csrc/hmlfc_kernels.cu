@@ -1,0 +1,809 @@
+// CUDA kernels of the HMLFC library for sm_103a (GB300).
+//
+// The decode is a gather over a small, L2-resident working set, not a dense
+// contraction, so no tensor cores are used.  The render kernel stages the
+// samples a CTA's rays share: it reduces the tile's footprint (cameras and
+// pixels its 16-sample neighbourhoods reach), decodes every block record and
+// motion vector of that footprint once into shared memory (per level, node,
+// channel and block), reconstructs the level-1 images of the footprint once
+// (root + levels L-1..1, shared by up to four cameras), then the level-0
+// samples, and finally blends each ray's 16 samples from shared memory.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+
+#include "hmlfc_internal.h"
+
+namespace hmlfc {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// bit fields and BISE (Sec. 4.6)
+// ---------------------------------------------------------------------------
+
+// `width` (<= 16) bits at bit `pos` of the word array; reads w[pos/32 + 1]
+// too, which the device copies pad.
+__device__ __forceinline__ uint32_t bits_at(const uint32_t *__restrict__ w, uint32_t pos, uint32_t width) {
+    const uint32_t k = pos >> 5;
+    const uint32_t v = __funnelshift_r(__ldg(w + k), __ldg(w + k + 1), pos & 31u);
+    return v & ((1u << width) - 1u);
+}
+
+// Digit r (0-based, least significant first) of a packed trit byte or quint
+// field, without a runtime divide: floor(p / 3^r) = (p * M3[r]) >> 16 for
+// p < 256 and floor(p / 5^r) = (p * M5[r]) >> 16 for p < 128 (checked
+// exhaustively), then the last digit by the same trick.
+__device__ __forceinline__ uint32_t trit_digit(uint32_t packed, uint32_t r) {
+    const uint32_t m = r == 0 ? 65536u : (uint32_t)((0x032A097C1C725556ull >> (16u * (r - 1u))) & 0xFFFFu);
+    const uint32_t d = (packed * m) >> 16;
+    return d - 3u * ((d * 171u) >> 9);
+}
+
+__device__ __forceinline__ uint32_t quint_digit(uint32_t packed, uint32_t r) {
+    const uint32_t m = r == 0 ? 65536u : (r == 1 ? 13108u : 2622u);
+    const uint32_t d = (packed * m) >> 16;
+    return d - 5u * ((d * 205u) >> 10);
+}
+
+// Value i of a BISE sequence starting at word w (i < 2^16: block payloads).
+__device__ __forceinline__ uint32_t bise_get_small(const uint32_t *__restrict__ w, uint32_t mode, uint32_t b,
+                                                   uint32_t i) {
+    if (mode == 0) return bits_at(w, i * b, b);
+    if (mode == 1) {
+        const uint32_t g = i / 5u, r = i - 5u * g;
+        const uint32_t pos = g * (8u + 5u * b);
+        const uint32_t hi = trit_digit(bits_at(w, pos, 8), r);
+        return (hi << b) | bits_at(w, pos + 8u + r * b, b);
+    }
+    const uint32_t g = i / 3u, r = i - 3u * g;
+    const uint32_t pos = g * (7u + 3u * b);
+    const uint32_t hi = quint_digit(bits_at(w, pos, 7), r);
+    return (hi << b) | bits_at(w, pos + 7u + r * b, b);
+}
+
+// Value i of a long BISE sequence (the motion-vector symbols).
+__device__ __forceinline__ uint32_t bise_get_long(const uint32_t *__restrict__ w, uint32_t mode, uint32_t b,
+                                                  uint64_t i) {
+    uint64_t pos;
+    uint32_t r = 0, hw = 0;
+    if (mode == 0) {
+        pos = i * b;
+        return bits_at(w + (pos >> 5), (uint32_t)(pos & 31u), b);
+    }
+    if (mode == 1) {
+        const uint64_t g = i / 5u;
+        r = (uint32_t)(i - 5u * g);
+        pos = g * (8u + 5u * b);
+        hw = 8;
+    } else {
+        const uint64_t g = i / 3u;
+        r = (uint32_t)(i - 3u * g);
+        pos = g * (7u + 3u * b);
+        hw = 7;
+    }
+    const uint32_t *base = w + (pos >> 5);
+    const uint32_t p0 = (uint32_t)(pos & 31u);
+    const uint32_t packed = bits_at(base, p0, hw);
+    const uint32_t hi = mode == 1 ? trit_digit(packed, r) : quint_digit(packed, r);
+    return (hi << b) | bits_at(base, p0 + hw + r * b, b);
+}
+
+// ---------------------------------------------------------------------------
+// per-level tables, copied to shared memory by every CTA
+// ---------------------------------------------------------------------------
+
+struct LevelTabs {
+    int gu[kMaxLevels + 1], gv[kMaxLevels + 1];
+    int nc_base[kMaxLevels], ref_base[kMaxLevels], pred_base[kMaxLevels];
+};
+
+__device__ __forceinline__ void load_tabs(const DevStream &S, LevelTabs &T) {
+    for (int t = threadIdx.x; t <= kMaxLevels; t += blockDim.x) {
+        T.gu[t] = S.gu[t];
+        T.gv[t] = S.gv[t];
+        if (t < kMaxLevels) {
+            T.nc_base[t] = S.nc_base[t];
+            T.ref_base[t] = S.ref_base[t];
+            T.pred_base[t] = S.pred_base[t];
+        }
+    }
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
+
+__device__ __forceinline__ bool is_ref(int a, int b) { return ((a | b) & 1) == 0; }
+
+__device__ __forceinline__ int ref_rank(const LevelTabs &T, int l, int a, int b, int c) {
+    return T.ref_base[l] + ((a >> 1) * ((T.gv[l] + 1) >> 1) + (b >> 1)) * 3 + c;
+}
+
+__device__ __forceinline__ int pred_rank(const LevelTabs &T, int l, int a, int b, int c) {
+    const int gv = T.gv[l];
+    const int refs_before = ((a + 1) >> 1) * ((gv + 1) >> 1) + ((a & 1) == 0 ? (b + 1) >> 1 : 0);
+    return T.pred_base[l] + (a * gv + b - refs_before) * 3 + c;
+}
+
+__device__ __forceinline__ int nc_index(const LevelTabs &T, int l, int a, int b, int c) {
+    return T.nc_base[l] + (a * T.gv[l] + b) * 3 + c;
+}
+
+// Block geometry, specialised on the block size (BS > 0: compile-time power
+// of two; BS == 0: the runtime value S.B).
+template <int BS>
+struct Blk {
+    int B;
+    __device__ __forceinline__ explicit Blk(int b) : B(BS > 0 ? BS : b) {}
+    __device__ __forceinline__ int div(int v) const { return BS > 0 ? (v / BS) : (v / B); }
+    __device__ __forceinline__ int size() const { return BS > 0 ? BS : B; }
+};
+
+// Resident reference coefficient R^ at (x, y) of reference node-channel row
+// `row` (= ref rank * nblocks).
+template <int BS>
+__device__ __forceinline__ int ref_coef(const DevStream &S, const Blk<BS> &bk, uint32_t row, int x, int y) {
+    const int bx = bk.div(x), by = bk.div(y);
+    const int B = bk.size();
+    const uint32_t tile = __ldg(S.ref_tab + row + (uint32_t)(by * S.nbx + bx));
+    return __ldg(S.tiles + (size_t)tile * (B * B) + (y - by * B) * B + (x - bx * B));
+}
+
+// Sec. 4.4 motion re-compensation with the quarter-pel bilinear predictor.
+template <int BS>
+__device__ __forceinline__ int mc_pred(const DevStream &S, const Blk<BS> &bk, uint32_t row, int x, int y, int mvx,
+                                       int mvy) {
+    const int X = 4 * x + mvx, Y = 4 * y + mvy;
+    const int x0 = X >> 2, y0 = Y >> 2, fx = X & 3, fy = Y & 3;
+    const int xa = clampi(x0, 0, S.W - 1), xb = clampi(x0 + 1, 0, S.W - 1);
+    const int ya = clampi(y0, 0, S.H - 1), yb = clampi(y0 + 1, 0, S.H - 1);
+    const int a = ref_coef(S, bk, row, xa, ya), b = ref_coef(S, bk, row, xb, ya);
+    const int c = ref_coef(S, bk, row, xa, yb), d = ref_coef(S, bk, row, xb, yb);
+    const int s = (4 - fx) * (4 - fy) * a + fx * (4 - fy) * b + (4 - fx) * fy * c + fx * fy * d;
+    return (s + 8) >> 4;
+}
+
+__device__ __forceinline__ void decode_mv(const DevStream &S, uint32_t sym, int &mvx, int &mvy, int &sign) {
+    sign = (sym & 1u) ? -1 : 1;
+    const uint32_t s2 = sym >> 1;
+    const uint32_t qx = s2 / (uint32_t)S.side;
+    mvx = (int)qx - 4 * S.Ws;
+    mvy = (int)(s2 - qx * (uint32_t)S.side) - 4 * S.Ws;
+}
+
+// Residual r^ of block k (record lookup through the group index).
+__device__ __forceinline__ int residual(const DevStream &S, int nc, int k, uint32_t idx) {
+    const uint4 g = __ldg(S.groups + (size_t)nc * S.ngroups + (k >> 5));
+    const uint32_t bit = (uint32_t)k & 31u;
+    if (!((g.x >> bit) & 1u)) return 0;
+    const uint32_t rank = __popc(g.x & ((1u << bit) - 1u));
+    const uint32_t rec = g.y + __ldg(S.offs + g.z + rank);
+    const uint32_t hdr = __ldg(S.recs + rec);
+    const int m = (int)(int16_t)(hdr & 0xFFFFu);
+    return S.q * (m + (int)bise_get_small(S.recs + rec + 1, (hdr >> 21) & 3u, (hdr >> 16) & 31u, idx));
+}
+
+// SRV value of node (a, b) at level l, channel c, pixel (x, y), straight
+// from the index (no staging).
+template <int BS>
+__device__ int srv_direct(const DevStream &S, const LevelTabs &T, const Blk<BS> &bk, int l, int a, int b, int c, int x,
+                          int y) {
+    const int B = bk.size();
+    const int bx = bk.div(x), by = bk.div(y);
+    const int k = by * S.nbx + bx;
+    if (is_ref(a, b)) return ref_coef(S, bk, (uint32_t)ref_rank(T, l, a, b, c) * S.nblocks, x, y);
+    const int x0 = bx * B, y0 = by * B;
+    const int bw = min(B, S.W - x0);
+    const int r = residual(S, nc_index(T, l, a, b, c), k, (uint32_t)((y - y0) * bw + (x - x0)));
+    if (!S.mc) return r;
+    const uint32_t sym =
+        bise_get_long(S.mvs, S.mv_mode, S.mv_b, (uint64_t)pred_rank(T, l, a, b, c) * S.nblocks + k);
+    int mvx, mvy, sign;
+    decode_mv(S, sym, mvx, mvy, sign);
+    const uint32_t row = (uint32_t)ref_rank(T, l, a & ~1, b & ~1, c) * S.nblocks;
+    return sign * mc_pred(S, bk, row, x, y, mvx, mvy) + r;
+}
+
+__device__ __forceinline__ uint32_t ycocg_to_rgb8(int Y, int Co, int Cg) {
+    const int t = Y - (Cg >> 1);
+    const int G = Cg + t;
+    const int Bc = t - (Co >> 1);
+    const int R = Bc + Co;
+    return (uint32_t)clampi(R, 0, 255) | ((uint32_t)clampi(G, 0, 255) << 8) | ((uint32_t)clampi(Bc, 0, 255) << 16);
+}
+
+// Full random-access decoding of one sample (Sec. 4.8.1).
+template <int BS>
+__device__ uint32_t sample_direct(const DevStream &S, const LevelTabs &T, const Blk<BS> &bk, int i, int j, int x,
+                                  int y) {
+    const int L = S.L;
+    const size_t plane = (size_t)S.W * S.H;
+    const size_t rbase = ((size_t)(i >> L) * T.gv[L] + (j >> L)) * 3 * plane + (size_t)y * S.W + x;
+    int v0 = __ldg(S.roots + rbase), v1 = __ldg(S.roots + rbase + plane), v2 = __ldg(S.roots + rbase + 2 * plane);
+    for (int l = 0; l < L; l++) {
+        const int a = i >> l, b = j >> l;
+        v0 += srv_direct(S, T, bk, l, a, b, 0, x, y);
+        v1 += srv_direct(S, T, bk, l, a, b, 1, x, y);
+        v2 += srv_direct(S, T, bk, l, a, b, 2, x, y);
+    }
+    return ycocg_to_rgb8(v0, v1, v2);
+}
+
+// ---------------------------------------------------------------------------
+// K3: load-time decode of the reference SRV blocks into resident tiles
+// ---------------------------------------------------------------------------
+
+// src[t] = {record word, block valid width, block valid height, unused} for
+// tile t + 1 (tile 0 is the shared zero tile).
+__global__ void k_decode_tiles(const DevStream S, const uint4 *__restrict__ src, int n_tiles,
+                               int16_t *__restrict__ tiles) {
+    const int t = blockIdx.x;
+    if (t >= n_tiles) return;
+    const uint4 s = src[t];
+    const uint32_t hdr = __ldg(S.recs + s.x);
+    const int m = (int)(int16_t)(hdr & 0xFFFFu);
+    const uint32_t mode = (hdr >> 21) & 3u, b = (hdr >> 16) & 31u;
+    const int B = S.B;
+    int16_t *dst = tiles + (size_t)(t + 1) * B * B;
+    for (int p = threadIdx.x; p < B * B; p += blockDim.x) {
+        const int yy = p / B, xx = p - yy * B;
+        int v = 0;
+        if (xx < (int)s.y && yy < (int)s.z)
+            v = S.q * (m + (int)bise_get_small(S.recs + s.x + 1, mode, b, (uint32_t)(yy * (int)s.y + xx)));
+        dst[p] = (int16_t)v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K2: random-access decoding of a list of samples
+// ---------------------------------------------------------------------------
+
+template <int BS>
+__global__ void __launch_bounds__(256) k_decode_pixels(const DevStream S, const int4 *__restrict__ coords, int64_t n,
+                                                       uint8_t *__restrict__ rgb) {
+    __shared__ LevelTabs T;
+    load_tabs(S, T);
+    __syncthreads();
+    const Blk<BS> bk(S.B);
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int4 c = __ldg(coords + k);
+        uint32_t v = 0;
+        if (c.x < 0 || c.x >= S.nu || c.y < 0 || c.y >= S.nv || c.z < 0 || c.z >= S.W || c.w < 0 || c.w >= S.H) {
+            atomicOr(S.status, 1u);
+        } else {
+            v = sample_direct(S, T, bk, c.x, c.y, c.z, c.w);
+        }
+        rgb[3 * k] = (uint8_t)(v & 0xFFu);
+        rgb[3 * k + 1] = (uint8_t)((v >> 8) & 0xFFu);
+        rgb[3 * k + 2] = (uint8_t)((v >> 16) & 0xFFu);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// ray setup (Sec. 2.1 two-plane parameterisation)
+// ---------------------------------------------------------------------------
+
+struct Ray {
+    int i0, i1, j0, j1, x0, x1, y0, y1;
+    float fu, fv, fs, ft;
+};
+
+__device__ __forceinline__ float axis_nb(float c, int n, int &i0, int &i1) {
+    const float cc = fminf(fmaxf(c, -1.0f), (float)n);
+    const float fl = floorf(cc);
+    const int k = (int)fl;
+    i0 = clampi(k, 0, n - 1);
+    i1 = clampi(k + 1, 0, n - 1);
+    return cc - fl;
+}
+
+__device__ __forceinline__ void ray_setup(const hmlfc_view &V, int nu, int nv, int W, int H, int px, int py, Ray &r) {
+    const float X = (float)px + 0.5f, Y = (float)py + 0.5f;
+    const float *h = V.H_uv;
+    const float wu = h[6] * X + h[7] * Y + h[8];
+    const float u = (h[0] * X + h[1] * Y + h[2]) / wu;
+    const float v = (h[3] * X + h[4] * Y + h[5]) / wu;
+    const float *g = V.H_st;
+    const float ws = g[6] * X + g[7] * Y + g[8];
+    const float s = (g[0] * X + g[1] * Y + g[2]) / ws;
+    const float t = (g[3] * X + g[4] * Y + g[5]) / ws;
+    r.fu = axis_nb(u, nu, r.i0, r.i1);
+    r.fv = axis_nb(v, nv, r.j0, r.j1);
+    r.fs = axis_nb(s, W, r.x0, r.x1);
+    r.ft = axis_nb(t, H, r.y0, r.y1);
+}
+
+// Quadrilinear blend of the 16 samples, in a fixed order (a, b, xs, ys).
+template <class F>
+__device__ __forceinline__ void blend16(const Ray &r, F fetch, float out[3]) {
+    const float wu[2] = {1.0f - r.fu, r.fu}, wv[2] = {1.0f - r.fv, r.fv};
+    const float ws[2] = {1.0f - r.fs, r.fs}, wt[2] = {1.0f - r.ft, r.ft};
+    const int ii[2] = {r.i0, r.i1}, jj[2] = {r.j0, r.j1}, xx[2] = {r.x0, r.x1}, yy[2] = {r.y0, r.y1};
+    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int b = 0; b < 2; b++)
+#pragma unroll
+            for (int xs = 0; xs < 2; xs++)
+#pragma unroll
+                for (int ys = 0; ys < 2; ys++) {
+                    const float w = wu[a] * wv[b] * ws[xs] * wt[ys];
+                    const uint32_t p = fetch(ii[a], jj[b], xx[xs], yy[ys]);
+                    acc0 += w * (float)(p & 0xFFu);
+                    acc1 += w * (float)((p >> 8) & 0xFFu);
+                    acc2 += w * (float)((p >> 16) & 0xFFu);
+                }
+    const float inv = 1.0f / 255.0f;
+    out[0] = acc0 * inv;
+    out[1] = acc1 * inv;
+    out[2] = acc2 * inv;
+}
+
+__device__ __forceinline__ int find_view(const LaunchViews &LV, int tile) {
+    int lo = 0, hi = LV.n_views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (LV.tile_start[mid] <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// K1: fused decode + render
+// ---------------------------------------------------------------------------
+
+constexpr int kMaxCam = 9;          // cameras of a staged footprint (3 x 3)
+constexpr int kMaxPx = 400;         // pixels of a staged footprint
+constexpr int kMaxDesc = 512;       // block descriptors of a staged footprint
+constexpr int kMaxN1 = 4;           // level-1 nodes of a staged footprint
+
+struct Footprint {
+    int imin, imax, jmin, jmax, xmin, xmax, ymin, ymax;
+    int ncv, nx, npx, nbxb, nblk, bx0, by0, n1v;
+    int staged;
+    int a0[kMaxLevels], b0[kMaxLevels], nnv[kMaxLevels], dbase[kMaxLevels + 1];
+};
+
+constexpr size_t kStageSmem = (size_t)kMaxDesc * 16 + (size_t)kMaxN1 * 3 * kMaxPx * 4 + (size_t)kMaxCam * kMaxPx * 4;
+
+template <int BS>
+__device__ __forceinline__ int srv_staged(const DevStream &S, const Footprint &F, const Blk<BS> &bk,
+                                          const uint4 *__restrict__ desc, int l, int a, int b, int c, int x, int y) {
+    const int B = bk.size();
+    const int bx = bk.div(x), by = bk.div(y);
+    const int blk = (by - F.by0) * F.nbxb + (bx - F.bx0);
+    const uint4 d = desc[F.dbase[l] + (((a - F.a0[l]) * F.nnv[l] + (b - F.b0[l])) * 3 + c) * F.nblk + blk];
+    const int x0 = bx * B, y0 = by * B;
+    if (is_ref(a, b)) return __ldg(S.tiles + (size_t)d.y * (B * B) + (y - y0) * B + (x - x0));
+    int r = 0;
+    if (d.x != kNone) {
+        const int bw = min(B, S.W - x0);
+        const int m = (int)(int16_t)(d.y & 0xFFFFu);
+        r = S.q * (m + (int)bise_get_small(S.recs + d.x + 1, (d.y >> 21) & 3u, (d.y >> 16) & 31u,
+                                           (uint32_t)((y - y0) * bw + (x - x0))));
+    }
+    if (!S.mc) return r;
+    const int mvx = (int)(d.z & 1023u) - 512, mvy = (int)((d.z >> 10) & 1023u) - 512;
+    const int sign = ((d.z >> 20) & 1u) ? -1 : 1;
+    return sign * mc_pred(S, bk, d.w, x, y, mvx, mvy) + r;
+}
+
+template <int BS, int TW, int TH>
+__global__ void __launch_bounds__(TW *TH) k_render(const __grid_constant__ DevStream S,
+                                                  const __grid_constant__ LaunchViews LV, float *__restrict__ out,
+                                                  int force_direct) {
+    constexpr int NT = TW * TH;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ LevelTabs T;
+    __shared__ Footprint F;
+    __shared__ int s_view;
+    __shared__ int s_red[NT / 32][8];
+
+    load_tabs(S, T);
+    if (threadIdx.x == 0) s_view = find_view(LV, blockIdx.x);
+    __syncthreads();
+    const hmlfc_view &V = LV.views[s_view];
+    const int tiles_x = (V.width + TW - 1) / TW;
+    const int local = blockIdx.x - LV.tile_start[s_view];
+    const int px = (local % tiles_x) * TW + (int)threadIdx.x % TW;
+    const int py = (local / tiles_x) * TH + (int)threadIdx.x / TW;
+    const bool act = px < V.width && py < V.height;
+    const Blk<BS> bk(S.B);
+
+    Ray r;
+    ray_setup(V, S.nu, S.nv, S.W, S.H, act ? px : 0, act ? py : 0, r);
+
+    // ---- footprint of the tile (min/max over active rays) ----
+    int red[8] = {act ? r.i0 : INT_MAX, act ? -r.i1 : INT_MAX, act ? r.j0 : INT_MAX, act ? -r.j1 : INT_MAX,
+                  act ? r.x0 : INT_MAX, act ? -r.x1 : INT_MAX, act ? r.y0 : INT_MAX, act ? -r.y1 : INT_MAX};
+#pragma unroll
+    for (int q = 0; q < 8; q++) red[q] = __reduce_min_sync(0xFFFFFFFFu, red[q]);
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int q = 0; q < 8; q++) s_red[threadIdx.x >> 5][q] = red[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int m[8];
+        for (int q = 0; q < 8; q++) m[q] = INT_MAX;
+        for (int w = 0; w < NT / 32; w++)
+            for (int q = 0; q < 8; q++) m[q] = min(m[q], s_red[w][q]);
+        F.imin = m[0]; F.imax = -m[1]; F.jmin = m[2]; F.jmax = -m[3];
+        F.xmin = m[4]; F.xmax = -m[5]; F.ymin = m[6]; F.ymax = -m[7];
+        const int ncu = F.imax - F.imin + 1, ncv = F.jmax - F.jmin + 1;
+        F.ncv = ncv;
+        F.nx = F.xmax - F.xmin + 1;
+        F.npx = F.nx * (F.ymax - F.ymin + 1);
+        F.bx0 = F.xmin / S.B;
+        F.by0 = F.ymin / S.B;
+        F.nbxb = F.xmax / S.B - F.bx0 + 1;
+        F.nblk = F.nbxb * (F.ymax / S.B - F.by0 + 1);
+        int nd = 0;
+        for (int l = 0; l < S.L; l++) {
+            F.a0[l] = F.imin >> l;
+            F.b0[l] = F.jmin >> l;
+            F.nnv[l] = (F.jmax >> l) - F.b0[l] + 1;
+            F.dbase[l] = nd;
+            nd += ((F.imax >> l) - F.a0[l] + 1) * F.nnv[l] * 3 * F.nblk;
+        }
+        F.dbase[S.L] = nd;
+        F.n1v = (F.jmax >> 1) - (F.jmin >> 1) + 1;
+        const int n1 = ((F.imax >> 1) - (F.imin >> 1) + 1) * F.n1v;
+        F.staged = !force_direct && ncu * ncv <= kMaxCam && F.npx <= kMaxPx && nd <= kMaxDesc && n1 <= kMaxN1;
+    }
+    __syncthreads();
+
+    float o[3];
+    if (!F.staged) {
+        // ---- direct path: every ray decodes its own 16 samples ----
+        if (act) {
+            blend16(r, [&](int i, int j, int x, int y) { return sample_direct(S, T, bk, i, j, x, y); }, o);
+        }
+    } else {
+        uint4 *desc = reinterpret_cast<uint4 *>(smem);
+        int *acc1 = reinterpret_cast<int *>(smem + (size_t)kMaxDesc * 16);
+        uint32_t *rgb = reinterpret_cast<uint32_t *>(smem + (size_t)kMaxDesc * 16 + (size_t)kMaxN1 * 3 * kMaxPx * 4);
+        const int L = S.L;
+        const int B = bk.size();
+        // ---- B1: block descriptors (index, header, motion vector) ----
+        for (int d = threadIdx.x; d < F.dbase[L]; d += NT) {
+            int l = 0;
+            while (d >= F.dbase[l + 1]) l++;
+            int e = d - F.dbase[l];
+            const int blk = e % F.nblk;
+            e /= F.nblk;
+            const int c = e % 3;
+            e /= 3;
+            const int b = F.b0[l] + e % F.nnv[l];
+            const int a = F.a0[l] + e / F.nnv[l];
+            const int bx = F.bx0 + blk % F.nbxb, by = F.by0 + blk / F.nbxb;
+            const int k = by * S.nbx + bx;
+            uint4 out4 = make_uint4(kNone, 0u, 0u, 0u);
+            const bool inside = a < T.gu[l] && b < T.gv[l] && bx < S.nbx && by < S.nby;
+            if (inside) {
+                if (is_ref(a, b)) {
+                    out4.y = __ldg(S.ref_tab + (size_t)ref_rank(T, l, a, b, c) * S.nblocks + k);
+                } else {
+                    const int nc = nc_index(T, l, a, b, c);
+                    const uint4 g = __ldg(S.groups + (size_t)nc * S.ngroups + (k >> 5));
+                    const uint32_t bit = (uint32_t)k & 31u;
+                    if ((g.x >> bit) & 1u) {
+                        const uint32_t rec = g.y + __ldg(S.offs + g.z + __popc(g.x & ((1u << bit) - 1u)));
+                        out4.x = rec;
+                        out4.y = __ldg(S.recs + rec);
+                    }
+                    if (S.mc) {
+                        const uint32_t sym = bise_get_long(S.mvs, S.mv_mode, S.mv_b,
+                                                           (uint64_t)pred_rank(T, l, a, b, c) * S.nblocks + k);
+                        int mvx, mvy, sign;
+                        decode_mv(S, sym, mvx, mvy, sign);
+                        out4.z = (uint32_t)(mvx + 512) | ((uint32_t)(mvy + 512) << 10) | ((sign < 0 ? 1u : 0u) << 20);
+                        out4.w = (uint32_t)ref_rank(T, l, a & ~1, b & ~1, c) * S.nblocks;
+                    }
+                }
+            }
+            desc[d] = out4;
+        }
+        __syncthreads();
+        // ---- B2: level-1 reconstructions = root + SRV levels L-1 .. 1 ----
+        const int a1 = F.imin >> 1, b1 = F.jmin >> 1;
+        const int n1 = ((F.imax >> 1) - a1 + 1) * F.n1v;
+        const size_t plane = (size_t)S.W * S.H;
+        for (int e = threadIdx.x; e < n1 * 3 * F.npx; e += NT) {
+            const int p = e % F.npx;
+            const int c = (e / F.npx) % 3;
+            const int nd = e / (F.npx * 3);
+            const int a = a1 + nd / F.n1v, b = b1 + nd % F.n1v;
+            const int x = F.xmin + p % F.nx, y = F.ymin + p / F.nx;
+            int v = 0;
+            if (a < T.gu[1] && b < T.gv[1]) {
+                // node (a, b) of level 1 lies under root (a >> (L-1), b >> (L-1))
+                const int ra = a >> (L - 1), rb = b >> (L - 1);
+                v = __ldg(S.roots + ((size_t)(ra * T.gv[L] + rb) * 3 + c) * plane + (size_t)y * S.W + x);
+                for (int l = L - 1; l >= 1; l--)
+                    v += srv_staged(S, F, bk, desc, l, a >> (l - 1), b >> (l - 1), c, x, y);
+            }
+            acc1[e] = v;
+        }
+        __syncthreads();
+        // ---- B3: level-0 samples of the footprint's cameras -> RGB8 ----
+        const int ncam = (F.imax - F.imin + 1) * F.ncv;
+        for (int e = threadIdx.x; e < ncam * F.npx; e += NT) {
+            const int p = e % F.npx;
+            const int cam = e / F.npx;
+            const int i = F.imin + cam / F.ncv, j = F.jmin + cam % F.ncv;
+            const int x = F.xmin + p % F.nx, y = F.ymin + p / F.nx;
+            const int nd = ((i >> 1) - a1) * F.n1v + ((j >> 1) - b1);
+            const int *base = acc1 + (size_t)nd * 3 * F.npx + p;
+            const int v0 = base[0] + srv_staged(S, F, bk, desc, 0, i, j, 0, x, y);
+            const int v1 = base[F.npx] + srv_staged(S, F, bk, desc, 0, i, j, 1, x, y);
+            const int v2 = base[2 * F.npx] + srv_staged(S, F, bk, desc, 0, i, j, 2, x, y);
+            rgb[e] = ycocg_to_rgb8(v0, v1, v2);
+        }
+        (void)B;
+        __syncthreads();
+        // ---- C: blend ----
+        if (act) {
+            blend16(r,
+                    [&](int i, int j, int x, int y) {
+                        return rgb[((i - F.imin) * F.ncv + (j - F.jmin)) * F.npx + (y - F.ymin) * F.nx + (x - F.xmin)];
+                    },
+                    o);
+        }
+    }
+    if (act) {
+        float *dst = out + V.out_offset + ((size_t)py * V.width + px) * 3;
+        dst[0] = o[0];
+        dst[1] = o[1];
+        dst[2] = o[2];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// differentiable relaxation: forward and adjoint (one thread per ray)
+// ---------------------------------------------------------------------------
+
+struct RelaxTap {
+    int x[4], y[4];
+    float w[4];
+};
+
+__device__ __forceinline__ void relax_taps(const DevStream &S, int x, int y, int mvx, int mvy, RelaxTap &t) {
+    const int X = 4 * x + mvx, Y = 4 * y + mvy;
+    const int x0 = X >> 2, y0 = Y >> 2, fx = X & 3, fy = Y & 3;
+    const int xa = clampi(x0, 0, S.W - 1), xb = clampi(x0 + 1, 0, S.W - 1);
+    const int ya = clampi(y0, 0, S.H - 1), yb = clampi(y0 + 1, 0, S.H - 1);
+    t.x[0] = xa; t.y[0] = ya; t.w[0] = (float)((4 - fx) * (4 - fy)) * 0.0625f;
+    t.x[1] = xb; t.y[1] = ya; t.w[1] = (float)(fx * (4 - fy)) * 0.0625f;
+    t.x[2] = xa; t.y[2] = yb; t.w[2] = (float)((4 - fx) * fy) * 0.0625f;
+    t.x[3] = xb; t.y[3] = yb; t.w[3] = (float)(fx * fy) * 0.0625f;
+}
+
+template <int BS, bool kBackward>
+__global__ void __launch_bounds__(256) k_relax(const __grid_constant__ DevStream S,
+                                              const __grid_constant__ LaunchViews LV, const float *__restrict__ coeff,
+                                              const float *__restrict__ root, float *__restrict__ out,
+                                              const float *__restrict__ gout, float *__restrict__ gcoeff,
+                                              float *__restrict__ groot) {
+    constexpr int TW = 16, TH = 16;
+    __shared__ LevelTabs T;
+    __shared__ int s_view;
+    load_tabs(S, T);
+    if (threadIdx.x == 0) s_view = find_view(LV, blockIdx.x);
+    __syncthreads();
+    const hmlfc_view &V = LV.views[s_view];
+    const int tiles_x = (V.width + TW - 1) / TW;
+    const int local = blockIdx.x - LV.tile_start[s_view];
+    const int px = (local % tiles_x) * TW + (int)threadIdx.x % TW;
+    const int py = (local / tiles_x) * TH + (int)threadIdx.x / TW;
+    if (px >= V.width || py >= V.height) return;
+    const Blk<BS> bk(S.B);
+    Ray r;
+    ray_setup(V, S.nu, S.nv, S.W, S.H, px, py, r);
+    const size_t plane = (size_t)S.W * S.H;
+    const int L = S.L;
+    const size_t opix = V.out_offset + ((size_t)py * V.width + px) * 3;
+    float g[3] = {0.f, 0.f, 0.f};
+    if (kBackward) {
+        g[0] = gout[opix] * (1.0f / 255.0f);
+        g[1] = gout[opix + 1] * (1.0f / 255.0f);
+        g[2] = gout[opix + 2] * (1.0f / 255.0f);
+    }
+    const float wu[2] = {1.0f - r.fu, r.fu}, wv[2] = {1.0f - r.fv, r.fv};
+    const float ws[2] = {1.0f - r.fs, r.fs}, wt[2] = {1.0f - r.ft, r.ft};
+    const int ii[2] = {r.i0, r.i1}, jj[2] = {r.j0, r.j1}, xx[2] = {r.x0, r.x1}, yy[2] = {r.y0, r.y1};
+    float acc[3] = {0.f, 0.f, 0.f};
+    for (int s = 0; s < 16; s++) {
+        const int a = s >> 3, b = (s >> 2) & 1, xs = (s >> 1) & 1, ys = s & 1;
+        const float w = wu[a] * wv[b] * ws[xs] * wt[ys];
+        const int i = ii[a], j = jj[b], x = xx[xs], y = yy[ys];
+        const int B = bk.size();
+        const int k = bk.div(y) * S.nbx + bk.div(x);
+        const size_t pix = (size_t)y * S.W + x;
+        const size_t rb = ((size_t)(i >> L) * T.gv[L] + (j >> L)) * 3 * plane + pix;
+        (void)B;
+        if (!kBackward) {
+            float v[3];
+            for (int c = 0; c < 3; c++) v[c] = root[rb + c * plane];
+            for (int l = 0; l < L; l++) {
+                const int na = i >> l, nb = j >> l;
+                for (int c = 0; c < 3; c++) {
+                    const int nc = nc_index(T, l, na, nb, c);
+                    v[c] += coeff[(size_t)nc * plane + pix];
+                    if (!is_ref(na, nb) && S.mc) {
+                        const uint32_t sym = bise_get_long(S.mvs, S.mv_mode, S.mv_b,
+                                                           (uint64_t)pred_rank(T, l, na, nb, c) * S.nblocks + k);
+                        int mvx, mvy, sign;
+                        decode_mv(S, sym, mvx, mvy, sign);
+                        RelaxTap t;
+                        relax_taps(S, x, y, mvx, mvy, t);
+                        const int rnc = nc_index(T, l, na & ~1, nb & ~1, c);
+                        float p = 0.f;
+                        for (int q = 0; q < 4; q++) p += t.w[q] * coeff[(size_t)rnc * plane + (size_t)t.y[q] * S.W + t.x[q]];
+                        v[c] += (float)sign * p;
+                    }
+                }
+            }
+            const float tt = v[0] - 0.5f * v[2];
+            const float G = v[2] + tt;
+            const float Bc = tt - 0.5f * v[1];
+            acc[0] += w * (Bc + v[1]);
+            acc[1] += w * G;
+            acc[2] += w * Bc;
+        } else {
+            const float gR = w * g[0], gG = w * g[1], gB = w * g[2];
+            const float gv3[3] = {gR + gG + gB, 0.5f * gR - 0.5f * gB, -0.5f * gR + 0.5f * gG - 0.5f * gB};
+            for (int c = 0; c < 3; c++) atomicAdd(groot + rb + c * plane, gv3[c]);
+            for (int l = 0; l < L; l++) {
+                const int na = i >> l, nb = j >> l;
+                for (int c = 0; c < 3; c++) {
+                    const int nc = nc_index(T, l, na, nb, c);
+                    atomicAdd(gcoeff + (size_t)nc * plane + pix, gv3[c]);
+                    if (!is_ref(na, nb) && S.mc) {
+                        const uint32_t sym = bise_get_long(S.mvs, S.mv_mode, S.mv_b,
+                                                           (uint64_t)pred_rank(T, l, na, nb, c) * S.nblocks + k);
+                        int mvx, mvy, sign;
+                        decode_mv(S, sym, mvx, mvy, sign);
+                        RelaxTap t;
+                        relax_taps(S, x, y, mvx, mvy, t);
+                        const int rnc = nc_index(T, l, na & ~1, nb & ~1, c);
+                        for (int q = 0; q < 4; q++)
+                            if (t.w[q] != 0.f)
+                                atomicAdd(gcoeff + (size_t)rnc * plane + (size_t)t.y[q] * S.W + t.x[q],
+                                          (float)sign * t.w[q] * gv3[c]);
+                    }
+                }
+            }
+        }
+    }
+    if (!kBackward) {
+        out[opix] = acc[0] * (1.0f / 255.0f);
+        out[opix + 1] = acc[1] * (1.0f / 255.0f);
+        out[opix + 2] = acc[2] * (1.0f / 255.0f);
+    }
+}
+
+// Dequantised coefficients of every node-channel (float [n_nc][H][W]); the
+// rows after the last node-channel copy the root planes (float
+// [roots][3][H][W]).
+template <int BS>
+__global__ void __launch_bounds__(256) k_dequant(const __grid_constant__ DevStream S, int64_t n_nc,
+                                                float *__restrict__ coeff, float *__restrict__ root) {
+    __shared__ LevelTabs T;
+    __shared__ int s_l, s_a, s_b, s_c;
+    load_tabs(S, T);
+    const int64_t plane = (int64_t)S.W * S.H;
+    const int64_t row = blockIdx.y;
+    if (threadIdx.x == 0 && row < n_nc) {
+        int l = S.L - 1;
+        while (l > 0 && row >= S.nc_base[l - 1]) l--;
+        const int e = (int)(row - S.nc_base[l]);
+        s_l = l;
+        s_c = e % 3;
+        s_a = (e / 3) / S.gv[l];
+        s_b = (e / 3) % S.gv[l];
+    }
+    __syncthreads();
+    const Blk<BS> bk(S.B);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < plane; p += (int64_t)gridDim.x * blockDim.x) {
+        if (row >= n_nc) {
+            const int64_t q = (row - n_nc) * plane + p;
+            root[q] = (float)S.roots[q];
+            continue;
+        }
+        const int x = (int)(p % S.W), y = (int)(p / S.W);
+        const int B = bk.size();
+        const int bx = bk.div(x), by = bk.div(y);
+        int v;
+        if (is_ref(s_a, s_b)) {
+            v = ref_coef(S, bk, (uint32_t)ref_rank(T, s_l, s_a, s_b, s_c) * S.nblocks, x, y);
+        } else {
+            const int bw = min(B, S.W - bx * B);
+            v = residual(S, (int)row, by * S.nbx + bx, (uint32_t)((y - by * B) * bw + (x - bx * B)));
+        }
+        coeff[row * plane + p] = (float)v;
+    }
+}
+
+template <int BS>
+cudaError_t render_dispatch_tw(const DevStream &ds, const LaunchViews &lv, int total_tiles, float *d_out, int mode,
+                               cudaStream_t st) {
+    constexpr int TW = 16, TH = 16;
+    auto kern = k_render<BS, TW, TH>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageSmem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    kern<<<total_tiles, TW * TH, kStageSmem, st>>>(ds, lv, d_out, mode == 1 ? 1 : 0);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+cudaError_t launch_decode_tiles(const DevStream &ds, const uint32_t *d_src, int n_tiles, int16_t *d_tiles,
+                                cudaStream_t st) {
+    if (n_tiles <= 0) return cudaSuccess;
+    k_decode_tiles<<<n_tiles, 256, 0, st>>>(ds, reinterpret_cast<const uint4 *>(d_src), n_tiles, d_tiles);
+    return cudaGetLastError();
+}
+
+#define HMLFC_DISPATCH_B(B, CALL) \
+    switch (B) {                  \
+        case 4: { constexpr int BS = 4; CALL; } break;   \
+        case 8: { constexpr int BS = 8; CALL; } break;   \
+        case 16: { constexpr int BS = 16; CALL; } break; \
+        case 32: { constexpr int BS = 32; CALL; } break; \
+        default: { constexpr int BS = 0; CALL; } break;  \
+    }
+
+cudaError_t launch_decode_pixels(const DevStream &ds, const int32_t *d_coords, int64_t n, uint8_t *d_rgb,
+                                 cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t want = (n + 255) / 256;
+    const int grid = (int)(want < 152 * 64 ? want : 152 * 64);
+    HMLFC_DISPATCH_B(ds.B, (k_decode_pixels<BS><<<grid, 256, 0, st>>>(ds, reinterpret_cast<const int4 *>(d_coords), n,
+                                                                       d_rgb)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render(const DevStream &ds, const LaunchViews &lv, int total_tiles, float *d_out, int mode,
+                          cudaStream_t st) {
+    if (total_tiles <= 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    HMLFC_DISPATCH_B(ds.B, (e = render_dispatch_tw<BS>(ds, lv, total_tiles, d_out, mode, st)));
+    return e;
+}
+
+cudaError_t launch_render_relaxed(const DevStream &ds, const LaunchViews &lv, int total_tiles, const float *coeff,
+                                  const float *root, float *d_out, cudaStream_t st) {
+    if (total_tiles <= 0) return cudaSuccess;
+    HMLFC_DISPATCH_B(ds.B, (k_relax<BS, false><<<total_tiles, 256, 0, st>>>(ds, lv, coeff, root, d_out, nullptr,
+                                                                            nullptr, nullptr)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render_backward(const DevStream &ds, const LaunchViews &lv, int total_tiles,
+                                   const float *grad_out, float *grad_coeff, float *grad_root, cudaStream_t st) {
+    if (total_tiles <= 0) return cudaSuccess;
+    HMLFC_DISPATCH_B(ds.B, (k_relax<BS, true><<<total_tiles, 256, 0, st>>>(ds, lv, nullptr, nullptr, nullptr,
+                                                                           grad_out, grad_coeff, grad_root)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dequant(const DevStream &ds, int64_t n_nc, float *coeff, float *root, cudaStream_t st) {
+    const int64_t plane = (int64_t)ds.W * ds.H;
+    const int64_t n_roots = (int64_t)ds.gu[ds.L] * ds.gv[ds.L];
+    const int64_t gx = (plane + 255) / 256;
+    dim3 grid((unsigned)(gx < 4096 ? gx : 4096), (unsigned)(n_nc + n_roots * 3));
+    HMLFC_DISPATCH_B(ds.B, (k_dequant<BS><<<grid, 256, 0, st>>>(ds, n_nc, coeff, root)));
+    return cudaGetLastError();
+}
+
+}  // namespace hmlfc

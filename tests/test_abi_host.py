@@ -1,0 +1,104 @@
+"""Host-side tests of the product library (no GPU needed): the shared object
+builds and exports every entry point of include/hmlfc.h; its encoder writes
+the same bytes as the oracle's; the loader rejects corrupt streams before
+touching a device; the touched-bytes counter agrees with the oracle's."""
+import ctypes as C
+import re
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1902_09396_gb300 as H
+import synthlf as S
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+def test_library_exports_every_declared_symbol():
+    header = (ROOT / "include" / "hmlfc.h").read_text()
+    names = sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*(hmlfc_\w+)\s*\(", header, re.M)))
+    assert len(names) >= 15
+    lib = C.CDLL(str(H.build()))
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+@pytest.mark.parametrize("mc", [O.MC_OFF, O.MC_QPEL, O.MC_ZERO, O.MC_INTEGER])
+def test_encoder_matches_oracle_bytes(tiny_lf, tiny_cfg, ragged_lf, mc):
+    """The product encoder follows the same readings (tie-breaks, quantiser,
+    thresholds, layout) and writes byte-identical streams."""
+    c = tiny_cfg
+    for lf, L, B, q, tr, tp in [(tiny_lf, c.levels, c.block, 1, 0, 0), (tiny_lf, c.levels, c.block, 4, 0, 0),
+                                (ragged_lf, 2, 8, 4, 40, 90), (ragged_lf, 3, 16, 2, 0, 0)]:
+        a = O.encode(lf, L, B, c.search, q, t_ref=tr, t_pred=tp, mc=mc).stream
+        b = H.encode(lf, L, B, c.search, q, t_ref=tr, t_pred=tp, mc=mc, threads=3)
+        assert a == b
+
+
+def test_encoder_thread_count_does_not_change_output(ragged_lf):
+    a = H.encode(ragged_lf, 2, 8, 4, 4, threads=1)
+    b = H.encode(ragged_lf, 2, 8, 4, 4, threads=7)
+    assert a == b
+
+
+def _load_error(data: bytes) -> int:
+    h = C.c_void_p()
+    return H.lib().hmlfc_load_stream(data, len(data), 0, None, C.byref(h))
+
+
+def test_loader_rejects_corrupt_streams(tiny_streams, tiny_cfg):
+    """Truncated or bit-flipped streams fail with HMLFC_E_CORRUPT (or
+    UNSUPPORTED) during host validation, before any device work."""
+    good = tiny_streams[tiny_cfg.qstep].stream
+    bad_cases = {
+        "truncated": good[:-16],
+        "short": good[:64],
+        "magic": b"XXXX" + good[4:],
+        "total": good[:104] + (len(good) + 16).to_bytes(4, "little") + good[108:],
+    }
+    b = bytearray(good)
+    # first group entry: a record base far past the end
+    off_groups = int.from_bytes(good[88:92], "little")
+    b[off_groups + 4:off_groups + 8] = (0x7FFFFFF0).to_bytes(4, "little")
+    bad_cases["record_base"] = bytes(b)
+    b = bytearray(good)
+    b[off_groups + 8:off_groups + 12] = (5).to_bytes(4, "little")
+    bad_cases["offset_base"] = bytes(b)
+    b = bytearray(good)
+    assert b[off_groups:off_groups + 4] != b"\x00\x00\x00\x00"
+    b[off_groups:off_groups + 4] = b"\x00\x00\x00\x00"      # drops blocks: offsets no longer line up
+    bad_cases["bitmap"] = bytes(b)
+    b = bytearray(good)
+    off_recs = int.from_bytes(good[96:100], "little")
+    b[off_recs + 2:off_recs + 4] = (0x7F | 0x60).to_bytes(2, "little")   # mode 3 / b > 16
+    bad_cases["record_header"] = bytes(b)
+    for name, data in bad_cases.items():
+        rc = _load_error(data)
+        assert rc in (H.E_CORRUPT, H.E_UNSUPPORTED), (name, rc)
+        assert H.lib().hmlfc_last_error()
+
+
+def test_null_and_invalid_arguments():
+    L = H.lib()
+    h = C.c_void_p()
+    assert L.hmlfc_load_stream(None, 0, 0, None, C.byref(h)) == H.E_CORRUPT
+    assert L.hmlfc_decode_pixels(None, None, 0, None, None) == H.E_INVALID_ARG
+    assert L.hmlfc_render_views(None, 0, None, 0, None, None) == H.E_INVALID_ARG
+    L.hmlfc_free_stream(None)
+
+
+@pytest.mark.gpu
+def test_touched_bytes_matches_oracle(tiny_streams, tiny_cfg):
+    """The product's counter (the roofline numerator of the benchmark)
+    reproduces the oracle's definition exactly on the same views (a stream
+    object lives on a device, hence the GPU mark)."""
+    c = tiny_cfg
+    data = tiny_streams[c.qstep].stream
+    geo = S.lf_geometry(c.nu, c.nv, c.width, c.height)
+    views = S.views_to_array(S.random_views(21, geo, 4, [(64, 64), (40, 24)]) +
+                             [S.grid_view(1.0, 2.0, 0.0, 0.0, 64, 64)])
+    want = O.Stream(data).touched_bytes(views)
+    got = H.touched_bytes([H.Stream(data)], views)
+    assert np.allclose(got, want, rtol=0, atol=1e-6)

@@ -1,0 +1,237 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Decoded samples must be bit-exact; rendered FP32 views within max-abs 1e-3
+(on the [0, 1] scale) of the oracle's FP64 render.  The FP32 render differs
+from FP64 only by rounding of the ray setup and the 16-term blend (about
+1e-6 here), so 1e-3 is the stated bound, not a loose fit.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synthlf as S
+
+pytestmark = pytest.mark.gpu
+
+RENDER_TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def H(torch_cuda):
+    import paper_1902_09396_gb300 as H
+    H.lib()
+    return H
+
+
+def _all_coords(nu, nv, W, H_):
+    ii, jj, xx, yy = np.meshgrid(np.arange(nu), np.arange(nv), np.arange(W), np.arange(H_), indexing="ij")
+    return np.stack([ii, jj, xx, yy], -1).reshape(-1, 4).astype(np.int32)
+
+
+def _decode_gpu(torch, st, coords):
+    c = torch.from_numpy(np.ascontiguousarray(coords, np.int32)).cuda()
+    out = st.decode_pixels(c)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("q", [1, 4])
+def test_decode_all_samples_bit_exact_tiny(H, torch_cuda, tiny_streams, q):
+    enc = tiny_streams[q]
+    ost = O.Stream(enc.stream)
+    full = ost.decode_all()
+    st = H.Stream(enc.stream)
+    coords = _all_coords(ost.nu, ost.nv, ost.W, ost.H)
+    got = _decode_gpu(torch_cuda, st, coords)
+    want = full[coords[:, 0], coords[:, 1], coords[:, 3], coords[:, 2]]
+    assert np.array_equal(got, want)
+    st.check_status()
+
+
+@pytest.mark.parametrize("mc", [O.MC_OFF, O.MC_QPEL, O.MC_ZERO, O.MC_INTEGER])
+@pytest.mark.parametrize("shape", [(2, 8), (3, 16), (2, 5)])
+def test_decode_ragged_bit_exact(H, torch_cuda, ragged_lf, mc, shape):
+    """Odd grids, partial edge blocks, a non power-of-two block size, every
+    MC mode, thresholds on."""
+    L, B = shape
+    data = O.encode(ragged_lf, L, B, 3, 4, t_ref=30, t_pred=60, mc=mc).stream
+    ost = O.Stream(data)
+    st = H.Stream(data)
+    coords = _all_coords(ost.nu, ost.nv, ost.W, ost.H)
+    assert np.array_equal(_decode_gpu(torch_cuda, st, coords), ost.decode_samples(coords))
+
+
+def test_decode_out_of_range_sets_status(H, torch_cuda, tiny_streams):
+    st = H.Stream(tiny_streams[4].stream)
+    coords = np.array([[0, 0, 0, 0], [4, 0, 0, 0], [0, 0, 64, 0], [-1, 2, 3, 4], [3, 3, 63, 63]], np.int32)
+    got = _decode_gpu(torch_cuda, st, coords)
+    assert np.array_equal(got[1:4], np.zeros((3, 3), np.uint8))
+    with pytest.raises(H.HmlfcError) as ei:
+        st.check_status()
+    assert ei.value.code == H.E_INVALID_ARG
+    st.check_status()          # cleared by the first check
+    want = O.Stream(tiny_streams[4].stream).decode_samples(coords[[0, 4]])
+    assert np.array_equal(got[[0, 4]], want)
+
+
+def test_decode_empty_and_odd_counts(H, torch_cuda, tiny_streams):
+    st = H.Stream(tiny_streams[4].stream)
+    ost = O.Stream(tiny_streams[4].stream)
+    torch = torch_cuda
+    empty = torch.zeros((0, 4), dtype=torch.int32, device="cuda")
+    assert st.decode_pixels(empty).shape == (0, 3)
+    rng = np.random.default_rng(5)
+    for n in (1, 255, 257, 70001):
+        coords = np.stack([rng.integers(0, 4, n), rng.integers(0, 4, n), rng.integers(0, 64, n),
+                           rng.integers(0, 64, n)], -1).astype(np.int32)
+        assert np.array_equal(_decode_gpu(torch, st, coords), ost.decode_samples(coords))
+
+
+def _render_gpu(H, torch, streams, views):
+    out = H.render_views(streams, views)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64)
+
+
+def _views_mix(cfg, seed, n, sizes):
+    geo = S.lf_geometry(cfg.nu, cfg.nv, cfg.width, cfg.height)
+    return S.random_views(seed, geo, n, sizes)
+
+
+@pytest.mark.parametrize("path", [0, 1])
+def test_render_tiny_within_tolerance(H, torch_cuda, tiny_streams, tiny_cfg, path):
+    """The configured novel view (camera on the (u,v) plane at a random
+    (u0, v0), (s,t) offset) plus random pinhole views of ragged sizes; both
+    render paths."""
+    c = tiny_cfg
+    enc = tiny_streams[c.qstep]
+    ost = O.Stream(enc.stream)
+    dec = ost.decode_all()
+    rng = np.random.default_rng(c.seed)
+    views = [S.grid_view(rng.random() * 3, rng.random() * 3, rng.random() * 4 - 2, rng.random() * 4 - 2, 64, 64)]
+    views += _views_mix(c, 31, 6, [(64, 64), (37, 23), (1, 1), (16, 17), (100, 3)])
+    arr = S.views_to_array(views)
+    want = O.render_dense(dec, arr)
+    H.set_render_path(path)
+    try:
+        got = _render_gpu(H, torch_cuda, [H.Stream(enc.stream)], arr)
+    finally:
+        H.set_render_path(0)
+    assert np.max(np.abs(got - want)) <= RENDER_TOL
+
+
+def test_render_paths_identical(H, torch_cuda, tiny_streams, tiny_cfg):
+    """The staged and the direct path decode the same integers and blend in
+    the same order: bitwise equal outputs."""
+    c = tiny_cfg
+    st = H.Stream(tiny_streams[c.qstep].stream)
+    arr = S.views_to_array(_views_mix(c, 32, 8, [(64, 64), (48, 40)]))
+    a = _render_gpu(H, torch_cuda, [st], arr)
+    H.set_render_path(1)
+    try:
+        b = _render_gpu(H, torch_cuda, [st], arr)
+    finally:
+        H.set_render_path(0)
+    assert np.array_equal(a, b)
+
+
+def test_render_grid_samples_exact(H, torch_cuda, tiny_streams, tiny_cfg):
+    """At a camera position with (s,t) on pixel centres the render is the
+    decoded view / 255."""
+    c = tiny_cfg
+    enc = tiny_streams[c.qstep]
+    dec = O.Stream(enc.stream).decode_all()
+    st = H.Stream(enc.stream)
+    for i, j in [(0, 0), (1, 3), (3, 2)]:
+        arr = S.views_to_array([S.grid_view(float(i), float(j), 0.0, 0.0, 64, 64)])
+        got = _render_gpu(H, torch_cuda, [st], arr).reshape(64, 64, 3)
+        assert np.max(np.abs(got - dec[i, j] / 255.0)) <= 1e-6
+
+
+def test_render_clamped_and_degenerate_views(H, torch_cuda, tiny_streams, tiny_cfg):
+    """Rays far outside the grid and image clamp to the edges; a zero-size
+    view writes nothing."""
+    c = tiny_cfg
+    enc = tiny_streams[c.qstep]
+    dec = O.Stream(enc.stream).decode_all()
+    views = [S.grid_view(-5.0, 9.0, -80.0, 200.0, 20, 20), S.grid_view(1.5, 1.5, 0.0, 0.0, 0, 0),
+             S.grid_view(3.9, -0.2, 60.5, -3.25, 33, 9)]
+    arr = S.views_to_array(views)
+    want = O.render_dense(dec, arr)
+    got = _render_gpu(H, torch_cuda, [H.Stream(enc.stream)], arr)
+    assert np.max(np.abs(got - want)) <= RENDER_TOL
+
+
+def test_render_multiple_streams(H, torch_cuda, tiny_streams, tiny_cfg, ragged_lf):
+    """Views of different light fields in one call."""
+    c = tiny_cfg
+    d1 = tiny_streams[c.qstep].stream
+    d2 = O.encode(ragged_lf, 2, 8, 4, 2).stream
+    s1, s2 = H.Stream(d1), H.Stream(d2)
+    geo2 = S.lf_geometry(5, 3, 37, 29)
+    v1 = _views_mix(c, 33, 3, [(40, 40)])
+    v2 = S.random_views(34, geo2, 3, [(30, 20)], lf=1)
+    arr = S.views_to_array([v1[0], v2[0], v1[1], v2[1], v2[2], v1[2]])
+    got = _render_gpu(H, torch_cuda, [s1, s2], arr)
+    want1 = O.render_dense(O.Stream(d1).decode_all(), arr[arr["lf"] == 0])
+    want2 = O.render_dense(O.Stream(d2).decode_all(), arr[arr["lf"] == 1])
+    for k in range(len(arr)):
+        o = int(arr[k]["out_offset"])
+        n = int(arr[k]["width"]) * int(arr[k]["height"]) * 3
+        ref = want1 if arr[k]["lf"] == 0 else want2
+        assert np.max(np.abs(got[o:o + n] - ref[o:o + n])) <= RENDER_TOL
+
+
+def test_dequant_matches_oracle(H, torch_cuda, tiny_streams, ragged_lf):
+    for data in (tiny_streams[4].stream, O.encode(ragged_lf, 3, 8, 4, 2).stream):
+        co, ro = H.Stream(data).dequant()
+        oc, orr = O.Stream(data).dequant()
+        assert np.array_equal(co.cpu().numpy().astype(np.float64), oc)
+        assert np.array_equal(ro.cpu().numpy().astype(np.float64), orr)
+
+
+def test_relaxed_forward_and_adjoint(H, torch_cuda, tiny_streams, tiny_cfg):
+    """FP32 relaxed render vs the FP64 oracle, and the adjoint (FP32 atomics)
+    vs the oracle's transpose, relative to the gradient scale."""
+    torch = torch_cuda
+    c = tiny_cfg
+    data = tiny_streams[c.qstep].stream
+    ost = O.Stream(data)
+    st = H.Stream(data)
+    arr = S.views_to_array(_views_mix(c, 35, 3, [(32, 32), (21, 19)]))
+    rng = np.random.default_rng(36)
+    co = rng.standard_normal((ost.n_nc, ost.H, ost.W))
+    ro = rng.standard_normal((ost.n_roots, 3, ost.H, ost.W))
+    want = ost.relax_render(co, ro, arr)
+    got = H.render_views_relaxed([st], [torch.tensor(co, dtype=torch.float32, device="cuda")],
+                                 [torch.tensor(ro, dtype=torch.float32, device="cuda")], arr)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(got.cpu().numpy() - want)) <= 1e-5 * max(1.0, np.max(np.abs(want)))
+    g = rng.standard_normal(want.shape)
+    wc, wr = ost.relax_adjoint(arr, g)
+    gc = torch.zeros((ost.n_nc, ost.H, ost.W), dtype=torch.float32, device="cuda")
+    gr = torch.zeros((ost.n_roots, 3, ost.H, ost.W), dtype=torch.float32, device="cuda")
+    H.render_backward([st], arr, torch.tensor(g, dtype=torch.float32, device="cuda"), [gc], [gr])
+    torch.cuda.synchronize()
+    scale = max(np.max(np.abs(wc)), np.max(np.abs(wr)))
+    assert np.max(np.abs(gc.cpu().numpy() - wc)) <= 1e-5 * scale
+    assert np.max(np.abs(gr.cpu().numpy() - wr)) <= 1e-5 * scale
+
+
+def test_requantize_round_trip(H, torch_cuda, tiny_streams, tiny_cfg):
+    """Re-encoding a stream's own dequantised coefficients reproduces a
+    stream that decodes to the same samples."""
+    data = tiny_streams[tiny_cfg.qstep].stream
+    st = H.Stream(data)
+    co, ro = st.dequant()
+    new = H.requantize(st, co.cpu().numpy(), ro.cpu().numpy())
+    a, b = O.Stream(data).decode_all(), O.Stream(new).decode_all()
+    assert np.array_equal(a, b)
