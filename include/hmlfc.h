@@ -237,13 +237,26 @@ void hmlfc_free_host(void *p);
 int hmlfc_touched_bytes(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views, int n_views,
                         double *h_bytes);
 
+/* The same count over the whole call: every distinct item once, however
+ * many views reach it, plus every view's output (one total into h_total). */
+int hmlfc_touched_bytes_union(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views,
+                              int n_views, double *h_total);
+
 /*
- * Diagnostic switch of the render kernels (process-wide): 0 (default) stages
- * each tile's footprint in shared memory where it fits and decodes per ray
- * otherwise; 1 decodes every ray's samples directly.  Both give identical
- * results; the switch exists to test and time the two paths.
+ * Render strategy (process-wide).  0 (default): decode every (camera, block)
+ * pair the call's views reach once, into a decoded-block cache held in
+ * stream-ordered scratch memory (cudaMallocAsync on the call's stream, freed
+ * on it when the call's work ends), then blend each ray from the cache;
+ * blocks beyond the cache capacity, or all of them if the scratch cannot be
+ * allocated, are decoded per tile instead.  1: every ray decodes its own 16
+ * samples.  2: each 16 x 16 tile stages its footprint in shared memory.
+ * All give bit-identical output.
  */
 int hmlfc_set_render_path(int path);
+
+/* Capacity of the decoded-block cache of one render call, in bytes
+ * (default 256 MiB; B * B * 4 bytes per block; 0 disables the cache). */
+int hmlfc_set_block_cache_bytes(size_t bytes);
 
 const char *hmlfc_last_error(void);
 

@@ -19,7 +19,7 @@ from .build import LIB, build  # noqa: F401
 
 # Identifies the render kernel's code; profile figures recorded for another
 # version are not reused.
-KERNEL_VERSION = "render-staged-v1"
+KERNEL_VERSION = "render-cached-v1"
 
 OK, E_INVALID_ARG, E_CORRUPT, E_OOM, E_CUDA, E_TIMEOUT, E_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 MC_OFF, MC_QPEL, MC_ZERO, MC_INTEGER = 0, 1, 2, 3
@@ -81,7 +81,9 @@ def lib() -> C.CDLL:
     L.hmlfc_free_host.argtypes = [P]
     L.hmlfc_free_host.restype = None
     L.hmlfc_touched_bytes.argtypes = [P, I, P, I, P]
+    L.hmlfc_touched_bytes_union.argtypes = [P, I, P, I, P]
     L.hmlfc_set_render_path.argtypes = [I]
+    L.hmlfc_set_block_cache_bytes.argtypes = [SZ]
     _lib = L
     return L
 
@@ -215,8 +217,16 @@ def render_backward(streams, views, grad_out, grad_coeffs, grad_roots, cuda_stre
                                        _stream_handle(cuda_stream)))
 
 
+RENDER_CACHED, RENDER_DIRECT, RENDER_TILE = 0, 1, 2
+
+
 def set_render_path(path: int):
+    """0: decoded-block cache per call (default); 1: per-ray decode; 2: per-tile staging."""
     _check(lib().hmlfc_set_render_path(int(path)))
+
+
+def set_block_cache_bytes(n: int):
+    _check(lib().hmlfc_set_block_cache_bytes(int(n)))
 
 
 def encode(lf: np.ndarray, levels: int, block: int, search: int, qstep: int, t_ref: int = 0, t_pred: int = 0,
@@ -243,6 +253,14 @@ def requantize(stream: Stream, coeff: np.ndarray, root: np.ndarray) -> bytes:
     data = C.string_at(out, n.value)
     lib().hmlfc_free_host(out)
     return data
+
+
+def touched_bytes_union(streams, views) -> float:
+    """Compulsory bytes of a whole call: distinct items counted once."""
+    va = _views_array(views)
+    out = C.c_double()
+    _check(lib().hmlfc_touched_bytes_union(_streams_array(streams), len(streams), va, len(va), C.byref(out)))
+    return out.value
 
 
 def touched_bytes(streams, views) -> np.ndarray:

@@ -19,7 +19,8 @@ using namespace hmlfc;
 namespace {
 
 thread_local std::string g_err;
-int g_render_path = 0;  // 0 = staged where the footprint fits, 1 = direct only
+int g_render_path = 0;                      // 0 cached blocks, 1 direct per ray, 2 per-tile staging
+size_t g_cache_bytes = (size_t)256 << 20;   // decoded-block cache of one render call
 
 }  // namespace
 
@@ -222,36 +223,97 @@ int check_views(const hmlfc_stream *const *streams, int n_streams, const hmlfc_v
     return HMLFC_OK;
 }
 
-// Launch one kernel family over the views of each stream, in chunks that fit
-// the by-value view table.
+// The views of stream `lf`, in launch chunks that fit the by-value view table.
+int view_chunks(const hmlfc_view *views, int n_views, int lf, std::vector<LaunchViews> &chunks,
+                std::vector<int> &tiles) {
+    chunks.clear();
+    tiles.clear();
+    std::vector<int> idx;
+    for (int v = 0; v < n_views; v++)
+        if (views[v].lf == lf && views[v].width > 0 && views[v].height > 0) idx.push_back(v);
+    for (size_t s = 0; s < idx.size(); s += kMaxViewsPerLaunch) {
+        chunks.emplace_back();
+        LaunchViews &lv = chunks.back();
+        std::memset(&lv, 0, sizeof lv);
+        lv.tile_w = 16;
+        lv.tile_h = 16;
+        const size_t e = std::min(idx.size(), s + kMaxViewsPerLaunch);
+        int64_t t = 0;
+        for (size_t k = s; k < e; k++) {
+            const hmlfc_view &V = views[idx[k]];
+            lv.tile_start[k - s] = (int)t;
+            lv.views[k - s] = V;
+            t += (int64_t)((V.width + 15) / 16) * ((V.height + 15) / 16);
+        }
+        lv.n_views = (int)(e - s);
+        lv.tile_start[lv.n_views] = (int)t;
+        if (t >= INT32_MAX) return fail(HMLFC_E_INVALID_ARG, "too many tiles in one launch");
+        tiles.push_back((int)t);
+    }
+    return HMLFC_OK;
+}
+
+// Launch one kernel family over the views of each stream, chunk by chunk.
 template <class F>
 int for_view_chunks(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *views, int n_views, F launch) {
-    std::vector<int> idx;
+    std::vector<LaunchViews> chunks;
+    std::vector<int> tiles;
     for (int lf = 0; lf < n_streams; lf++) {
-        idx.clear();
-        for (int v = 0; v < n_views; v++)
-            if (views[v].lf == lf && views[v].width > 0 && views[v].height > 0) idx.push_back(v);
-        for (size_t s = 0; s < idx.size(); s += kMaxViewsPerLaunch) {
-            LaunchViews lv;
-            std::memset(&lv, 0, sizeof lv);
-            lv.tile_w = 16;
-            lv.tile_h = 16;
-            const size_t e = std::min(idx.size(), s + kMaxViewsPerLaunch);
-            int64_t tiles = 0;
-            for (size_t t = s; t < e; t++) {
-                const hmlfc_view &V = views[idx[t]];
-                lv.tile_start[t - s] = (int)tiles;
-                lv.views[t - s] = V;
-                tiles += (int64_t)((V.width + 15) / 16) * ((V.height + 15) / 16);
-            }
-            lv.n_views = (int)(e - s);
-            lv.tile_start[lv.n_views] = (int)tiles;
-            if (tiles >= INT32_MAX) return fail(HMLFC_E_INVALID_ARG, "too many tiles in one launch");
-            const int rc = launch(streams[lf], lv, (int)tiles);
+        int rc = view_chunks(views, n_views, lf, chunks, tiles);
+        if (rc != HMLFC_OK) return rc;
+        for (size_t c = 0; c < chunks.size(); c++) {
+            rc = launch(streams[lf], chunks[c], tiles[c]);
             if (rc != HMLFC_OK) return rc;
         }
     }
     return HMLFC_OK;
+}
+
+int sm_count(int device) {
+    static int cached[64] = {0};
+    if (device >= 0 && device < 64 && cached[device]) return cached[device];
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n <= 0) n = 1;
+    if (device >= 0 && device < 64) cached[device] = n;
+    return n;
+}
+
+// Cached render of the views of one stream: mark the (camera, block) pairs
+// the tiles reach, give each a slot of a stream-ordered scratch cache, decode
+// those blocks once, then blend every ray from the cache.  Returns 1 (and
+// launches nothing) when the scratch cannot be had, so the caller falls back.
+int render_cached(const hmlfc_stream *s, const std::vector<LaunchViews> &chunks, const std::vector<int> &tiles,
+                  float *d_out, cudaStream_t st) {
+    const Geometry &g = s->g;
+    const int64_t n_keys = (int64_t)g.nu * g.nv * g.nblocks;
+    const size_t blk_bytes = (size_t)g.B * g.B * 4;
+    const uint32_t capacity = (uint32_t)std::min<int64_t>(n_keys, (int64_t)(g_cache_bytes / blk_bytes));
+    if (capacity == 0) return 1;
+    const int64_t n_ck = (int64_t)g.gu[1] * g.gv[1] * g.nblocks;
+    const size_t o_flags = 0, o_slot = up256(o_flags + (size_t)n_keys), o_items = up256(o_slot + (size_t)n_keys * 4),
+                 o_count = up256(o_items + (size_t)n_ck * 16), o_cache = up256(o_count + 8),
+                 total = up256(o_cache + (size_t)capacity * blk_bytes);
+    void *base = nullptr;
+    if (cudaMallocAsync(&base, total, st) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    uint8_t *b = static_cast<uint8_t *>(base);
+    uint8_t *flags = b + o_flags;
+    uint32_t *slotmap = reinterpret_cast<uint32_t *>(b + o_slot);
+    uint4 *items = reinterpret_cast<uint4 *>(b + o_items);
+    unsigned long long *counters = reinterpret_cast<unsigned long long *>(b + o_count);
+    uint32_t *cache = reinterpret_cast<uint32_t *>(b + o_cache);
+    cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)n_keys, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 8, st);
+    for (size_t c = 0; c < chunks.size() && e == cudaSuccess; c++) e = launch_mark(s->ds, chunks[c], tiles[c], flags, st);
+    if (e == cudaSuccess) e = launch_assign(s->ds, flags, slotmap, items, counters, capacity, st);
+    if (e == cudaSuccess) e = launch_decode_blocks(s->ds, items, counters, cache, sm_count(s->device) * 8, st);
+    for (size_t c = 0; c < chunks.size() && e == cudaSuccess; c++)
+        e = launch_render_cached(s->ds, chunks[c], tiles[c], slotmap, cache, d_out, st);
+    const cudaError_t ef = cudaFreeAsync(base, st);
+    if (e == cudaSuccess) e = ef;
+    return e == cudaSuccess ? HMLFC_OK : cuda_fail(e, "cached render");
 }
 
 }  // namespace
@@ -261,8 +323,13 @@ extern "C" {
 const char *hmlfc_last_error(void) { return g_err.c_str(); }
 
 int hmlfc_set_render_path(int path) {
-    if (path < 0 || path > 1) return fail(HMLFC_E_INVALID_ARG, "render path %d", path);
+    if (path < 0 || path > 2) return fail(HMLFC_E_INVALID_ARG, "render path %d", path);
     g_render_path = path;
+    return HMLFC_OK;
+}
+
+int hmlfc_set_block_cache_bytes(size_t bytes) {
+    g_cache_bytes = bytes;
     return HMLFC_OK;
 }
 
@@ -410,11 +477,25 @@ int hmlfc_render_views(const hmlfc_stream *const *streams, int n_streams, const 
     if (n_views == 0) return HMLFC_OK;
     DeviceGuard guard(streams[0]->device);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    return for_view_chunks(streams, n_streams, h_views, n_views,
-                           [&](const hmlfc_stream *s, const LaunchViews &lv, int tiles) {
-                               const cudaError_t e = launch_render(s->ds, lv, tiles, d_out, g_render_path, st);
-                               return e == cudaSuccess ? HMLFC_OK : cuda_fail(e, "render launch");
-                           });
+    std::vector<LaunchViews> chunks;
+    std::vector<int> tiles;
+    for (int lf = 0; lf < n_streams; lf++) {
+        rc = view_chunks(h_views, n_views, lf, chunks, tiles);
+        if (rc != HMLFC_OK) return rc;
+        if (chunks.empty()) continue;
+        int path = g_render_path;
+        if (path == 0) {
+            rc = render_cached(streams[lf], chunks, tiles, d_out, st);
+            if (rc == HMLFC_OK) continue;
+            if (rc != 1) return rc;
+            path = 2;   // no scratch: per-tile staging needs none
+        }
+        for (size_t c = 0; c < chunks.size(); c++) {
+            const cudaError_t e = launch_render(streams[lf]->ds, chunks[c], tiles[c], d_out, path == 1 ? 1 : 0, st);
+            if (e != cudaSuccess) return cuda_fail(e, "render launch");
+        }
+    }
+    return HMLFC_OK;
 }
 
 int hmlfc_render_views_relaxed(const hmlfc_stream *const *streams, int n_streams, const float *const *d_coeff,

@@ -56,6 +56,13 @@ cudaError_t launch_decode_pixels(const DevStream &ds, const int32_t *d_coords, i
                                  cudaStream_t st);
 cudaError_t launch_render(const DevStream &ds, const LaunchViews &lv, int total_tiles, float *d_out, int mode,
                           cudaStream_t st);
+cudaError_t launch_mark(const DevStream &ds, const LaunchViews &lv, int total_tiles, uint8_t *flags, cudaStream_t st);
+cudaError_t launch_assign(const DevStream &ds, const uint8_t *flags, uint32_t *slotmap, uint4 *items,
+                          unsigned long long *counters, uint32_t capacity, cudaStream_t st);
+cudaError_t launch_decode_blocks(const DevStream &ds, const uint4 *items, const unsigned long long *counters,
+                                 uint32_t *cache, int grid, cudaStream_t st);
+cudaError_t launch_render_cached(const DevStream &ds, const LaunchViews &lv, int total_tiles, const uint32_t *slotmap,
+                                 const uint32_t *cache, float *d_out, cudaStream_t st);
 cudaError_t launch_render_relaxed(const DevStream &ds, const LaunchViews &lv, int total_tiles, const float *coeff,
                                   const float *root, float *d_out, cudaStream_t st);
 cudaError_t launch_render_backward(const DevStream &ds, const LaunchViews &lv, int total_tiles,

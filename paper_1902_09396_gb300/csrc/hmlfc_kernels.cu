@@ -48,19 +48,20 @@ __device__ __forceinline__ uint32_t quint_digit(uint32_t packed, uint32_t r) {
 }
 
 // Value i of a BISE sequence starting at word w (i < 2^16: block payloads).
+// Branch-free over the three alphabets so that the lanes of a warp whose
+// pixels fall in blocks of different modes do not diverge: mode 0 is the
+// case "one value per group, no packed field".
 __device__ __forceinline__ uint32_t bise_get_small(const uint32_t *__restrict__ w, uint32_t mode, uint32_t b,
                                                    uint32_t i) {
-    if (mode == 0) return bits_at(w, i * b, b);
-    if (mode == 1) {
-        const uint32_t g = i / 5u, r = i - 5u * g;
-        const uint32_t pos = g * (8u + 5u * b);
-        const uint32_t hi = trit_digit(bits_at(w, pos, 8), r);
-        return (hi << b) | bits_at(w, pos + 8u + r * b, b);
-    }
-    const uint32_t g = i / 3u, r = i - 3u * g;
-    const uint32_t pos = g * (7u + 3u * b);
-    const uint32_t hi = quint_digit(bits_at(w, pos, 7), r);
-    return (hi << b) | bits_at(w, pos + 7u + r * b, b);
+    // groups: mode 0 -> 1 value, mode 1 -> 5, mode 2 -> 3; packed field 0 / 8 / 7 bits
+    const uint32_t g = mode == 1 ? (i * 52429u) >> 18 : (mode == 2 ? (i * 43691u) >> 17 : i);   // i / per
+    const uint32_t per = mode == 1 ? 5u : (mode == 2 ? 3u : 1u);
+    const uint32_t hw = mode == 1 ? 8u : (mode == 2 ? 7u : 0u);
+    const uint32_t r = i - g * per;
+    const uint32_t pos = g * (hw + per * b);
+    const uint32_t packed = bits_at(w, pos, hw);
+    const uint32_t hi = mode == 1 ? trit_digit(packed, r) : quint_digit(packed, r);   // 0 when hw == 0
+    return (hi << b) | bits_at(w, pos + hw + r * b, b);
 }
 
 // Value i of a long BISE sequence (the motion-vector symbols).
@@ -313,7 +314,8 @@ __device__ __forceinline__ void ray_setup(const hmlfc_view &V, int nu, int nv, i
     r.ft = axis_nb(t, H, r.y0, r.y1);
 }
 
-// Quadrilinear blend of the 16 samples, in a fixed order (a, b, xs, ys).
+// Quadrilinear blend of the 16 samples, in a fixed order (a, b, xs, ys);
+// fetch(a, b, xs, ys, i, j, x, y) returns the packed RGB8 sample.
 template <class F>
 __device__ __forceinline__ void blend16(const Ray &r, F fetch, float out[3]) {
     const float wu[2] = {1.0f - r.fu, r.fu}, wv[2] = {1.0f - r.fv, r.fv};
@@ -329,7 +331,7 @@ __device__ __forceinline__ void blend16(const Ray &r, F fetch, float out[3]) {
 #pragma unroll
                 for (int ys = 0; ys < 2; ys++) {
                     const float w = wu[a] * wv[b] * ws[xs] * wt[ys];
-                    const uint32_t p = fetch(ii[a], jj[b], xx[xs], yy[ys]);
+                    const uint32_t p = fetch(a, b, xs, ys, ii[a], jj[b], xx[xs], yy[ys]);
                     acc0 += w * (float)(p & 0xFFu);
                     acc1 += w * (float)((p >> 8) & 0xFFu);
                     acc2 += w * (float)((p >> 16) & 0xFFu);
@@ -355,42 +357,108 @@ __device__ __forceinline__ int find_view(const LaunchViews &LV, int tile) {
 
 constexpr int kMaxCam = 9;          // cameras of a staged footprint (3 x 3)
 constexpr int kMaxPx = 400;         // pixels of a staged footprint
-constexpr int kMaxDesc = 512;       // block descriptors of a staged footprint
-constexpr int kMaxN1 = 4;           // level-1 nodes of a staged footprint
+constexpr int kMaxDesc = 384;       // block descriptors of a staged footprint
+constexpr int kMaxNodes = 4;        // nodes of one level >= 1 in a staged footprint
 
 struct Footprint {
     int imin, imax, jmin, jmax, xmin, xmax, ymin, ymax;
-    int ncv, nx, npx, nbxb, nblk, bx0, by0, n1v;
+    int ncv, nx, npx, nbxb, nblk, bx0, by0;
+    uint32_t mag_nx, mag_npx;           // floor((2^32 - 1) / d) + 1, or 0 for d == 1
     int staged;
-    int a0[kMaxLevels], b0[kMaxLevels], nnv[kMaxLevels], dbase[kMaxLevels + 1];
+    int a0[kMaxLevels], b0[kMaxLevels], nnu[kMaxLevels], nnv[kMaxLevels], dbase[kMaxLevels + 1];
 };
 
-constexpr size_t kStageSmem = (size_t)kMaxDesc * 16 + (size_t)kMaxN1 * 3 * kMaxPx * 4 + (size_t)kMaxCam * kMaxPx * 4;
+// Shared memory of a staged tile: block descriptors, then two level
+// accumulators (int32 [kMaxNodes][3][kMaxPx]); the RGB8 samples of the
+// level-0 cameras reuse whichever accumulator is free at the end.
+constexpr size_t kDescBytes = (size_t)kMaxDesc * 32;
+constexpr size_t kAccBytes = (size_t)kMaxNodes * 3 * kMaxPx * 4;
+constexpr size_t kStageSmem = kDescBytes + 2 * kAccBytes;
+static_assert((size_t)kMaxCam * kMaxPx * 4 <= kAccBytes, "RGB8 staging must fit an accumulator");
+
+// A block descriptor (32 B): d0 = {record word or kNone, record header,
+// packed motion vector, tap tile origin cx | cy << 16}; d1 = the tiles of the
+// reference node covering the block's motion-compensated taps, {T(cx, cy),
+// T(cx+1, cy), T(cx, cy+1), T(cx+1, cy+1)} -- the taps of one block always
+// fall in a 2 x 2 tile neighbourhood.  A reference node's descriptor holds
+// its own tile in d1.x.
+struct Desc {
+    uint4 d0, d1;
+};
+
+// Pixel geometry shared by every level and channel of one staged item.
+struct PixGeom {
+    int x, y;
+    int blk;        // block index inside the footprint's block box
+    int idx;        // index of the pixel in its (possibly partial) block
+    int toff;       // offset of the pixel in a B x B tile
+};
+
+// q = floor(n / d) for n, d < 2^16 with m = floor((2^32 - 1) / d) + 1; that
+// m would be 2^32 for d == 1, which is stored as 0 and means "q = n".
+__device__ __forceinline__ int qdiv(int n, uint32_t m) { return m ? (int)__umulhi((uint32_t)n, m) : n; }
+
+__host__ __device__ __forceinline__ uint32_t qdiv_magic(uint32_t d) {
+    return d <= 1 ? 0u : (uint32_t)(0xFFFFFFFFull / d) + 1u;
+}
 
 template <int BS>
-__device__ __forceinline__ int srv_staged(const DevStream &S, const Footprint &F, const Blk<BS> &bk,
-                                          const uint4 *__restrict__ desc, int l, int a, int b, int c, int x, int y) {
+__device__ __forceinline__ PixGeom pix_geom(const DevStream &S, const Footprint &F, const Blk<BS> &bk, int p) {
+    PixGeom g;
+    const int row = qdiv(p, F.mag_nx);
+    g.x = F.xmin + p - row * F.nx;
+    g.y = F.ymin + row;
     const int B = bk.size();
-    const int bx = bk.div(x), by = bk.div(y);
-    const int blk = (by - F.by0) * F.nbxb + (bx - F.bx0);
-    const uint4 d = desc[F.dbase[l] + (((a - F.a0[l]) * F.nnv[l] + (b - F.b0[l])) * 3 + c) * F.nblk + blk];
+    const int bx = bk.div(g.x), by = bk.div(g.y);
     const int x0 = bx * B, y0 = by * B;
-    if (is_ref(a, b)) return __ldg(S.tiles + (size_t)d.y * (B * B) + (y - y0) * B + (x - x0));
+    g.blk = (by - F.by0) * F.nbxb + (bx - F.bx0);
+    g.idx = (g.y - y0) * min(B, S.W - x0) + (g.x - x0);
+    g.toff = (g.y - y0) * B + (g.x - x0);
+    return g;
+}
+
+// One tap of the resident reference SRV through a descriptor's 2x2 tiles.
+template <int BS>
+__device__ __forceinline__ int tap(const DevStream &S, const Blk<BS> &bk, const uint4 &t, int cx, int cy, int x, int y) {
+    const int B = bk.size();
+    const int tx = bk.div(x), ty = bk.div(y);
+    const uint32_t tile = (ty == cy) ? (tx == cx ? t.x : t.y) : (tx == cx ? t.z : t.w);
+    return __ldg(S.tiles + (size_t)tile * (B * B) + (y - ty * B) * B + (x - tx * B));
+}
+
+// SRV of one node-channel at a pixel, from its staged descriptor.
+template <int BS>
+__device__ __forceinline__ int srv_desc(const DevStream &S, const Blk<BS> &bk, const Desc &D, bool ref,
+                                        const PixGeom &g) {
+    const int B = bk.size();
+    if (ref) return __ldg(S.tiles + (size_t)D.d1.x * (B * B) + g.toff);
     int r = 0;
-    if (d.x != kNone) {
-        const int bw = min(B, S.W - x0);
-        const int m = (int)(int16_t)(d.y & 0xFFFFu);
-        r = S.q * (m + (int)bise_get_small(S.recs + d.x + 1, (d.y >> 21) & 3u, (d.y >> 16) & 31u,
-                                           (uint32_t)((y - y0) * bw + (x - x0))));
+    if (D.d0.x != kNone) {
+        const int m = (int)(int16_t)(D.d0.y & 0xFFFFu);
+        r = S.q * (m + (int)bise_get_small(S.recs + D.d0.x + 1, (D.d0.y >> 21) & 3u, (D.d0.y >> 16) & 31u,
+                                           (uint32_t)g.idx));
     }
     if (!S.mc) return r;
-    const int mvx = (int)(d.z & 1023u) - 512, mvy = (int)((d.z >> 10) & 1023u) - 512;
-    const int sign = ((d.z >> 20) & 1u) ? -1 : 1;
-    return sign * mc_pred(S, bk, d.w, x, y, mvx, mvy) + r;
+    const int mvx = (int)(D.d0.z & 1023u) - 512, mvy = (int)((D.d0.z >> 10) & 1023u) - 512;
+    const int X = 4 * g.x + mvx, Y = 4 * g.y + mvy;
+    const int x0 = X >> 2, y0 = Y >> 2, fx = X & 3, fy = Y & 3;
+    const int xa = clampi(x0, 0, S.W - 1), xb = clampi(x0 + 1, 0, S.W - 1);
+    const int ya = clampi(y0, 0, S.H - 1), yb = clampi(y0 + 1, 0, S.H - 1);
+    const int cx = (int)(D.d0.w & 0xFFFFu), cy = (int)(D.d0.w >> 16);
+    const int a = tap(S, bk, D.d1, cx, cy, xa, ya), b = tap(S, bk, D.d1, cx, cy, xb, ya);
+    const int c = tap(S, bk, D.d1, cx, cy, xa, yb), d = tap(S, bk, D.d1, cx, cy, xb, yb);
+    const int pred = ((4 - fx) * (4 - fy) * a + fx * (4 - fy) * b + (4 - fx) * fy * c + fx * fy * d + 8) >> 4;
+    return ((D.d0.z >> 20) & 1u) ? r - pred : r + pred;
+}
+
+template <int BS>
+__device__ __forceinline__ const Desc &desc_at(const Desc *desc, const Footprint &F, int l, int a, int b, int c,
+                                              int blk) {
+    return desc[F.dbase[l] + (((a - F.a0[l]) * F.nnv[l] + (b - F.b0[l])) * 3 + c) * F.nblk + blk];
 }
 
 template <int BS, int TW, int TH>
-__global__ void __launch_bounds__(TW *TH) k_render(const __grid_constant__ DevStream S,
+__global__ void __launch_bounds__(TW *TH, 4) k_render(const __grid_constant__ DevStream S,
                                                   const __grid_constant__ LaunchViews LV, float *__restrict__ out,
                                                   int force_direct) {
     constexpr int NT = TW * TH;
@@ -435,22 +503,24 @@ __global__ void __launch_bounds__(TW *TH) k_render(const __grid_constant__ DevSt
         F.ncv = ncv;
         F.nx = F.xmax - F.xmin + 1;
         F.npx = F.nx * (F.ymax - F.ymin + 1);
+        F.mag_nx = qdiv_magic((uint32_t)F.nx);
+        F.mag_npx = qdiv_magic((uint32_t)F.npx);
         F.bx0 = F.xmin / S.B;
         F.by0 = F.ymin / S.B;
         F.nbxb = F.xmax / S.B - F.bx0 + 1;
         F.nblk = F.nbxb * (F.ymax / S.B - F.by0 + 1);
-        int nd = 0;
+        int nd = 0, maxn = 0;
         for (int l = 0; l < S.L; l++) {
             F.a0[l] = F.imin >> l;
             F.b0[l] = F.jmin >> l;
+            F.nnu[l] = (F.imax >> l) - F.a0[l] + 1;
             F.nnv[l] = (F.jmax >> l) - F.b0[l] + 1;
             F.dbase[l] = nd;
-            nd += ((F.imax >> l) - F.a0[l] + 1) * F.nnv[l] * 3 * F.nblk;
+            nd += F.nnu[l] * F.nnv[l] * 3 * F.nblk;
+            if (l >= 1) maxn = max(maxn, F.nnu[l] * F.nnv[l]);
         }
         F.dbase[S.L] = nd;
-        F.n1v = (F.jmax >> 1) - (F.jmin >> 1) + 1;
-        const int n1 = ((F.imax >> 1) - (F.imin >> 1) + 1) * F.n1v;
-        F.staged = !force_direct && ncu * ncv <= kMaxCam && F.npx <= kMaxPx && nd <= kMaxDesc && n1 <= kMaxN1;
+        F.staged = !force_direct && ncu * ncv <= kMaxCam && F.npx <= kMaxPx && nd <= kMaxDesc && maxn <= kMaxNodes;
     }
     __syncthreads();
 
@@ -458,15 +528,17 @@ __global__ void __launch_bounds__(TW *TH) k_render(const __grid_constant__ DevSt
     if (!F.staged) {
         // ---- direct path: every ray decodes its own 16 samples ----
         if (act) {
-            blend16(r, [&](int i, int j, int x, int y) { return sample_direct(S, T, bk, i, j, x, y); }, o);
+            blend16(r, [&](int, int, int, int, int i, int j, int x, int y) { return sample_direct(S, T, bk, i, j, x, y); },
+                    o);
         }
     } else {
-        uint4 *desc = reinterpret_cast<uint4 *>(smem);
-        int *acc1 = reinterpret_cast<int *>(smem + (size_t)kMaxDesc * 16);
-        uint32_t *rgb = reinterpret_cast<uint32_t *>(smem + (size_t)kMaxDesc * 16 + (size_t)kMaxN1 * 3 * kMaxPx * 4);
+        Desc *desc = reinterpret_cast<Desc *>(smem);
+        int *acc_base = reinterpret_cast<int *>(smem + kDescBytes);
+        constexpr int kAccInts = (int)(kAccBytes / 4);
         const int L = S.L;
         const int B = bk.size();
-        // ---- B1: block descriptors (index, header, motion vector) ----
+        const size_t plane = (size_t)S.W * S.H;
+        // ---- 1: block descriptors (index, header, motion vector, tap tiles) ----
         for (int d = threadIdx.x; d < F.dbase[L]; d += NT) {
             int l = 0;
             while (d >= F.dbase[l + 1]) l++;
@@ -479,76 +551,115 @@ __global__ void __launch_bounds__(TW *TH) k_render(const __grid_constant__ DevSt
             const int a = F.a0[l] + e / F.nnv[l];
             const int bx = F.bx0 + blk % F.nbxb, by = F.by0 + blk / F.nbxb;
             const int k = by * S.nbx + bx;
-            uint4 out4 = make_uint4(kNone, 0u, 0u, 0u);
-            const bool inside = a < T.gu[l] && b < T.gv[l] && bx < S.nbx && by < S.nby;
-            if (inside) {
+            Desc D;
+            D.d0 = make_uint4(kNone, 0u, 0u, 0u);
+            D.d1 = make_uint4(0u, 0u, 0u, 0u);
+            if (a < T.gu[l] && b < T.gv[l] && bx < S.nbx && by < S.nby) {
                 if (is_ref(a, b)) {
-                    out4.y = __ldg(S.ref_tab + (size_t)ref_rank(T, l, a, b, c) * S.nblocks + k);
+                    D.d1.x = __ldg(S.ref_tab + (size_t)ref_rank(T, l, a, b, c) * S.nblocks + k);
                 } else {
                     const int nc = nc_index(T, l, a, b, c);
                     const uint4 g = __ldg(S.groups + (size_t)nc * S.ngroups + (k >> 5));
                     const uint32_t bit = (uint32_t)k & 31u;
                     if ((g.x >> bit) & 1u) {
                         const uint32_t rec = g.y + __ldg(S.offs + g.z + __popc(g.x & ((1u << bit) - 1u)));
-                        out4.x = rec;
-                        out4.y = __ldg(S.recs + rec);
+                        D.d0.x = rec;
+                        D.d0.y = __ldg(S.recs + rec);
                     }
                     if (S.mc) {
                         const uint32_t sym = bise_get_long(S.mvs, S.mv_mode, S.mv_b,
                                                            (uint64_t)pred_rank(T, l, a, b, c) * S.nblocks + k);
                         int mvx, mvy, sign;
                         decode_mv(S, sym, mvx, mvy, sign);
-                        out4.z = (uint32_t)(mvx + 512) | ((uint32_t)(mvy + 512) << 10) | ((sign < 0 ? 1u : 0u) << 20);
-                        out4.w = (uint32_t)ref_rank(T, l, a & ~1, b & ~1, c) * S.nblocks;
+                        D.d0.z = (uint32_t)(mvx + 512) | ((uint32_t)(mvy + 512) << 10) | ((sign < 0 ? 1u : 0u) << 20);
+                        // the taps of this block start at the clamped (x0 + floor(mvx/4), y0 + floor(mvy/4))
+                        const int cx = bk.div(clampi(bx * B + (mvx >> 2), 0, S.W - 1));
+                        const int cy = bk.div(clampi(by * B + (mvy >> 2), 0, S.H - 1));
+                        const size_t row = (size_t)ref_rank(T, l, a & ~1, b & ~1, c) * S.nblocks;
+                        const int cx1 = min(cx + 1, S.nbx - 1), cy1 = min(cy + 1, S.nby - 1);
+                        D.d0.w = (uint32_t)cx | ((uint32_t)cy << 16);
+                        D.d1.x = __ldg(S.ref_tab + row + cy * S.nbx + cx);
+                        D.d1.y = __ldg(S.ref_tab + row + cy * S.nbx + cx1);
+                        D.d1.z = __ldg(S.ref_tab + row + cy1 * S.nbx + cx);
+                        D.d1.w = __ldg(S.ref_tab + row + cy1 * S.nbx + cx1);
                     }
                 }
             }
-            desc[d] = out4;
+            desc[d] = D;
         }
         __syncthreads();
-        // ---- B2: level-1 reconstructions = root + SRV levels L-1 .. 1 ----
-        const int a1 = F.imin >> 1, b1 = F.jmin >> 1;
-        const int n1 = ((F.imax >> 1) - a1 + 1) * F.n1v;
-        const size_t plane = (size_t)S.W * S.H;
-        for (int e = threadIdx.x; e < n1 * 3 * F.npx; e += NT) {
-            const int p = e % F.npx;
-            const int c = (e / F.npx) % 3;
-            const int nd = e / (F.npx * 3);
-            const int a = a1 + nd / F.n1v, b = b1 + nd % F.n1v;
-            const int x = F.xmin + p % F.nx, y = F.ymin + p / F.nx;
-            int v = 0;
-            if (a < T.gu[1] && b < T.gv[1]) {
-                // node (a, b) of level 1 lies under root (a >> (L-1), b >> (L-1))
-                const int ra = a >> (L - 1), rb = b >> (L - 1);
-                v = __ldg(S.roots + ((size_t)(ra * T.gv[L] + rb) * 3 + c) * plane + (size_t)y * S.W + x);
-                for (int l = L - 1; l >= 1; l--)
-                    v += srv_staged(S, F, bk, desc, l, a >> (l - 1), b >> (l - 1), c, x, y);
+        // ---- 2: levels L-1 .. 1: acc_l(node) = acc_{l+1}(parent) + SRV_l(node) ----
+        int cur = 0;
+        for (int l = L - 1; l >= 1; l--) {
+            const int nn = F.nnu[l] * F.nnv[l];
+            const int *par = acc_base + (cur ^ 1) * kAccInts;
+            int *acc = acc_base + cur * kAccInts;
+            for (int e = threadIdx.x; e < nn * F.npx; e += NT) {
+                const int nd = qdiv(e, F.mag_npx);
+                const int p = e - nd * F.npx;
+                const int nv = F.nnv[l];   // nd < 4 nodes: the quotient by a few compares
+                const int qa = nd >= nv ? (nd >= 2 * nv ? (nd >= 3 * nv ? 3 : 2) : 1) : 0;
+                const int a = F.a0[l] + qa, b = F.b0[l] + nd - qa * nv;
+                const PixGeom g = pix_geom(S, F, bk, p);
+                const bool ref = is_ref(a, b);
+                int v[3];
+                if (l == L - 1) {
+                    const size_t rb = ((size_t)(a >> 1) * T.gv[L] + (b >> 1)) * 3 * plane + (size_t)g.y * S.W + g.x;
+                    v[0] = __ldg(S.roots + rb);
+                    v[1] = __ldg(S.roots + rb + plane);
+                    v[2] = __ldg(S.roots + rb + 2 * plane);
+                } else {
+                    const int pn = ((a >> 1) - F.a0[l + 1]) * F.nnv[l + 1] + ((b >> 1) - F.b0[l + 1]);
+                    const int *pp = par + pn * 3 * kMaxPx + p;
+                    v[0] = pp[0];
+                    v[1] = pp[kMaxPx];
+                    v[2] = pp[2 * kMaxPx];
+                }
+                int *dst = acc + nd * 3 * kMaxPx + p;
+#pragma unroll
+                for (int c = 0; c < 3; c++)
+                    dst[c * kMaxPx] = v[c] + srv_desc(S, bk, desc_at<BS>(desc, F, l, a, b, c, g.blk), ref, g);
             }
-            acc1[e] = v;
+            __syncthreads();
+            cur ^= 1;
         }
-        __syncthreads();
-        // ---- B3: level-0 samples of the footprint's cameras -> RGB8 ----
+        // ---- 3: level-0 samples of the footprint's cameras -> RGB8 ----
+        const int *acc1 = acc_base + (cur ^ 1) * kAccInts;          // level 1 (unused when L == 1)
+        uint32_t *rgb = reinterpret_cast<uint32_t *>(acc_base + cur * kAccInts);
         const int ncam = (F.imax - F.imin + 1) * F.ncv;
         for (int e = threadIdx.x; e < ncam * F.npx; e += NT) {
-            const int p = e % F.npx;
-            const int cam = e / F.npx;
+            const int cam = qdiv(e, F.mag_npx);
+            const int p = e - cam * F.npx;
             const int i = F.imin + cam / F.ncv, j = F.jmin + cam % F.ncv;
-            const int x = F.xmin + p % F.nx, y = F.ymin + p / F.nx;
-            const int nd = ((i >> 1) - a1) * F.n1v + ((j >> 1) - b1);
-            const int *base = acc1 + (size_t)nd * 3 * F.npx + p;
-            const int v0 = base[0] + srv_staged(S, F, bk, desc, 0, i, j, 0, x, y);
-            const int v1 = base[F.npx] + srv_staged(S, F, bk, desc, 0, i, j, 1, x, y);
-            const int v2 = base[2 * F.npx] + srv_staged(S, F, bk, desc, 0, i, j, 2, x, y);
-            rgb[e] = ycocg_to_rgb8(v0, v1, v2);
+            const PixGeom g = pix_geom(S, F, bk, p);
+            int v[3];
+            if (L == 1) {
+                const size_t rb = ((size_t)(i >> 1) * T.gv[1] + (j >> 1)) * 3 * plane + (size_t)g.y * S.W + g.x;
+                v[0] = __ldg(S.roots + rb);
+                v[1] = __ldg(S.roots + rb + plane);
+                v[2] = __ldg(S.roots + rb + 2 * plane);
+            } else {
+                const int pn = ((i >> 1) - F.a0[1]) * F.nnv[1] + ((j >> 1) - F.b0[1]);
+                const int *pp = acc1 + pn * 3 * kMaxPx + p;
+                v[0] = pp[0];
+                v[1] = pp[kMaxPx];
+                v[2] = pp[2 * kMaxPx];
+            }
+            const bool ref = is_ref(i, j);
+#pragma unroll
+            for (int c = 0; c < 3; c++) v[c] += srv_desc(S, bk, desc_at<BS>(desc, F, 0, i, j, c, g.blk), ref, g);
+            rgb[e] = ycocg_to_rgb8(v[0], v[1], v[2]);
         }
         (void)B;
         __syncthreads();
-        // ---- C: blend ----
+        // ---- 4: blend ----
         if (act) {
-            blend16(r,
-                    [&](int i, int j, int x, int y) {
-                        return rgb[((i - F.imin) * F.ncv + (j - F.jmin)) * F.npx + (y - F.ymin) * F.nx + (x - F.xmin)];
-                    },
+            const int npx = F.npx;
+            const int ci[2] = {(r.i0 - F.imin) * F.ncv * npx, (r.i1 - F.imin) * F.ncv * npx};
+            const int cj[2] = {(r.j0 - F.jmin) * npx, (r.j1 - F.jmin) * npx};
+            const int cy[2] = {(r.y0 - F.ymin) * F.nx, (r.y1 - F.ymin) * F.nx};
+            const int cx[2] = {r.x0 - F.xmin, r.x1 - F.xmin};
+            blend16(r, [&](int a, int b, int xs, int ys, int, int, int, int) { return rgb[ci[a] + cj[b] + cy[ys] + cx[xs]]; },
                     o);
         }
     }
@@ -726,6 +837,333 @@ __global__ void __launch_bounds__(256) k_dequant(const __grid_constant__ DevStre
     }
 }
 
+// ---------------------------------------------------------------------------
+// K1 (cached form): decode every block a call's views reach once, then blend
+// ---------------------------------------------------------------------------
+//
+// mark:   each 16 x 16 ray tile flags the (camera, block) pairs of its
+//         footprint's bounding box (idempotent byte stores);
+// assign: flagged keys get consecutive slots of the call's decoded-block
+//         cache (keys past the capacity keep kNone and are decoded per ray);
+// decode: a persistent kernel decodes each slot's block -- root + every level
+//         of the tree path with motion re-compensation -- to RGB8, with the
+//         block's per-(level, channel) descriptors staged once;
+// render: each ray gathers its 16 RGB8 samples from the cache and blends.
+
+// Descriptor of block (bx, by) of node (a, b) at level l, channel c.
+template <int BS>
+__device__ Desc make_desc(const DevStream &S, const LevelTabs &T, const Blk<BS> &bk, int l, int a, int b, int c, int bx,
+                          int by) {
+    const int B = bk.size();
+    const int k = by * S.nbx + bx;
+    Desc D;
+    D.d0 = make_uint4(kNone, 0u, 0u, 0u);
+    D.d1 = make_uint4(0u, 0u, 0u, 0u);
+    if (is_ref(a, b)) {
+        D.d1.x = __ldg(S.ref_tab + (size_t)ref_rank(T, l, a, b, c) * S.nblocks + k);
+        return D;
+    }
+    const int nc = nc_index(T, l, a, b, c);
+    const uint4 g = __ldg(S.groups + (size_t)nc * S.ngroups + (k >> 5));
+    const uint32_t bit = (uint32_t)k & 31u;
+    if ((g.x >> bit) & 1u) {
+        const uint32_t rec = g.y + __ldg(S.offs + g.z + __popc(g.x & ((1u << bit) - 1u)));
+        D.d0.x = rec;
+        D.d0.y = __ldg(S.recs + rec);
+    }
+    if (S.mc) {
+        const uint32_t sym =
+            bise_get_long(S.mvs, S.mv_mode, S.mv_b, (uint64_t)pred_rank(T, l, a, b, c) * S.nblocks + k);
+        int mvx, mvy, sign;
+        decode_mv(S, sym, mvx, mvy, sign);
+        D.d0.z = (uint32_t)(mvx + 512) | ((uint32_t)(mvy + 512) << 10) | ((sign < 0 ? 1u : 0u) << 20);
+        const int cx = bk.div(clampi(bx * B + (mvx >> 2), 0, S.W - 1));
+        const int cy = bk.div(clampi(by * B + (mvy >> 2), 0, S.H - 1));
+        const size_t row = (size_t)ref_rank(T, l, a & ~1, b & ~1, c) * S.nblocks;
+        const int cx1 = min(cx + 1, S.nbx - 1), cy1 = min(cy + 1, S.nby - 1);
+        D.d0.w = (uint32_t)cx | ((uint32_t)cy << 16);
+        D.d1.x = __ldg(S.ref_tab + row + cy * S.nbx + cx);
+        D.d1.y = __ldg(S.ref_tab + row + cy * S.nbx + cx1);
+        D.d1.z = __ldg(S.ref_tab + row + cy1 * S.nbx + cx);
+        D.d1.w = __ldg(S.ref_tab + row + cy1 * S.nbx + cx1);
+    }
+    return D;
+}
+
+template <int BS, int TW, int TH>
+__global__ void __launch_bounds__(TW *TH) k_mark(const __grid_constant__ DevStream S,
+                                                const __grid_constant__ LaunchViews LV, uint8_t *__restrict__ flags) {
+    constexpr int NT = TW * TH;
+    __shared__ int s_view;
+    __shared__ int s_red[NT / 32][8];
+    __shared__ int s_box[8];
+    if (threadIdx.x == 0) s_view = find_view(LV, blockIdx.x);
+    __syncthreads();
+    const hmlfc_view &V = LV.views[s_view];
+    const int tiles_x = (V.width + TW - 1) / TW;
+    const int local = blockIdx.x - LV.tile_start[s_view];
+    const int px = (local % tiles_x) * TW + (int)threadIdx.x % TW;
+    const int py = (local / tiles_x) * TH + (int)threadIdx.x / TW;
+    const bool act = px < V.width && py < V.height;
+    Ray r;
+    ray_setup(V, S.nu, S.nv, S.W, S.H, act ? px : 0, act ? py : 0, r);
+    const Blk<BS> bk(S.B);
+    int red[8] = {act ? r.i0 : INT_MAX, act ? -r.i1 : INT_MAX, act ? r.j0 : INT_MAX, act ? -r.j1 : INT_MAX,
+                  act ? bk.div(r.x0) : INT_MAX, act ? -bk.div(r.x1) : INT_MAX, act ? bk.div(r.y0) : INT_MAX,
+                  act ? -bk.div(r.y1) : INT_MAX};
+#pragma unroll
+    for (int q = 0; q < 8; q++) red[q] = __reduce_min_sync(0xFFFFFFFFu, red[q]);
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int q = 0; q < 8; q++) s_red[threadIdx.x >> 5][q] = red[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        int m = INT_MAX;
+        for (int w = 0; w < NT / 32; w++) m = min(m, s_red[w][threadIdx.x]);
+        s_box[threadIdx.x] = (threadIdx.x & 1) ? -m : m;
+    }
+    __syncthreads();
+    const int ncu = s_box[1] - s_box[0] + 1, ncv = s_box[3] - s_box[2] + 1;
+    const int nbu = s_box[5] - s_box[4] + 1, nbv = s_box[7] - s_box[6] + 1;
+    const int nb = nbu * nbv;
+    for (int e = threadIdx.x; e < ncu * ncv * nb; e += NT) {
+        const int cam = e / nb, blk = e - cam * nb;
+        const int i = s_box[0] + cam / ncv, j = s_box[2] + cam % ncv;
+        const int bx = s_box[4] + blk % nbu, by = s_box[6] + blk / nbu;
+        flags[((size_t)i * S.nv + j) * S.nblocks + (size_t)by * S.nbx + bx] = 1;
+    }
+}
+
+// Compact the flags into cache slots, cluster by cluster: a cluster key is a
+// (level-1 node, block) pair; its up to four cameras (the node's 2 x 2
+// children) get consecutive slots, and every cluster with a flagged camera
+// becomes one work item {cluster key, camera mask, first slot} of the decode.
+// Keys beyond the capacity get no slot (kNone): their rays decode directly.
+__global__ void __launch_bounds__(256) k_assign(const __grid_constant__ DevStream S, const uint8_t *__restrict__ flags,
+                                                uint32_t *__restrict__ slotmap, uint4 *__restrict__ items,
+                                                unsigned long long *__restrict__ counters, uint32_t capacity) {
+    __shared__ uint32_t s_warp[8][2];
+    __shared__ uint32_t s_base[2];
+    const int64_t n_ck = (int64_t)S.gu[1] * S.gv[1] * S.nblocks;
+    const int64_t ck = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    uint32_t mask = 0;
+    int64_t keys[4];
+    if (ck < n_ck) {
+        const int node = (int)(ck / S.nblocks), k = (int)(ck - (int64_t)node * S.nblocks);
+        const int a1 = node / S.gv[1], b1 = node - (node / S.gv[1]) * S.gv[1];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int i = 2 * a1 + (q >> 1), j = 2 * b1 + (q & 1);
+            keys[q] = -1;
+            if (i < S.nu && j < S.nv) {
+                keys[q] = ((int64_t)i * S.nv + j) * S.nblocks + k;
+                if (flags[keys[q]]) mask |= 1u << q;
+            }
+        }
+    }
+    const uint32_t nslot = __popc(mask), nitem = mask ? 1u : 0u;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t is = nslot, ii = nitem;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t vs = __shfl_up_sync(0xFFFFFFFFu, is, o), vi = __shfl_up_sync(0xFFFFFFFFu, ii, o);
+        if (lane >= o) {
+            is += vs;
+            ii += vi;
+        }
+    }
+    if (lane == 31) {
+        s_warp[warp][0] = is;
+        s_warp[warp][1] = ii;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t as = 0, ai = 0;
+        for (int w = 0; w < 8; w++) {
+            const uint32_t vs = s_warp[w][0], vi = s_warp[w][1];
+            s_warp[w][0] = as;
+            s_warp[w][1] = ai;
+            as += vs;
+            ai += vi;
+        }
+        const unsigned long long old = atomicAdd(counters, ((unsigned long long)ai << 32) | as);
+        s_base[0] = (uint32_t)(old & 0xFFFFFFFFull);
+        s_base[1] = (uint32_t)(old >> 32);
+    }
+    __syncthreads();
+    if (ck >= n_ck) return;
+    const uint32_t slot0 = s_base[0] + s_warp[warp][0] + is - nslot;
+    const uint32_t item = s_base[1] + s_warp[warp][1] + ii - nitem;
+    uint32_t slot = slot0;
+    const bool fits = slot0 + nslot <= capacity;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        if (keys[q] < 0) continue;
+        if ((mask >> q) & 1u) {
+            slotmap[keys[q]] = fits ? slot : kNone;
+            slot++;
+        } else {
+            slotmap[keys[q]] = kNone;
+        }
+    }
+    if (mask && fits) items[item] = make_uint4((uint32_t)ck, mask, slot0, 0u);
+    else if (mask) items[item] = make_uint4((uint32_t)ck, 0u, 0u, 0u);   // over capacity: nothing to decode
+}
+
+// Decode the cached blocks, one (level-1 node, block) item at a time: the
+// level-1 reconstruction (root + SRV levels L-1 .. 1) of each pixel is shared
+// by the item's cameras, which then add their own level-0 SRV.  Persistent
+// CTAs; several items per pass when a block has fewer pixels than threads.
+template <int BS>
+__global__ void __launch_bounds__(256) k_decode_blocks(const __grid_constant__ DevStream S,
+                                                      const uint4 *__restrict__ items,
+                                                      const unsigned long long *__restrict__ counters,
+                                                      uint32_t *__restrict__ cache) {
+    constexpr int kMaxGroup = 16;                 // items per pass (B = 4)
+    constexpr int kDescPer = (kMaxLevels - 1) * 3 + 4 * 3;
+    __shared__ LevelTabs T;
+    __shared__ Desc s_desc[kMaxGroup * kDescPer];
+    load_tabs(S, T);
+    const Blk<BS> bk(S.B);
+    const int B = bk.size(), B2 = B * B;
+    const int G = max(1, min(kMaxGroup, (int)blockDim.x / B2));
+    const int L = S.L;
+    const uint32_t n = (uint32_t)(__ldg(counters) >> 32);
+    const size_t plane = (size_t)S.W * S.H;
+    const int nd = (L - 1) * 3 + 12;              // descriptors per item
+    __syncthreads();
+    for (uint32_t first = blockIdx.x * G; first < n; first += gridDim.x * G) {
+        for (int d = threadIdx.x; d < G * nd; d += blockDim.x) {
+            const int gi = d / nd, e = d - gi * nd;
+            if (first + gi >= n) continue;
+            const uint4 it = __ldg(items + first + gi);
+            if (!it.y) continue;
+            const int node = (int)(it.x / (uint32_t)S.nblocks), k = (int)(it.x - (uint32_t)node * S.nblocks);
+            const int a1 = node / T.gv[1], b1 = node - (node / T.gv[1]) * T.gv[1];
+            int l, a, b, c;
+            if (e < (L - 1) * 3) {                // level l >= 1 of the shared path
+                l = 1 + e / 3;
+                c = e - 3 * (l - 1);
+                a = a1 >> (l - 1);
+                b = b1 >> (l - 1);
+            } else {                              // level 0 of camera q of the cluster
+                const int q = (e - (L - 1) * 3) / 3;
+                c = (e - (L - 1) * 3) - 3 * q;
+                l = 0;
+                a = 2 * a1 + (q >> 1);
+                b = 2 * b1 + (q & 1);
+                if (!((it.y >> q) & 1u)) continue;
+            }
+            s_desc[d] = make_desc(S, T, bk, l, a, b, c, k % S.nbx, k / S.nbx);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < G * B2; e += blockDim.x) {
+            const int gi = e / B2, p = e - gi * B2;
+            if (first + gi >= n) continue;
+            const uint4 it = __ldg(items + first + gi);
+            if (!it.y) continue;
+            const int node = (int)(it.x / (uint32_t)S.nblocks), k = (int)(it.x - (uint32_t)node * S.nblocks);
+            const int a1 = node / T.gv[1], b1 = node - (node / T.gv[1]) * T.gv[1];
+            const int bx = k % S.nbx, by = k / S.nbx;
+            const int yy = p / B, xx = p - yy * B;
+            const int bw = min(B, S.W - bx * B), bh = min(B, S.H - by * B);
+            const bool inside = xx < bw && yy < bh;
+            PixGeom g;
+            g.x = bx * B + min(xx, bw - 1);
+            g.y = by * B + min(yy, bh - 1);
+            g.blk = 0;
+            g.idx = (g.y - by * B) * bw + (g.x - bx * B);
+            g.toff = (g.y - by * B) * B + (g.x - bx * B);
+            const size_t rb = ((size_t)(a1 >> (L - 1)) * T.gv[L] + (b1 >> (L - 1))) * 3 * plane + (size_t)g.y * S.W + g.x;
+            int v[3] = {__ldg(S.roots + rb), __ldg(S.roots + rb + plane), __ldg(S.roots + rb + 2 * plane)};
+            const Desc *dd = s_desc + gi * nd;
+            for (int l = L - 1; l >= 1; l--) {
+                const bool ref = is_ref(a1 >> (l - 1), b1 >> (l - 1));
+#pragma unroll
+                for (int c = 0; c < 3; c++) v[c] += srv_desc(S, bk, dd[(l - 1) * 3 + c], ref, g);
+            }
+            uint32_t slot = it.z;
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                if (!((it.y >> q) & 1u)) continue;
+                const int i = 2 * a1 + (q >> 1), j = 2 * b1 + (q & 1);
+                const bool ref = is_ref(i, j);
+                const Desc *d0 = dd + (L - 1) * 3 + q * 3;
+                const int w0 = v[0] + srv_desc(S, bk, d0[0], ref, g);
+                const int w1 = v[1] + srv_desc(S, bk, d0[1], ref, g);
+                const int w2 = v[2] + srv_desc(S, bk, d0[2], ref, g);
+                cache[(size_t)slot * B2 + p] = inside ? ycocg_to_rgb8(w0, w1, w2) : 0u;
+                slot++;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Blend of one ray whose samples are decoded directly (kept out of line so
+// that the cached fast path keeps its registers).
+template <int BS>
+__device__ __noinline__ void blend_direct(const DevStream &S, const LevelTabs &T, const Blk<BS> &bk, const Ray &r,
+                                          float o[3]) {
+    blend16(r, [&](int, int, int, int, int i, int j, int x, int y) { return sample_direct(S, T, bk, i, j, x, y); }, o);
+}
+
+template <int BS, int TW, int TH>
+__global__ void __launch_bounds__(TW *TH) k_render_cached(const __grid_constant__ DevStream S,
+                                                         const __grid_constant__ LaunchViews LV,
+                                                         const uint32_t *__restrict__ slotmap,
+                                                         const uint32_t *__restrict__ cache, float *__restrict__ out) {
+    __shared__ LevelTabs T;
+    __shared__ int s_view;
+    load_tabs(S, T);
+    if (threadIdx.x == 0) s_view = find_view(LV, blockIdx.x);
+    __syncthreads();
+    const hmlfc_view &V = LV.views[s_view];
+    const int tiles_x = (V.width + TW - 1) / TW;
+    const int local = blockIdx.x - LV.tile_start[s_view];
+    const int px = (local % tiles_x) * TW + (int)threadIdx.x % TW;
+    const int py = (local / tiles_x) * TH + (int)threadIdx.x / TW;
+    if (px >= V.width || py >= V.height) return;
+    const Blk<BS> bk(S.B);
+    const int B = bk.size();
+    Ray r;
+    ray_setup(V, S.nu, S.nv, S.W, S.H, px, py, r);
+    // slots of the 16 samples first (independent loads), then their values
+    const uint32_t nv = (uint32_t)S.nv, nbl = (uint32_t)S.nblocks, nbx = (uint32_t)S.nbx;
+    const uint32_t cam[4] = {(uint32_t)r.i0 * nv + r.j0, (uint32_t)r.i0 * nv + r.j1, (uint32_t)r.i1 * nv + r.j0,
+                             (uint32_t)r.i1 * nv + r.j1};
+    const int bx[2] = {bk.div(r.x0), bk.div(r.x1)}, by[2] = {bk.div(r.y0), bk.div(r.y1)};
+    const uint32_t blk[4] = {(uint32_t)(by[0] * S.nbx + bx[0]), (uint32_t)(by[1] * S.nbx + bx[0]),
+                             (uint32_t)(by[0] * S.nbx + bx[1]), (uint32_t)(by[1] * S.nbx + bx[1])};
+    const uint32_t off[4] = {(uint32_t)((r.y0 - by[0] * B) * B + (r.x0 - bx[0] * B)),
+                             (uint32_t)((r.y1 - by[1] * B) * B + (r.x0 - bx[0] * B)),
+                             (uint32_t)((r.y0 - by[0] * B) * B + (r.x1 - bx[1] * B)),
+                             (uint32_t)((r.y1 - by[1] * B) * B + (r.x1 - bx[1] * B))};
+    (void)nbx;
+    uint32_t slot[16];
+    bool all = true;
+#pragma unroll
+    for (int q = 0; q < 16; q++) {
+        slot[q] = __ldg(slotmap + cam[q >> 2] * nbl + blk[q & 3]);
+        all &= slot[q] != kNone;
+    }
+    float o[3];
+    if (all) {
+        uint32_t val[16];
+#pragma unroll
+        for (int q = 0; q < 16; q++) val[q] = __ldg(cache + slot[q] * (uint32_t)(B * B) + off[q & 3]);
+        // sample order of blend16: q = a*8 + b*4 + xs*2 + ys  ->  cam a*2+b, corner xs*2+ys
+        blend16(r, [&](int a, int b, int xs, int ys, int, int, int, int) { return val[a * 8 + b * 4 + xs * 2 + ys]; }, o);
+    } else {
+        blend_direct(S, T, bk, r, o);      // a sample beyond the cache capacity: decode this ray directly
+    }
+    float *dst = out + V.out_offset + ((size_t)py * V.width + px) * 3;
+    dst[0] = o[0];
+    dst[1] = o[1];
+    dst[2] = o[2];
+}
+
 template <int BS>
 cudaError_t render_dispatch_tw(const DevStream &ds, const LaunchViews &lv, int total_tiles, float *d_out, int mode,
                                cudaStream_t st) {
@@ -779,6 +1217,34 @@ cudaError_t launch_render(const DevStream &ds, const LaunchViews &lv, int total_
     cudaError_t e = cudaSuccess;
     HMLFC_DISPATCH_B(ds.B, (e = render_dispatch_tw<BS>(ds, lv, total_tiles, d_out, mode, st)));
     return e;
+}
+
+cudaError_t launch_mark(const DevStream &ds, const LaunchViews &lv, int total_tiles, uint8_t *flags, cudaStream_t st) {
+    if (total_tiles <= 0) return cudaSuccess;
+    HMLFC_DISPATCH_B(ds.B, (k_mark<BS, 16, 16><<<total_tiles, 256, 0, st>>>(ds, lv, flags)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assign(const DevStream &ds, const uint8_t *flags, uint32_t *slotmap, uint4 *items,
+                          unsigned long long *counters, uint32_t capacity, cudaStream_t st) {
+    const int64_t n_ck = (int64_t)ds.gu[1] * ds.gv[1] * ds.nblocks;
+    const int64_t grid = (n_ck + 255) / 256;
+    if (grid <= 0) return cudaSuccess;
+    k_assign<<<(unsigned)grid, 256, 0, st>>>(ds, flags, slotmap, items, counters, capacity);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decode_blocks(const DevStream &ds, const uint4 *items, const unsigned long long *counters,
+                                 uint32_t *cache, int grid, cudaStream_t st) {
+    HMLFC_DISPATCH_B(ds.B, (k_decode_blocks<BS><<<grid, 256, 0, st>>>(ds, items, counters, cache)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render_cached(const DevStream &ds, const LaunchViews &lv, int total_tiles, const uint32_t *slotmap,
+                                 const uint32_t *cache, float *d_out, cudaStream_t st) {
+    if (total_tiles <= 0) return cudaSuccess;
+    HMLFC_DISPATCH_B(ds.B, (k_render_cached<BS, 16, 16><<<total_tiles, 256, 0, st>>>(ds, lv, slotmap, cache, d_out)));
+    return cudaGetLastError();
 }
 
 cudaError_t launch_render_relaxed(const DevStream &ds, const LaunchViews &lv, int total_tiles, const float *coeff,

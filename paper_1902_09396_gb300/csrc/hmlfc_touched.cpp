@@ -7,7 +7,9 @@
 // significant reference block reached directly or by a motion-compensation
 // tap (B * B * 2 B resident tile + 4 B table entry).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <memory>
 #include <cstring>
 #include <vector>
 
@@ -76,21 +78,36 @@ void nb(double c, int n, int &i0, int &i1, double &f) {
     f = cc - fl;
 }
 
-double count_view(const Counter &C, const hmlfc_view &V) {
+// Seen-sets as atomic bitsets, so that several views can share them (the
+// union over a call) while host threads count in parallel.
+struct Bits {
+    std::unique_ptr<std::atomic<uint64_t>[]> w;
+    explicit Bits(size_t n) : w(new std::atomic<uint64_t>[(n + 63) / 64]) {
+        for (size_t i = 0; i < (n + 63) / 64; i++) w[i].store(0, std::memory_order_relaxed);
+    }
+    // true if the bit was clear (first visit)
+    bool set(size_t k) {
+        const uint64_t m = 1ull << (k & 63);
+        return !(w[k >> 6].fetch_or(m, std::memory_order_relaxed) & m);
+    }
+};
+
+struct Seen {
+    Bits sample, root, blk, grp;
+    explicit Seen(const Geometry &g)
+        : sample((size_t)g.nu * g.nv * g.W * g.H), root((size_t)g.n_roots * g.W * g.H),
+          blk((size_t)g.n_nc * g.nblocks), grp((size_t)g.n_nc * g.ngroups) {}
+};
+
+// Bytes first reached by view V (all of its bytes when `seen` is fresh).
+double count_view(const Counter &C, const hmlfc_view &V, Seen &seen, bool with_output = true) {
     const Geometry &g = C.g;
     const size_t plane = (size_t)g.W * g.H;
-    std::vector<uint64_t> sample_seen(((size_t)g.nu * g.nv * plane + 63) / 64, 0);
-    std::vector<uint8_t> root_seen((size_t)g.n_roots * plane, 0);
-    std::vector<uint8_t> blk_seen((size_t)g.n_nc * g.nblocks, 0);
-    std::vector<uint8_t> grp_seen((size_t)g.n_nc * g.ngroups, 0);
-    double acc = (double)V.width * V.height * 12.0;
+    double acc = with_output ? (double)V.width * V.height * 12.0 : 0.0;
     const double tile_bytes = (double)g.B * g.B * 2.0 + 4.0;
     auto nc_of = [&](int l, int a, int b, int c) { return g.nc_base[l] + ((int64_t)a * g.gv[l] + b) * 3 + c; };
     auto touch_ref = [&](int64_t nc, int k) {
-        const size_t key = (size_t)nc * g.nblocks + k;
-        if (blk_seen[key]) return;
-        blk_seen[key] = 1;
-        if (C.record_bytes(nc, k) >= 0) acc += tile_bytes;
+        if (seen.blk.set((size_t)nc * g.nblocks + k) && C.record_bytes(nc, k) >= 0) acc += tile_bytes;
     };
     for (int py = 0; py < V.height; py++)
         for (int px = 0; px < V.width; px++) {
@@ -111,13 +128,9 @@ double count_view(const Counter &C, const hmlfc_view &V) {
             for (int q = 0; q < 16; q++) {
                 const int i = ii[q >> 3], j = jj[(q >> 2) & 1], x = xx[(q >> 1) & 1], y = yy[q & 1];
                 const size_t sk = ((size_t)i * g.nv + j) * plane + (size_t)y * g.W + x;
-                if ((sample_seen[sk >> 6] >> (sk & 63)) & 1u) continue;
-                sample_seen[sk >> 6] |= 1ull << (sk & 63);
+                if (!seen.sample.set(sk)) continue;
                 const size_t rp = ((size_t)(i >> g.L) * g.gv[g.L] + (j >> g.L)) * plane + (size_t)y * g.W + x;
-                if (!root_seen[rp]) {
-                    root_seen[rp] = 1;
-                    acc += 6.0;
-                }
+                if (seen.root.set(rp)) acc += 6.0;
                 const int k = (y / g.B) * g.nbx + x / g.B;
                 for (int l = 0; l < g.L; l++) {
                     const int a = i >> l, b = j >> l;
@@ -129,13 +142,8 @@ double count_view(const Counter &C, const hmlfc_view &V) {
                             continue;
                         }
                         const size_t key = (size_t)nc * g.nblocks + k;
-                        if (!blk_seen[key]) {
-                            blk_seen[key] = 1;
-                            const size_t gk = (size_t)nc * g.ngroups + k / 32;
-                            if (!grp_seen[gk]) {
-                                grp_seen[gk] = 1;
-                                acc += 16.0;
-                            }
+                        if (seen.blk.set(key)) {
+                            if (seen.grp.set((size_t)nc * g.ngroups + k / 32)) acc += 16.0;
                             const int64_t rb = C.record_bytes(nc, k);
                             if (rb >= 0) acc += 2.0 + (double)rb;
                             acc += C.mv_bits / 8.0;
@@ -177,6 +185,34 @@ extern "C" int hmlfc_touched_bytes(const hmlfc_stream *const *streams, int n_str
     for (int v = 0; v < n_views; v++)
         if (h_views[v].lf < 0 || h_views[v].lf >= n_streams || h_views[v].width < 0 || h_views[v].height < 0)
             return fail(HMLFC_E_INVALID_ARG, "view %d", v);
-    parallel_for(n_views, 0, [&](int64_t v) { h_bytes[v] = count_view(counters[h_views[v].lf], h_views[v]); });
+    parallel_for(n_views, 0, [&](int64_t v) {
+        Seen seen(streams[h_views[v].lf]->g);
+        h_bytes[v] = count_view(counters[h_views[v].lf], h_views[v], seen);
+    });
+    return HMLFC_OK;
+}
+
+extern "C" int hmlfc_touched_bytes_union(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views,
+                                         int n_views, double *h_total) {
+    if (!streams || n_streams < 1 || n_streams > HMLFC_MAX_STREAMS || n_views < 0 || !h_total ||
+        (n_views && !h_views))
+        return fail(HMLFC_E_INVALID_ARG, "bad arguments");
+    std::vector<Counter> counters;
+    std::vector<std::unique_ptr<Seen>> seen;
+    for (int k = 0; k < n_streams; k++) {
+        if (!streams[k]) return fail(HMLFC_E_INVALID_ARG, "stream %d is NULL", k);
+        counters.emplace_back(streams[k]->g, streams[k]->bytes.data());
+        seen.emplace_back(new Seen(streams[k]->g));
+    }
+    for (int v = 0; v < n_views; v++)
+        if (h_views[v].lf < 0 || h_views[v].lf >= n_streams || h_views[v].width < 0 || h_views[v].height < 0)
+            return fail(HMLFC_E_INVALID_ARG, "view %d", v);
+    std::vector<double> part(n_views, 0.0);
+    parallel_for(n_views, 0, [&](int64_t v) {
+        part[v] = count_view(counters[h_views[v].lf], h_views[v], *seen[h_views[v].lf]);
+    });
+    double t = 0.0;
+    for (double p : part) t += p;
+    *h_total = t;
     return HMLFC_OK;
 }

@@ -102,3 +102,22 @@ def test_touched_bytes_matches_oracle(tiny_streams, tiny_cfg):
     want = O.Stream(data).touched_bytes(views)
     got = H.touched_bytes([H.Stream(data)], views)
     assert np.allclose(got, want, rtol=0, atol=1e-6)
+
+
+@pytest.mark.gpu
+def test_touched_bytes_union(tiny_streams, tiny_cfg):
+    """Union over a call: one view alone equals its per-view count (and the
+    oracle's); a repeated view adds only its output; the union never exceeds
+    the sum of the per-view counts."""
+    c = tiny_cfg
+    data = tiny_streams[c.qstep].stream
+    geo = S.lf_geometry(c.nu, c.nv, c.width, c.height)
+    vs = S.random_views(22, geo, 3, [(48, 40)])
+    st = H.Stream(data)
+    one = S.views_to_array(vs[:1])
+    want = O.Stream(data).touched_bytes(one)[0]
+    assert abs(H.touched_bytes_union([st], one) - want) < 1e-6
+    twice = S.views_to_array([vs[0], vs[0]])
+    assert abs(H.touched_bytes_union([st], twice) - (want + 48 * 40 * 12)) < 1e-6
+    three = S.views_to_array(vs)
+    assert H.touched_bytes_union([st], three) <= float(np.sum(H.touched_bytes([st], three))) + 1e-6

@@ -106,7 +106,7 @@ def _views_mix(cfg, seed, n, sizes):
     return S.random_views(seed, geo, n, sizes)
 
 
-@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("path", [0, 1, 2])
 def test_render_tiny_within_tolerance(H, torch_cuda, tiny_streams, tiny_cfg, path):
     """The configured novel view (camera on the (u,v) plane at a random
     (u0, v0), (s,t) offset) plus random pinhole views of ragged sizes; both
@@ -128,19 +128,31 @@ def test_render_tiny_within_tolerance(H, torch_cuda, tiny_streams, tiny_cfg, pat
     assert np.max(np.abs(got - want)) <= RENDER_TOL
 
 
-def test_render_paths_identical(H, torch_cuda, tiny_streams, tiny_cfg):
-    """The staged and the direct path decode the same integers and blend in
-    the same order: bitwise equal outputs."""
+def test_render_paths_identical(H, torch_cuda, tiny_streams, tiny_cfg, ragged_lf):
+    """The cached, direct and per-tile paths decode the same integers and
+    blend in the same order: bitwise equal outputs; so does the cached path
+    when its capacity overflows and some blocks fall back to per-ray decode."""
     c = tiny_cfg
-    st = H.Stream(tiny_streams[c.qstep].stream)
-    arr = S.views_to_array(_views_mix(c, 32, 8, [(64, 64), (48, 40)]))
-    a = _render_gpu(H, torch_cuda, [st], arr)
-    H.set_render_path(1)
-    try:
-        b = _render_gpu(H, torch_cuda, [st], arr)
-    finally:
-        H.set_render_path(0)
-    assert np.array_equal(a, b)
+    cases = [(H.Stream(tiny_streams[c.qstep].stream), _views_mix(c, 32, 8, [(64, 64), (48, 40), (5, 70)]))]
+    geo2 = S.lf_geometry(5, 3, 37, 29)
+    d2 = O.encode(ragged_lf, 3, 8, 4, 2, t_ref=20, t_pred=30).stream
+    cases.append((H.Stream(d2), S.random_views(37, geo2, 5, [(40, 31), (17, 9)])))
+    for st, views in cases:
+        arr = S.views_to_array(views)
+        outs = []
+        try:
+            for path in (0, 1, 2):
+                H.set_render_path(path)
+                outs.append(_render_gpu(H, torch_cuda, [st], arr))
+            H.set_render_path(0)
+            for cap in (4 * 8 * 8 * 4, 0):        # four blocks, then none
+                H.set_block_cache_bytes(cap)
+                outs.append(_render_gpu(H, torch_cuda, [st], arr))
+        finally:
+            H.set_render_path(0)
+            H.set_block_cache_bytes(256 << 20)
+        for o in outs[1:]:
+            assert np.array_equal(outs[0], o)
 
 
 def test_render_grid_samples_exact(H, torch_cuda, tiny_streams, tiny_cfg):
