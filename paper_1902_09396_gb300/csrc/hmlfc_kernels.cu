@@ -302,40 +302,52 @@ __device__ __forceinline__ void ray_setup(const hmlfc_view &V, int nu, int nv, i
     const float X = (float)px + 0.5f, Y = (float)py + 0.5f;
     const float *h = V.H_uv;
     const float wu = h[6] * X + h[7] * Y + h[8];
-    const float u = (h[0] * X + h[1] * Y + h[2]) / wu;
-    const float v = (h[3] * X + h[4] * Y + h[5]) / wu;
+    const float u = __fdividef(h[0] * X + h[1] * Y + h[2], wu);
+    const float v = __fdividef(h[3] * X + h[4] * Y + h[5], wu);
     const float *g = V.H_st;
     const float ws = g[6] * X + g[7] * Y + g[8];
-    const float s = (g[0] * X + g[1] * Y + g[2]) / ws;
-    const float t = (g[3] * X + g[4] * Y + g[5]) / ws;
+    const float s = __fdividef(g[0] * X + g[1] * Y + g[2], ws);
+    const float t = __fdividef(g[3] * X + g[4] * Y + g[5], ws);
     r.fu = axis_nb(u, nu, r.i0, r.i1);
     r.fv = axis_nb(v, nv, r.j0, r.j1);
     r.fs = axis_nb(s, W, r.x0, r.x1);
     r.ft = axis_nb(t, H, r.y0, r.y1);
 }
 
-// Quadrilinear blend of the 16 samples, in a fixed order (a, b, xs, ys);
+// Byte k of a packed RGB8 sample as a float (exact: 2^23 + byte - 2^23).
+__device__ __forceinline__ float byte_f(uint32_t p, int k) {
+    return __uint_as_float(0x4B000000u | ((p >> (8 * k)) & 0xFFu)) - 8388608.0f;
+}
+
+// Quadrilinear blend of the 16 samples, separably: the 2 x 2 pixels of each
+// camera first (weights in s, t), then the 2 x 2 cameras (weights in u, v).
 // fetch(a, b, xs, ys, i, j, x, y) returns the packed RGB8 sample.
 template <class F>
 __device__ __forceinline__ void blend16(const Ray &r, F fetch, float out[3]) {
-    const float wu[2] = {1.0f - r.fu, r.fu}, wv[2] = {1.0f - r.fv, r.fv};
     const float ws[2] = {1.0f - r.fs, r.fs}, wt[2] = {1.0f - r.ft, r.ft};
+    const float wu[2] = {1.0f - r.fu, r.fu}, wv[2] = {1.0f - r.fv, r.fv};
     const int ii[2] = {r.i0, r.i1}, jj[2] = {r.j0, r.j1}, xx[2] = {r.x0, r.x1}, yy[2] = {r.y0, r.y1};
+    float wp[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) wp[q] = ws[q >> 1] * wt[q & 1];
     float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
 #pragma unroll
     for (int a = 0; a < 2; a++)
 #pragma unroll
-        for (int b = 0; b < 2; b++)
+        for (int b = 0; b < 2; b++) {
+            float c0 = 0.f, c1 = 0.f, c2 = 0.f;
 #pragma unroll
-            for (int xs = 0; xs < 2; xs++)
-#pragma unroll
-                for (int ys = 0; ys < 2; ys++) {
-                    const float w = wu[a] * wv[b] * ws[xs] * wt[ys];
-                    const uint32_t p = fetch(a, b, xs, ys, ii[a], jj[b], xx[xs], yy[ys]);
-                    acc0 += w * (float)(p & 0xFFu);
-                    acc1 += w * (float)((p >> 8) & 0xFFu);
-                    acc2 += w * (float)((p >> 16) & 0xFFu);
-                }
+            for (int q = 0; q < 4; q++) {
+                const uint32_t p = fetch(a, b, q >> 1, q & 1, ii[a], jj[b], xx[q >> 1], yy[q & 1]);
+                c0 = fmaf(wp[q], byte_f(p, 0), c0);
+                c1 = fmaf(wp[q], byte_f(p, 1), c1);
+                c2 = fmaf(wp[q], byte_f(p, 2), c2);
+            }
+            const float wc = wu[a] * wv[b];
+            acc0 = fmaf(wc, c0, acc0);
+            acc1 = fmaf(wc, c1, acc1);
+            acc2 = fmaf(wc, c2, acc2);
+        }
     const float inv = 1.0f / 255.0f;
     out[0] = acc0 * inv;
     out[1] = acc1 * inv;
@@ -890,49 +902,75 @@ __device__ Desc make_desc(const DevStream &S, const LevelTabs &T, const Blk<BS> 
     return D;
 }
 
+// Mark the (camera, block) pairs of one tile's footprint.  Under a
+// projective map with w > 0 over the tile, each coordinate's extremes over
+// the tile's pixel centres are at its corner pixels, so the 4 corner rays
+// bound the footprint; the box is widened by a small margin against fp32
+// rounding of interior rays (a pair missed all the same only sends its rays
+// to the direct decode).  A tile whose w is not positive at all corners is
+// marked ray by ray.
 template <int BS, int TW, int TH>
-__global__ void __launch_bounds__(TW *TH) k_mark(const __grid_constant__ DevStream S,
-                                                const __grid_constant__ LaunchViews LV, uint8_t *__restrict__ flags) {
-    constexpr int NT = TW * TH;
-    __shared__ int s_view;
-    __shared__ int s_red[NT / 32][8];
-    __shared__ int s_box[8];
-    if (threadIdx.x == 0) s_view = find_view(LV, blockIdx.x);
-    __syncthreads();
-    const hmlfc_view &V = LV.views[s_view];
+__global__ void __launch_bounds__(128) k_mark(const __grid_constant__ DevStream S,
+                                             const __grid_constant__ LaunchViews LV, int total_tiles,
+                                             uint8_t *__restrict__ flags) {
+    const int tile = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tile >= total_tiles) return;
+    const int vi = find_view(LV, tile);
+    const hmlfc_view &V = LV.views[vi];
     const int tiles_x = (V.width + TW - 1) / TW;
-    const int local = blockIdx.x - LV.tile_start[s_view];
-    const int px = (local % tiles_x) * TW + (int)threadIdx.x % TW;
-    const int py = (local / tiles_x) * TH + (int)threadIdx.x / TW;
-    const bool act = px < V.width && py < V.height;
-    Ray r;
-    ray_setup(V, S.nu, S.nv, S.W, S.H, act ? px : 0, act ? py : 0, r);
+    const int local = tile - LV.tile_start[vi];
+    const int x0 = (local % tiles_x) * TW, y0 = (local / tiles_x) * TH;
+    const int x1 = min(x0 + TW, V.width) - 1, y1 = min(y0 + TH, V.height) - 1;
     const Blk<BS> bk(S.B);
-    int red[8] = {act ? r.i0 : INT_MAX, act ? -r.i1 : INT_MAX, act ? r.j0 : INT_MAX, act ? -r.j1 : INT_MAX,
-                  act ? bk.div(r.x0) : INT_MAX, act ? -bk.div(r.x1) : INT_MAX, act ? bk.div(r.y0) : INT_MAX,
-                  act ? -bk.div(r.y1) : INT_MAX};
+    const float eps_uv = 1e-3f, eps_st = 1e-2f;
+    float lo[4] = {1e30f, 1e30f, 1e30f, 1e30f}, hi[4] = {-1e30f, -1e30f, -1e30f, -1e30f};
+    bool ok = true;
 #pragma unroll
-    for (int q = 0; q < 8; q++) red[q] = __reduce_min_sync(0xFFFFFFFFu, red[q]);
-    if ((threadIdx.x & 31) == 0) {
+    for (int q = 0; q < 4; q++) {
+        const float X = (float)((q & 1) ? x1 : x0) + 0.5f, Y = (float)((q & 2) ? y1 : y0) + 0.5f;
+        const float *h = V.H_uv, *g = V.H_st;
+        const float wu = h[6] * X + h[7] * Y + h[8], ws = g[6] * X + g[7] * Y + g[8];
+        ok &= wu > 0.f && ws > 0.f;
+        const float c[4] = {__fdividef(h[0] * X + h[1] * Y + h[2], wu), __fdividef(h[3] * X + h[4] * Y + h[5], wu),
+                            __fdividef(g[0] * X + g[1] * Y + g[2], ws), __fdividef(g[3] * X + g[4] * Y + g[5], ws)};
 #pragma unroll
-        for (int q = 0; q < 8; q++) s_red[threadIdx.x >> 5][q] = red[q];
+        for (int k = 0; k < 4; k++) {
+            lo[k] = fminf(lo[k], c[k]);
+            hi[k] = fmaxf(hi[k], c[k]);
+        }
     }
-    __syncthreads();
-    if (threadIdx.x < 8) {
-        int m = INT_MAX;
-        for (int w = 0; w < NT / 32; w++) m = min(m, s_red[w][threadIdx.x]);
-        s_box[threadIdx.x] = (threadIdx.x & 1) ? -m : m;
+    const int n[4] = {S.nu, S.nv, S.W, S.H};
+    int bl[4], bh[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const float e = k < 2 ? eps_uv : eps_st;
+        int a0, a1, b0, b1;
+        axis_nb(lo[k] - e, n[k], a0, a1);
+        axis_nb(hi[k] + e, n[k], b0, b1);
+        bl[k] = a0;
+        bh[k] = b1;
+        if (!(lo[k] == lo[k]) || !(hi[k] == hi[k])) ok = false;   // NaN
     }
-    __syncthreads();
-    const int ncu = s_box[1] - s_box[0] + 1, ncv = s_box[3] - s_box[2] + 1;
-    const int nbu = s_box[5] - s_box[4] + 1, nbv = s_box[7] - s_box[6] + 1;
-    const int nb = nbu * nbv;
-    for (int e = threadIdx.x; e < ncu * ncv * nb; e += NT) {
-        const int cam = e / nb, blk = e - cam * nb;
-        const int i = s_box[0] + cam / ncv, j = s_box[2] + cam % ncv;
-        const int bx = s_box[4] + blk % nbu, by = s_box[6] + blk / nbu;
-        flags[((size_t)i * S.nv + j) * S.nblocks + (size_t)by * S.nbx + bx] = 1;
+    if (!ok) {                              // ray by ray
+        for (int py = y0; py <= y1; py++)
+            for (int px = x0; px <= x1; px++) {
+                Ray r;
+                ray_setup(V, S.nu, S.nv, S.W, S.H, px, py, r);
+                const int ci[2] = {r.i0, r.i1}, cj[2] = {r.j0, r.j1};
+                const int kb[4] = {bk.div(r.y0) * S.nbx + bk.div(r.x0), bk.div(r.y0) * S.nbx + bk.div(r.x1),
+                                   bk.div(r.y1) * S.nbx + bk.div(r.x0), bk.div(r.y1) * S.nbx + bk.div(r.x1)};
+                for (int q = 0; q < 16; q++)
+                    flags[((size_t)ci[q >> 3] * S.nv + cj[(q >> 2) & 1]) * S.nblocks + kb[q & 3]] = 1;
+            }
+        return;
     }
+    const int bx0 = bk.div(bl[2]), bx1 = bk.div(bh[2]), by0 = bk.div(bl[3]), by1 = bk.div(bh[3]);
+    for (int i = bl[0]; i <= bh[0]; i++)
+        for (int j = bl[1]; j <= bh[1]; j++) {
+            uint8_t *f = flags + ((size_t)i * S.nv + j) * S.nblocks;
+            for (int by = by0; by <= by1; by++)
+                for (int bx = bx0; bx <= bx1; bx++) f[by * S.nbx + bx] = 1;
+        }
 }
 
 // Compact the flags into cache slots, cluster by cluster: a cluster key is a
@@ -1021,13 +1059,14 @@ __global__ void __launch_bounds__(256) k_decode_blocks(const __grid_constant__ D
                                                       const unsigned long long *__restrict__ counters,
                                                       uint32_t *__restrict__ cache) {
     constexpr int kMaxGroup = 16;                 // items per pass (B = 4)
+    constexpr int kMinGroup = 4;                  // items per pass at least (amortises the descriptor phase)
     constexpr int kDescPer = (kMaxLevels - 1) * 3 + 4 * 3;
     __shared__ LevelTabs T;
     __shared__ Desc s_desc[kMaxGroup * kDescPer];
     load_tabs(S, T);
     const Blk<BS> bk(S.B);
     const int B = bk.size(), B2 = B * B;
-    const int G = max(1, min(kMaxGroup, (int)blockDim.x / B2));
+    const int G = max(B2 <= 256 ? kMinGroup : 1, min(kMaxGroup, (int)blockDim.x / B2));
     const int L = S.L;
     const uint32_t n = (uint32_t)(__ldg(counters) >> 32);
     const size_t plane = (size_t)S.W * S.H;
@@ -1104,8 +1143,17 @@ __global__ void __launch_bounds__(256) k_decode_blocks(const __grid_constant__ D
 // Blend of one ray whose samples are decoded directly (kept out of line so
 // that the cached fast path keeps its registers).
 template <int BS>
-__device__ __noinline__ void blend_direct(const DevStream &S, const LevelTabs &T, const Blk<BS> &bk, const Ray &r,
-                                          float o[3]) {
+__device__ __noinline__ void blend_direct(const DevStream &S, const Blk<BS> &bk, const Ray &r, float o[3]) {
+    LevelTabs T;
+    for (int t = 0; t <= kMaxLevels; t++) {
+        T.gu[t] = S.gu[t];
+        T.gv[t] = S.gv[t];
+        if (t < kMaxLevels) {
+            T.nc_base[t] = S.nc_base[t];
+            T.ref_base[t] = S.ref_base[t];
+            T.pred_base[t] = S.pred_base[t];
+        }
+    }
     blend16(r, [&](int, int, int, int, int i, int j, int x, int y) { return sample_direct(S, T, bk, i, j, x, y); }, o);
 }
 
@@ -1114,14 +1162,10 @@ __global__ void __launch_bounds__(TW *TH) k_render_cached(const __grid_constant_
                                                          const __grid_constant__ LaunchViews LV,
                                                          const uint32_t *__restrict__ slotmap,
                                                          const uint32_t *__restrict__ cache, float *__restrict__ out) {
-    __shared__ LevelTabs T;
-    __shared__ int s_view;
-    load_tabs(S, T);
-    if (threadIdx.x == 0) s_view = find_view(LV, blockIdx.x);
-    __syncthreads();
-    const hmlfc_view &V = LV.views[s_view];
+    const int vi = find_view(LV, blockIdx.x);      // uniform over the CTA
+    const hmlfc_view &V = LV.views[vi];
     const int tiles_x = (V.width + TW - 1) / TW;
-    const int local = blockIdx.x - LV.tile_start[s_view];
+    const int local = blockIdx.x - LV.tile_start[vi];
     const int px = (local % tiles_x) * TW + (int)threadIdx.x % TW;
     const int py = (local / tiles_x) * TH + (int)threadIdx.x / TW;
     if (px >= V.width || py >= V.height) return;
@@ -1156,7 +1200,7 @@ __global__ void __launch_bounds__(TW *TH) k_render_cached(const __grid_constant_
         // sample order of blend16: q = a*8 + b*4 + xs*2 + ys  ->  cam a*2+b, corner xs*2+ys
         blend16(r, [&](int a, int b, int xs, int ys, int, int, int, int) { return val[a * 8 + b * 4 + xs * 2 + ys]; }, o);
     } else {
-        blend_direct(S, T, bk, r, o);      // a sample beyond the cache capacity: decode this ray directly
+        blend_direct(S, bk, r, o);         // a sample beyond the cache capacity: decode this ray directly
     }
     float *dst = out + V.out_offset + ((size_t)py * V.width + px) * 3;
     dst[0] = o[0];
@@ -1221,7 +1265,7 @@ cudaError_t launch_render(const DevStream &ds, const LaunchViews &lv, int total_
 
 cudaError_t launch_mark(const DevStream &ds, const LaunchViews &lv, int total_tiles, uint8_t *flags, cudaStream_t st) {
     if (total_tiles <= 0) return cudaSuccess;
-    HMLFC_DISPATCH_B(ds.B, (k_mark<BS, 16, 16><<<total_tiles, 256, 0, st>>>(ds, lv, flags)));
+    HMLFC_DISPATCH_B(ds.B, (k_mark<BS, 16, 16><<<(total_tiles + 127) / 128, 128, 0, st>>>(ds, lv, total_tiles, flags)));
     return cudaGetLastError();
 }
 
