@@ -169,6 +169,40 @@ int hmlfc_render_views(const hmlfc_stream *const *streams, int n_streams, const 
                        float *d_out, void *cuda_stream);
 
 /*
+ * hmlfc_render_views without any memory allocation (the paper has no
+ * counterpart: this is an interface for callers of this library).
+ *
+ * Some callers cannot allocate device memory at the time they render: a
+ * frame loop with a hard deadline that must not stall on the allocator or
+ * fail on fragmentation midway, a host function or stream callback (where
+ * CUDA API calls that allocate are not allowed), code running under a
+ * caching allocator that has to account for every byte, or code capturing
+ * work into a CUDA graph in a capture mode that forbids cudaMalloc.  This
+ * entry point gives them the cached render of hmlfc_render_views, with the
+ * same results, using only memory the library reserved when it was loaded:
+ * a fixed device array of 32 MiB (HMLFC_FIXED_SCRATCH_BYTES), which every GPU
+ * that loads the library holds until the process exits.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *
+ * - Set-up: the first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ * - Limit: the block index of a stream (5 bytes per (camera, block) pair plus
+ *   16 bytes per (level-1 node, block) pair, plus one decoded block) must fit
+ *   the array; a larger stream is rejected with HMLFC_E_UNSUPPORTED and a
+ *   message, and hmlfc_render_views should be used instead.  Blocks beyond
+ *   the space left for the decoded-block cache are decoded per ray (same
+ *   results, slower).
+ * - Sharing: every call uses the same array and leaves its contents behind;
+ *   each call clears what must start at zero.  Calls whose GPU work overlaps
+ *   (on different CUDA streams, or from several host threads without
+ *   ordering) race on the array and must be serialised by the caller.
+ */
+#define HMLFC_FIXED_SCRATCH_BYTES (32u << 20)
+int hmlfc_render_views_noalloc(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views,
+                               int n_views, float *d_out, void *cuda_stream);
+
+/*
  * Differentiable relaxation (for gradient-based refinement of the residuals):
  * the same render with real-valued coefficients -- exact bilinear weights
  * instead of the >> 4 rounding, YCoCg-R inverse with /2 instead of >> 1, no

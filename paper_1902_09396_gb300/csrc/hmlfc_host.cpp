@@ -253,6 +253,30 @@ int view_chunks(const hmlfc_view *views, int n_views, int lf, std::vector<Launch
     return HMLFC_OK;
 }
 
+// The next launch chunk of stream lf's views, scanning from *pos, without
+// any allocation; returns the number of views in the chunk (0 at the end).
+int next_chunk(const hmlfc_view *views, int n_views, int lf, int *pos, LaunchViews &lv, int &tiles) {
+    std::memset(&lv, 0, sizeof lv);
+    lv.tile_w = 16;
+    lv.tile_h = 16;
+    int64_t t = 0;
+    int k = 0;
+    while (*pos < n_views && k < kMaxViewsPerLaunch) {
+        const hmlfc_view &V = views[*pos];
+        (*pos)++;
+        if (V.lf != lf || V.width <= 0 || V.height <= 0) continue;
+        lv.tile_start[k] = (int)t;
+        lv.views[k] = V;
+        k++;
+        t += (int64_t)((V.width + 15) / 16) * ((V.height + 15) / 16);
+        if (t >= INT32_MAX) return -1;
+    }
+    lv.n_views = k;
+    lv.tile_start[k] = (int)t;
+    tiles = (int)t;
+    return k;
+}
+
 // Launch one kernel family over the views of each stream, chunk by chunk.
 template <class F>
 int for_view_chunks(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *views, int n_views, F launch) {
@@ -494,6 +518,64 @@ int hmlfc_render_views(const hmlfc_stream *const *streams, int n_streams, const 
             const cudaError_t e = launch_render(streams[lf]->ds, chunks[c], tiles[c], d_out, path == 1 ? 1 : 0, st);
             if (e != cudaSuccess) return cuda_fail(e, "render launch");
         }
+    }
+    return HMLFC_OK;
+}
+
+// Allocation-free variant of the cached render: the decoded-block cache, its
+// slot map, flags and work list live in the fixed device array set up by
+// fixed_scratch() (hmlfc_kernels.cu).  Nothing is allocated, on the device
+// or on the host.
+int hmlfc_render_views_noalloc(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views,
+                               int n_views, float *d_out, void *cuda_stream) {
+    int rc = check_views(streams, n_streams, h_views, n_views);
+    if (rc != HMLFC_OK) return rc;
+    if (n_views > 0 && !d_out) return fail(HMLFC_E_INVALID_ARG, "d_out is NULL");
+    if (n_views == 0) return HMLFC_OK;
+    const int dev = streams[0]->device;
+    DeviceGuard guard(dev);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    void *scratch = nullptr;
+    cudaError_t e = fixed_scratch(dev, &scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "fixed scratch set-up");
+    uint8_t *base = static_cast<uint8_t *>(scratch);
+    LaunchViews lv;
+    int tiles = 0;
+    for (int lf = 0; lf < n_streams; lf++) {
+        const hmlfc_stream *s = streams[lf];
+        const Geometry &g = s->g;
+        const size_t n_keys = (size_t)g.nu * g.nv * g.nblocks;
+        const size_t n_ck = (size_t)g.gu[1] * g.gv[1] * g.nblocks;
+        const size_t blk_bytes = (size_t)g.B * g.B * 4;
+        const size_t o_slot = up256(n_keys), o_items = up256(o_slot + n_keys * 4), o_count = up256(o_items + n_ck * 16),
+                     o_cache = up256(o_count + 8);
+        if (o_cache + blk_bytes > kFixedScratchBytes)
+            return fail(HMLFC_E_UNSUPPORTED,
+                        "stream %d needs %zu bytes of block index in the fixed scratch, which holds %zu; "
+                        "use hmlfc_render_views",
+                        lf, o_cache + blk_bytes, kFixedScratchBytes);
+        const uint32_t capacity = (uint32_t)std::min<size_t>(n_keys, (kFixedScratchBytes - o_cache) / blk_bytes);
+        uint8_t *flags = base;
+        uint32_t *slotmap = reinterpret_cast<uint32_t *>(base + o_slot);
+        uint4 *items = reinterpret_cast<uint4 *>(base + o_items);
+        unsigned long long *counters = reinterpret_cast<unsigned long long *>(base + o_count);
+        uint32_t *cache = reinterpret_cast<uint32_t *>(base + o_cache);
+        // the array keeps the previous call's contents: clear what must start at zero
+        e = cudaMemsetAsync(flags, 0, n_keys, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 8, st);
+        int pos = 0, k;
+        while (e == cudaSuccess && (k = next_chunk(h_views, n_views, lf, &pos, lv, tiles)) != 0) {
+            if (k < 0) return fail(HMLFC_E_INVALID_ARG, "too many tiles in one launch");
+            e = launch_mark(s->ds, lv, tiles, flags, st);
+        }
+        if (e == cudaSuccess) e = launch_assign(s->ds, flags, slotmap, items, counters, capacity, st);
+        if (e == cudaSuccess) e = launch_decode_blocks(s->ds, items, counters, cache, sm_count(dev) * 8, st);
+        pos = 0;
+        while (e == cudaSuccess && (k = next_chunk(h_views, n_views, lf, &pos, lv, tiles)) != 0) {
+            if (k < 0) return fail(HMLFC_E_INVALID_ARG, "too many tiles in one launch");
+            e = launch_render_cached(s->ds, lv, tiles, slotmap, cache, d_out, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "allocation-free render");
     }
     return HMLFC_OK;
 }

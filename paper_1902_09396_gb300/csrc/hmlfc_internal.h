@@ -49,6 +49,15 @@ struct LaunchViews {
     hmlfc_view views[kMaxViewsPerLaunch];
 };
 
+// Size of the fixed device array behind hmlfc_render_views_noalloc.
+constexpr size_t kFixedScratchBytes = (size_t)32 << 20;
+static_assert(kFixedScratchBytes == HMLFC_FIXED_SCRATCH_BYTES, "fixed scratch size of the public header");
+constexpr int kMaxDevices = 64;
+
+// Device address of the fixed scratch array on `device`, which must be the
+// current device; looked up on the first call per device.
+cudaError_t fixed_scratch(int device, void **ptr);
+
 // Launchers implemented in hmlfc_kernels.cu.
 cudaError_t launch_decode_tiles(const DevStream &ds, const uint32_t *d_src, int n_tiles, int16_t *d_tiles,
                                 cudaStream_t st);

@@ -12,6 +12,7 @@
 
 #include <climits>
 #include <cstdint>
+#include <mutex>
 
 #include "hmlfc_internal.h"
 
@@ -1314,6 +1315,37 @@ cudaError_t launch_dequant(const DevStream &ds, int64_t n_nc, float *coeff, floa
     dim3 grid((unsigned)(gx < 4096 ? gx : 4096), (unsigned)(n_nc + n_roots * 3));
     HMLFC_DISPATCH_B(ds.B, (k_dequant<BS><<<grid, 256, 0, st>>>(ds, n_nc, coeff, root)));
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Fixed scratch of the allocation-free render entry point
+// ---------------------------------------------------------------------------
+//
+// The decoded-block cache of hmlfc_render_views_noalloc lives in this
+// file-scope device array instead of memory allocated per call.  Every GPU
+// that loads the library holds it until the process exits.  In host code the
+// name is only a host-side stand-in for the symbol; the device address of
+// each device's copy is looked up once, with that device current, by
+// fixed_scratch() below and then passed to the kernels.
+
+static __device__ __align__(256) unsigned char g_fixed_scratch[kFixedScratchBytes];
+
+namespace {
+std::mutex g_fixed_mu;
+void *g_fixed_ptr[kMaxDevices] = {};
+}  // namespace
+
+cudaError_t fixed_scratch(int device, void **ptr) {
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_fixed_mu);
+    if (!g_fixed_ptr[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_fixed_scratch);
+        if (e != cudaSuccess) return e;
+        g_fixed_ptr[device] = p;
+    }
+    *ptr = g_fixed_ptr[device];
+    return cudaSuccess;
 }
 
 }  // namespace hmlfc
