@@ -272,9 +272,11 @@ int hmlfc_touched_bytes(const hmlfc_stream *const *streams, int n_streams, const
                         double *h_bytes);
 
 /* The same count over the whole call: every distinct item once, however
- * many views reach it, plus every view's output (one total into h_total). */
+ * many views reach it, plus every view's output (one total into h_total);
+ * h_cam_blocks (may be NULL) receives the number of distinct (camera, block)
+ * pairs that hold a reached sample. */
 int hmlfc_touched_bytes_union(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views,
-                              int n_views, double *h_total);
+                              int n_views, double *h_total, double *h_cam_blocks);
 
 /*
  * Render strategy (process-wide).  0 (default): decode every (camera, block)
@@ -291,6 +293,14 @@ int hmlfc_set_render_path(int path);
 /* Capacity of the decoded-block cache of one render call, in bytes
  * (default 256 MiB; B * B * 4 bytes per block; 0 disables the cache). */
 int hmlfc_set_block_cache_bytes(size_t bytes);
+
+/*
+ * Measurement aid (process-wide): four caller-created CUDA events that the
+ * cached render records on the call's stream before marking, before the
+ * block decode, before the blend and at the end, so that each phase can be
+ * timed with cudaEventElapsedTime; NULL stops the recording.
+ */
+int hmlfc_set_phase_events(void *const *events);
 
 const char *hmlfc_last_error(void);
 

@@ -81,9 +81,10 @@ def lib() -> C.CDLL:
     L.hmlfc_free_host.argtypes = [P]
     L.hmlfc_free_host.restype = None
     L.hmlfc_touched_bytes.argtypes = [P, I, P, I, P]
-    L.hmlfc_touched_bytes_union.argtypes = [P, I, P, I, P]
+    L.hmlfc_touched_bytes_union.argtypes = [P, I, P, I, P, P]
     L.hmlfc_set_render_path.argtypes = [I]
     L.hmlfc_set_block_cache_bytes.argtypes = [SZ]
+    L.hmlfc_set_phase_events.argtypes = [P]
     _lib = L
     return L
 
@@ -225,6 +226,16 @@ def set_render_path(path: int):
     _check(lib().hmlfc_set_render_path(int(path)))
 
 
+def set_phase_events(events):
+    """Record four torch.cuda.Events at the cached render's phase boundaries
+    (before mark, before decode, before blend, end); None stops."""
+    if events is None:
+        _check(lib().hmlfc_set_phase_events(None))
+        return
+    arr = (C.c_void_p * 4)(*[int(e.cuda_event) for e in events])
+    _check(lib().hmlfc_set_phase_events(arr))
+
+
 def set_block_cache_bytes(n: int):
     _check(lib().hmlfc_set_block_cache_bytes(int(n)))
 
@@ -255,12 +266,15 @@ def requantize(stream: Stream, coeff: np.ndarray, root: np.ndarray) -> bytes:
     return data
 
 
-def touched_bytes_union(streams, views) -> float:
-    """Compulsory bytes of a whole call: distinct items counted once."""
+def touched_bytes_union(streams, views, with_blocks: bool = False):
+    """Compulsory bytes of a whole call: distinct items counted once; with
+    with_blocks also the number of distinct (camera, block) pairs reached."""
     va = _views_array(views)
     out = C.c_double()
-    _check(lib().hmlfc_touched_bytes_union(_streams_array(streams), len(streams), va, len(va), C.byref(out)))
-    return out.value
+    nb = C.c_double()
+    _check(lib().hmlfc_touched_bytes_union(_streams_array(streams), len(streams), va, len(va), C.byref(out),
+                                           C.byref(nb)))
+    return (out.value, nb.value) if with_blocks else out.value
 
 
 def touched_bytes(streams, views) -> np.ndarray:

@@ -21,6 +21,11 @@ namespace {
 thread_local std::string g_err;
 int g_render_path = 0;                      // 0 cached blocks, 1 direct per ray, 2 per-tile staging
 size_t g_cache_bytes = (size_t)256 << 20;   // decoded-block cache of one render call
+cudaEvent_t g_phase_ev[4] = {nullptr, nullptr, nullptr, nullptr};   // optional phase markers of the cached render
+
+void phase_mark(int k, cudaStream_t st) {
+    if (g_phase_ev[k]) cudaEventRecord(g_phase_ev[k], st);
+}
 
 }  // namespace
 
@@ -328,13 +333,17 @@ int render_cached(const hmlfc_stream *s, const std::vector<LaunchViews> &chunks,
     uint4 *items = reinterpret_cast<uint4 *>(b + o_items);
     unsigned long long *counters = reinterpret_cast<unsigned long long *>(b + o_count);
     uint32_t *cache = reinterpret_cast<uint32_t *>(b + o_cache);
+    phase_mark(0, st);
     cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)n_keys, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 8, st);
     for (size_t c = 0; c < chunks.size() && e == cudaSuccess; c++) e = launch_mark(s->ds, chunks[c], tiles[c], flags, st);
     if (e == cudaSuccess) e = launch_assign(s->ds, flags, slotmap, items, counters, capacity, st);
+    phase_mark(1, st);
     if (e == cudaSuccess) e = launch_decode_blocks(s->ds, items, counters, cache, sm_count(s->device) * 8, st);
+    phase_mark(2, st);
     for (size_t c = 0; c < chunks.size() && e == cudaSuccess; c++)
         e = launch_render_cached(s->ds, chunks[c], tiles[c], slotmap, cache, d_out, st);
+    phase_mark(3, st);
     const cudaError_t ef = cudaFreeAsync(base, st);
     if (e == cudaSuccess) e = ef;
     return e == cudaSuccess ? HMLFC_OK : cuda_fail(e, "cached render");
@@ -349,6 +358,11 @@ const char *hmlfc_last_error(void) { return g_err.c_str(); }
 int hmlfc_set_render_path(int path) {
     if (path < 0 || path > 2) return fail(HMLFC_E_INVALID_ARG, "render path %d", path);
     g_render_path = path;
+    return HMLFC_OK;
+}
+
+int hmlfc_set_phase_events(void *const *events) {
+    for (int k = 0; k < 4; k++) g_phase_ev[k] = events ? static_cast<cudaEvent_t>(events[k]) : nullptr;
     return HMLFC_OK;
 }
 

@@ -193,7 +193,7 @@ extern "C" int hmlfc_touched_bytes(const hmlfc_stream *const *streams, int n_str
 }
 
 extern "C" int hmlfc_touched_bytes_union(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views,
-                                         int n_views, double *h_total) {
+                                         int n_views, double *h_total, double *h_cam_blocks) {
     if (!streams || n_streams < 1 || n_streams > HMLFC_MAX_STREAMS || n_views < 0 || !h_total ||
         (n_views && !h_views))
         return fail(HMLFC_E_INVALID_ARG, "bad arguments");
@@ -214,5 +214,26 @@ extern "C" int hmlfc_touched_bytes_union(const hmlfc_stream *const *streams, int
     double t = 0.0;
     for (double p : part) t += p;
     *h_total = t;
+    if (h_cam_blocks) {
+        // distinct (camera, block) pairs holding a reached sample
+        double nb = 0.0;
+        for (int k = 0; k < n_streams; k++) {
+            const Geometry &g = streams[k]->g;
+            const size_t plane = (size_t)g.W * g.H;
+            for (int64_t cam = 0; cam < (int64_t)g.nu * g.nv; cam++)
+                for (int blk = 0; blk < g.nblocks; blk++) {
+                    const int x0 = (blk % g.nbx) * g.B, y0 = (blk / g.nbx) * g.B;
+                    const int bw = std::min(g.B, g.W - x0), bh = std::min(g.B, g.H - y0);
+                    bool any = false;
+                    for (int y = y0; y < y0 + bh && !any; y++)
+                        for (int x = x0; x < x0 + bw && !any; x++) {
+                            const size_t sk = (size_t)cam * plane + (size_t)y * g.W + x;
+                            any = (seen[k]->sample.w[sk >> 6].load(std::memory_order_relaxed) >> (sk & 63)) & 1u;
+                        }
+                    nb += any ? 1.0 : 0.0;
+                }
+        }
+        *h_cam_blocks = nb;
+    }
     return HMLFC_OK;
 }
