@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU baseline sample")
     ap.add_argument("--traffic-json", default=os.path.join(ROOT, "profiles", "decode_traffic.json"))
     ap.add_argument("--path", type=int, default=0, help="render path: 0 cached blocks, 1 direct, 2 per-tile")
-    ap.add_argument("--form", default="plain", choices=["plain", "diff"],
+    ap.add_argument("--form", default="plain", choices=["plain", "diff", "batched"],
                     help="plain: the paper-scale render step (default); diff: 200 Adam steps of the "
                          "differentiable form")
     return ap.parse_args()
@@ -239,10 +239,89 @@ def run_diff(args):
     }), flush=True)
 
 
+def run_batched(args):
+    """Batched form: 8 light fields of uneven size, 256 novel views of mixed
+    resolution (256^2-1024^2) rendered in one pass (persistent kernels,
+    tuned by the autotuner, replayed from a CUDA graph), against the plain
+    per-view launch (one render call per view) on the same views."""
+    import torch
+    import paper_1902_09396_gb300 as H
+    from paper_1902_09396_gb300.autotune import tune
+
+    cfgs = synthlf.batched_workload()
+    t0 = time.time()
+    streams, raw_px = [], 0
+    for c in cfgs:
+        lf = synthlf.make_lf(c.seed, c.nu, c.nv, c.width, c.height, c.n_planes, c.disp_max, c.texture)
+        raw_px += lf.size // 3
+        streams.append(H.Stream(H.encode(lf, c.levels, c.block, c.search, args.qstep, t_ref=400, t_pred=800)))
+        del lf
+    t_setup = time.time() - t0
+    views = synthlf.batched_views(4, cfgs, 256)
+    arr = synthlf.views_to_array(views)
+    rays = int(np.sum(arr["width"].astype(np.int64) * arr["height"]))
+    out = torch.empty(H.out_size(arr), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    steps = min(args.steps, 20)
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 2)):
+            fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / steps
+
+    single = [arr[k:k + 1].copy() for k in range(len(arr))]
+    for k in range(len(single)):
+        single[k]["out_offset"] = arr[k]["out_offset"]
+    ms_per_view = timed(lambda: [H.render_views(streams, single[k], out) for k in range(len(single))])
+    ms_views = timed(lambda: H.render_views(streams, arr, out))
+    tuned = tune(streams, arr, out)
+    ms_batch = timed(lambda: H.render_batch(streams, arr, out))
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        H.render_batch(streams, arr, out)
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        H.render_batch(streams, arr, out)
+    ms_graph = timed(graph.replay)
+    n = len(arr)
+    print(json.dumps({
+        "metric": "Mrays/s of 256 mixed-resolution novel views over 8 light fields (batched form, CUDA graph)",
+        "value": rays / (ms_graph / 1000.0) / 1e6, "unit": "Mrays/s", "n_gpus": 1, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32 decode, fp32 blend", "data": "synthetic",
+        "config": {"workload": "8 light fields " + ", ".join(f"{c.nu}x{c.nv}x{c.width}^2 L={c.levels}" for c in cfgs)
+                               + f"; q={args.qstep} T=(400,800); {n} views 256^2-1024^2 ({rays / 1e6:.1f} Mrays)",
+                   "l2": "flushed before every timed step"},
+        "views_per_s": n / (ms_graph / 1000.0),
+        "modes_ms": {"per_view_launch": ms_per_view, "render_views": ms_views, "render_batch": ms_batch,
+                     "render_batch_graph": ms_graph},
+        "speedup_vs_per_view_launch": ms_per_view / ms_graph,
+        "autotune": tuned, "setup_s": t_setup, "raw_gb": raw_px * 3 / 1e9,
+        "gpu_launches": 4,
+    }), flush=True)
+
+
 def main():
     args = parse()
     if args.form == "diff":
         run_diff(args)
+        return
+    if args.form == "batched":
+        run_batched(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -85,6 +85,8 @@ def lib() -> C.CDLL:
     L.hmlfc_set_render_path.argtypes = [I]
     L.hmlfc_set_block_cache_bytes.argtypes = [SZ]
     L.hmlfc_set_phase_events.argtypes = [P]
+    L.hmlfc_render_batch.argtypes = [P, I, P, I, P, P]
+    L.hmlfc_set_batch_tuning.argtypes = [I, I, I, SZ]
     _lib = L
     return L
 
@@ -195,6 +197,22 @@ def render_views(streams, views, out=None, cuda_stream=None):
     _check(lib().hmlfc_render_views(_streams_array(streams), len(streams), va, len(va), _ptr(out),
                                     _stream_handle(cuda_stream)))
     return out
+
+
+def render_batch(streams, views, out=None, cuda_stream=None):
+    """Batched form: every view of every stream in one pass (persistent
+    kernels, graph-capturable); same output as render_views."""
+    import torch
+    va = _views_array(views)
+    if out is None:
+        out = torch.empty(out_size(views), dtype=torch.float32, device=torch.device("cuda", streams[0].device))
+    _check(lib().hmlfc_render_batch(_streams_array(streams), len(streams), va, len(va), _ptr(out),
+                                    _stream_handle(cuda_stream)))
+    return out
+
+
+def set_batch_tuning(tile_shape: int = 0, group: int = 4, ctas_per_sm: int = 8, cache_bytes: int = 0):
+    _check(lib().hmlfc_set_batch_tuning(int(tile_shape), int(group), int(ctas_per_sm), int(cache_bytes)))
 
 
 def render_views_relaxed(streams, coeffs, roots, views, out=None, cuda_stream=None):

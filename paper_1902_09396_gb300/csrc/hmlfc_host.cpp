@@ -23,6 +23,13 @@ int g_render_path = 0;                      // 0 cached blocks, 1 direct per ray
 size_t g_cache_bytes = (size_t)256 << 20;   // decoded-block cache of one render call
 cudaEvent_t g_phase_ev[4] = {nullptr, nullptr, nullptr, nullptr};   // optional phase markers of the cached render
 
+struct BatchTuning {
+    int tile_shape = 0;                   // 0: 16x16, 1: 32x8, 2: 8x8 rays per tile
+    int group = 4;                        // decode items per pass
+    int ctas_per_sm = 8;                  // persistent CTAs per SM
+    size_t cache_bytes = (size_t)2 << 30; // decoded-block cache of one batched call
+} g_batch;
+
 void phase_mark(int k, cudaStream_t st) {
     if (g_phase_ev[k]) cudaEventRecord(g_phase_ev[k], st);
 }
@@ -592,6 +599,90 @@ int hmlfc_render_views_noalloc(const hmlfc_stream *const *streams, int n_streams
         if (e != cudaSuccess) return cuda_fail(e, "allocation-free render");
     }
     return HMLFC_OK;
+}
+
+int hmlfc_set_batch_tuning(int tile_shape, int group, int ctas_per_sm, size_t cache_bytes) {
+    if (tile_shape < 0 || tile_shape > 2 || group < 1 || group > 8 || ctas_per_sm < 1 || ctas_per_sm > 32)
+        return fail(HMLFC_E_INVALID_ARG, "batch tuning (%d, %d, %d)", tile_shape, group, ctas_per_sm);
+    g_batch.tile_shape = tile_shape;
+    g_batch.group = group;
+    g_batch.ctas_per_sm = ctas_per_sm;
+    if (cache_bytes) g_batch.cache_bytes = cache_bytes;
+    return HMLFC_OK;
+}
+
+int hmlfc_render_batch(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views, int n_views,
+                       float *d_out, void *cuda_stream) {
+    int rc = check_views(streams, n_streams, h_views, n_views);
+    if (rc != HMLFC_OK) return rc;
+    if (n_views > 0 && !d_out) return fail(HMLFC_E_INVALID_ARG, "d_out is NULL");
+    if (n_views == 0) return HMLFC_OK;
+    for (int k = 1; k < n_streams; k++)
+        if (streams[k]->g.B != streams[0]->g.B)   // one kernel instantiation per call: equal block sizes only
+            return hmlfc_render_views(streams, n_streams, h_views, n_views, d_out, cuda_stream);
+    const int dev = streams[0]->device;
+    DeviceGuard guard(dev);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int TW = g_batch.tile_shape == 1 ? 32 : (g_batch.tile_shape == 2 ? 8 : 16);
+    const int TH = g_batch.tile_shape == 1 ? 8 : (g_batch.tile_shape == 2 ? 8 : 16);
+    // the host image: header | light fields | views | tile prefix
+    std::vector<hmlfc_view> views;
+    std::vector<int> tile_start;
+    int64_t tiles = 0;
+    for (int v = 0; v < n_views; v++) {
+        const hmlfc_view &V = h_views[v];
+        if (V.width <= 0 || V.height <= 0) continue;
+        views.push_back(V);
+        tile_start.push_back((int)tiles);
+        tiles += (int64_t)((V.width + TW - 1) / TW) * ((V.height + TH - 1) / TH);
+        if (tiles >= INT32_MAX) return fail(HMLFC_E_INVALID_ARG, "too many tiles in one call");
+    }
+    tile_start.push_back((int)tiles);
+    if (views.empty()) return HMLFC_OK;
+    int64_t n_keys = 0, n_ck = 0;
+    const size_t lf_bytes = batch_lf_bytes(), hdr_bytes = batch_hdr_bytes();
+    auto a16 = [](size_t v) { return (v + 15) & ~(size_t)15; };
+    int offs[4];
+    offs[0] = 0;
+    offs[1] = (int)a16(hdr_bytes);
+    offs[2] = (int)a16(offs[1] + lf_bytes * n_streams);
+    offs[3] = (int)a16(offs[2] + sizeof(hmlfc_view) * views.size());
+    const size_t img_bytes = a16(offs[3] + sizeof(int) * tile_start.size());
+    std::vector<unsigned char> img(img_bytes, 0);
+    for (int k = 0; k < n_streams; k++) {
+        const Geometry &g = streams[k]->g;
+        batch_fill_lf(img.data() + offs[1] + lf_bytes * k, streams[k]->ds, n_keys, n_ck);
+        n_keys += (int64_t)g.nu * g.nv * g.nblocks;
+        n_ck += (int64_t)g.gu[1] * g.gv[1] * g.nblocks;
+    }
+    batch_fill_hdr(img.data(), n_streams, (int)views.size(), (int)tiles, TW, TH, n_keys, n_ck);
+    std::memcpy(img.data() + offs[2], views.data(), sizeof(hmlfc_view) * views.size());
+    std::memcpy(img.data() + offs[3], tile_start.data(), sizeof(int) * tile_start.size());
+    const int B = streams[0]->g.B;
+    const size_t blk_bytes = (size_t)B * B * 4;
+    const uint32_t capacity = (uint32_t)std::min<int64_t>(n_keys, (int64_t)(g_batch.cache_bytes / blk_bytes));
+    const size_t o_flags = up256(img_bytes), o_slot = up256(o_flags + (size_t)n_keys),
+                 o_items = up256(o_slot + (size_t)n_keys * 4), o_count = up256(o_items + (size_t)n_ck * 16),
+                 o_cache = up256(o_count + 16), total = up256(o_cache + (size_t)capacity * blk_bytes);
+    void *base = nullptr;
+    cudaError_t e = cudaMallocAsync(&base, total, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return hmlfc_render_views(streams, n_streams, h_views, n_views, d_out, cuda_stream);
+    }
+    uint8_t *b = static_cast<uint8_t *>(base);
+    e = launch_copy_blob(img.data(), (int)img_bytes, b, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b + o_flags, 0, (size_t)n_keys, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b + o_count, 0, 16, st);
+    if (e == cudaSuccess)
+        e = launch_batch(B, g_batch.tile_shape, b, offs, (int)tiles, b + o_flags, reinterpret_cast<uint32_t *>(b + o_slot),
+                         reinterpret_cast<uint4 *>(b + o_items), reinterpret_cast<unsigned long long *>(b + o_count),
+                         reinterpret_cast<unsigned int *>(b + o_count + 8), reinterpret_cast<uint32_t *>(b + o_cache),
+                         capacity, n_ck, g_batch.group, sm_count(dev) * g_batch.ctas_per_sm, d_out,
+                         g_phase_ev[0] ? g_phase_ev : nullptr, st);
+    const cudaError_t ef = cudaFreeAsync(base, st);
+    if (e == cudaSuccess) e = ef;
+    return e == cudaSuccess ? HMLFC_OK : cuda_fail(e, "batched render");
 }
 
 int hmlfc_render_views_relaxed(const hmlfc_stream *const *streams, int n_streams, const float *const *d_coeff,

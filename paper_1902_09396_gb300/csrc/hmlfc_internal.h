@@ -72,6 +72,17 @@ cudaError_t launch_decode_blocks(const DevStream &ds, const uint4 *items, const 
                                  uint32_t *cache, int grid, cudaStream_t st);
 cudaError_t launch_render_cached(const DevStream &ds, const LaunchViews &lv, int total_tiles, const uint32_t *slotmap,
                                  const uint32_t *cache, float *d_out, cudaStream_t st);
+// Batched form (one pass over many light fields).
+cudaError_t launch_copy_blob(const void *src, int n, void *dst, cudaStream_t st);
+size_t batch_lf_bytes();
+size_t batch_hdr_bytes();
+void batch_fill_lf(void *dst, const DevStream &ds, int64_t key_off, int64_t ck_off);
+void batch_fill_hdr(void *dst, int n_lf, int n_views, int total_tiles, int tile_w, int tile_h, int64_t n_keys,
+                    int64_t n_ck);
+cudaError_t launch_batch(int B, int tile_shape, const void *image, const int *ptr_offsets, int total_tiles,
+                         uint8_t *flags, uint32_t *slotmap, uint4 *items, unsigned long long *counters,
+                         unsigned int *work, uint32_t *cache, uint32_t capacity, int64_t n_ck, int group,
+                         int persistent_ctas, float *d_out, cudaEvent_t const *phase, cudaStream_t st);
 cudaError_t launch_render_relaxed(const DevStream &ds, const LaunchViews &lv, int total_tiles, const float *coeff,
                                   const float *root, float *d_out, cudaStream_t st);
 cudaError_t launch_render_backward(const DevStream &ds, const LaunchViews &lv, int total_tiles,

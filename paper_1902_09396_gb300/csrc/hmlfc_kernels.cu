@@ -12,6 +12,7 @@
 
 #include <climits>
 #include <cstdint>
+#include <cstring>
 #include <mutex>
 
 #include "hmlfc_internal.h"
@@ -1224,6 +1225,392 @@ cudaError_t render_dispatch_tw(const DevStream &ds, const LaunchViews &lv, int t
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Batched form: many light fields and views in one pass
+// ---------------------------------------------------------------------------
+//
+// A call's light-field descriptors, views and tile prefix live in device
+// scratch (written by k_copy_blob from kernel parameters, so a captured
+// graph keeps no pointer to host memory).  One launch each of mark, assign,
+// decode (persistent) and render (persistent, atomic work queue over
+// (view, tile) items) covers every light field of the call.
+
+// Host-built image at the start of the batch scratch.
+struct BatchHdr {
+    int n_lf, n_views, total_tiles, tile_w, tile_h;
+    int pad[3];
+    int64_t n_keys, n_ck;
+};
+
+struct BatchLF {
+    DevStream S;
+    int64_t key_off;   // first (camera, block) key of this light field
+    int64_t ck_off;    // first (level-1 node, block) key
+};
+
+struct BatchPtrs {     // device pointers into the scratch image
+    const BatchHdr *hdr;
+    const BatchLF *lf;
+    const hmlfc_view *views;
+    const int *tile_start;
+};
+
+// Copies a by-value blob of bytes into device memory.
+constexpr int kBlobBytes = 30000;
+struct Blob {
+    int n;
+    unsigned char b[kBlobBytes];
+};
+
+__global__ void k_copy_blob(const __grid_constant__ Blob blob, unsigned char *__restrict__ dst) {
+    for (int k = threadIdx.x; k < blob.n; k += blockDim.x) dst[k] = blob.b[k];
+}
+
+__device__ __forceinline__ int find_view_dev(const int *__restrict__ tile_start, int n_views, int tile) {
+    int lo = 0, hi = n_views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(tile_start + mid) <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One thread per tile: flag the (camera, block) pairs of its footprint.
+template <int BS, int TW, int TH>
+__global__ void __launch_bounds__(128) k_mark_batch(const BatchPtrs P, uint8_t *__restrict__ flags) {
+    const int tile = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tile >= P.hdr->total_tiles) return;
+    const int vi = find_view_dev(P.tile_start, P.hdr->n_views, tile);
+    const hmlfc_view V = P.views[vi];
+    const BatchLF &F = P.lf[V.lf];
+    const DevStream &S = F.S;
+    const int tiles_x = (V.width + TW - 1) / TW;
+    const int local = tile - __ldg(P.tile_start + vi);
+    const int x0 = (local % tiles_x) * TW, y0 = (local / tiles_x) * TH;
+    const int x1 = min(x0 + TW, V.width) - 1, y1 = min(y0 + TH, V.height) - 1;
+    const Blk<BS> bk(S.B);
+    const int nu = S.nu, nv = S.nv, W = S.W, Hh = S.H, nbx = S.nbx, nblocks = S.nblocks;
+    float lo[4] = {1e30f, 1e30f, 1e30f, 1e30f}, hi[4] = {-1e30f, -1e30f, -1e30f, -1e30f};
+    bool ok = true;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const float X = (float)((q & 1) ? x1 : x0) + 0.5f, Y = (float)((q & 2) ? y1 : y0) + 0.5f;
+        const float *h = V.H_uv, *g = V.H_st;
+        const float wu = h[6] * X + h[7] * Y + h[8], ws = g[6] * X + g[7] * Y + g[8];
+        ok &= wu > 0.f && ws > 0.f;
+        const float c[4] = {__fdividef(h[0] * X + h[1] * Y + h[2], wu), __fdividef(h[3] * X + h[4] * Y + h[5], wu),
+                            __fdividef(g[0] * X + g[1] * Y + g[2], ws), __fdividef(g[3] * X + g[4] * Y + g[5], ws)};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            lo[k] = fminf(lo[k], c[k]);
+            hi[k] = fmaxf(hi[k], c[k]);
+        }
+    }
+    uint8_t *fl = flags + F.key_off;
+    const int n[4] = {nu, nv, W, Hh};
+    int bl[4], bh[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const float e = k < 2 ? 1e-3f : 1e-2f;
+        int a0, a1, b0, b1;
+        axis_nb(lo[k] - e, n[k], a0, a1);
+        axis_nb(hi[k] + e, n[k], b0, b1);
+        bl[k] = a0;
+        bh[k] = b1;
+        if (!(lo[k] == lo[k]) || !(hi[k] == hi[k])) ok = false;
+    }
+    if (!ok) {
+        for (int py = y0; py <= y1; py++)
+            for (int px = x0; px <= x1; px++) {
+                Ray r;
+                ray_setup(V, nu, nv, W, Hh, px, py, r);
+                const int ci[2] = {r.i0, r.i1}, cj[2] = {r.j0, r.j1};
+                const int kb[4] = {bk.div(r.y0) * nbx + bk.div(r.x0), bk.div(r.y0) * nbx + bk.div(r.x1),
+                                   bk.div(r.y1) * nbx + bk.div(r.x0), bk.div(r.y1) * nbx + bk.div(r.x1)};
+                for (int q = 0; q < 16; q++) fl[((size_t)ci[q >> 3] * nv + cj[(q >> 2) & 1]) * nblocks + kb[q & 3]] = 1;
+            }
+        return;
+    }
+    const int bx0 = bk.div(bl[2]), bx1 = bk.div(bh[2]), by0 = bk.div(bl[3]), by1 = bk.div(bh[3]);
+    for (int i = bl[0]; i <= bh[0]; i++)
+        for (int j = bl[1]; j <= bh[1]; j++) {
+            uint8_t *f = fl + ((size_t)i * nv + j) * nblocks;
+            for (int by = by0; by <= by1; by++)
+                for (int bx = bx0; bx <= bx1; bx++) f[by * nbx + bx] = 1;
+        }
+}
+
+// One thread per (light field, level-1 node, block): slots of its flagged
+// cameras and one decode item {cluster key, camera mask, first slot, lf}.
+__global__ void __launch_bounds__(256) k_assign_batch(const BatchPtrs P, const uint8_t *__restrict__ flags,
+                                                      uint32_t *__restrict__ slotmap, uint4 *__restrict__ items,
+                                                      unsigned long long *__restrict__ counters, uint32_t capacity) {
+    __shared__ uint32_t s_warp[8][2];
+    __shared__ uint32_t s_base[2];
+    const int64_t gck = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    uint32_t mask = 0;
+    int64_t keys[4] = {-1, -1, -1, -1};
+    int lf = 0;
+    int64_t ck = 0;
+    if (gck < P.hdr->n_ck) {
+        while (lf + 1 < P.hdr->n_lf && gck >= P.lf[lf + 1].ck_off) lf++;
+        const BatchLF &F = P.lf[lf];
+        const DevStream &S = F.S;
+        ck = gck - F.ck_off;
+        const int node = (int)(ck / S.nblocks), k = (int)(ck - (int64_t)node * S.nblocks);
+        const int gv1 = S.gv[1];
+        const int a1 = node / gv1, b1 = node - (node / gv1) * gv1;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int i = 2 * a1 + (q >> 1), j = 2 * b1 + (q & 1);
+            if (i < S.nu && j < S.nv) {
+                keys[q] = F.key_off + ((int64_t)i * S.nv + j) * S.nblocks + k;
+                if (flags[keys[q]]) mask |= 1u << q;
+            }
+        }
+    }
+    const uint32_t nslot = __popc(mask), nitem = mask ? 1u : 0u;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t is = nslot, ii = nitem;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t vs = __shfl_up_sync(0xFFFFFFFFu, is, o), vi = __shfl_up_sync(0xFFFFFFFFu, ii, o);
+        if (lane >= o) {
+            is += vs;
+            ii += vi;
+        }
+    }
+    if (lane == 31) {
+        s_warp[warp][0] = is;
+        s_warp[warp][1] = ii;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t as = 0, ai = 0;
+        for (int w = 0; w < 8; w++) {
+            const uint32_t vs = s_warp[w][0], vi = s_warp[w][1];
+            s_warp[w][0] = as;
+            s_warp[w][1] = ai;
+            as += vs;
+            ai += vi;
+        }
+        const unsigned long long old = atomicAdd(counters, ((unsigned long long)ai << 32) | as);
+        s_base[0] = (uint32_t)(old & 0xFFFFFFFFull);
+        s_base[1] = (uint32_t)(old >> 32);
+    }
+    __syncthreads();
+    if (gck >= P.hdr->n_ck) return;
+    const uint32_t slot0 = s_base[0] + s_warp[warp][0] + is - nslot;
+    const uint32_t item = s_base[1] + s_warp[warp][1] + ii - nitem;
+    uint32_t slot = slot0;
+    const bool fits = slot0 + nslot <= capacity;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        if (keys[q] < 0) continue;
+        if ((mask >> q) & 1u) {
+            slotmap[keys[q]] = fits ? slot : kNone;
+            slot++;
+        } else {
+            slotmap[keys[q]] = kNone;
+        }
+    }
+    if (mask) items[item] = make_uint4((uint32_t)ck, fits ? mask : 0u, slot0, (uint32_t)lf);
+}
+
+__device__ __forceinline__ void copy_words(void *dst, const void *src, int bytes) {
+    const int n = bytes / 4;
+    for (int t = threadIdx.x; t < n; t += blockDim.x)
+        reinterpret_cast<uint32_t *>(dst)[t] = __ldg(reinterpret_cast<const uint32_t *>(src) + t);
+}
+
+// Persistent decode of every light field's items, G items per pass.
+template <int BS>
+__global__ void __launch_bounds__(256) k_decode_batch(const BatchPtrs P, const uint4 *__restrict__ items,
+                                                     const unsigned long long *__restrict__ counters,
+                                                     uint32_t *__restrict__ cache, int G) {
+    constexpr int kMaxGroup = 8;
+    constexpr int kDescPer = (kMaxLevels - 1) * 3 + 12;
+    __shared__ __align__(16) DevStream s_S[kMaxGroup];
+    __shared__ LevelTabs s_T[kMaxGroup];
+    __shared__ Desc s_desc[kMaxGroup * kDescPer];
+    __shared__ uint4 s_it[kMaxGroup];
+    const uint32_t n = (uint32_t)(__ldg(counters) >> 32);
+    G = max(1, min(G, kMaxGroup));
+    for (uint32_t first = blockIdx.x * G; first < n; first += gridDim.x * G) {
+        __syncthreads();
+        for (int gi = 0; gi < G; gi++) {
+            const uint32_t it_idx = first + gi;
+            const uint4 it = it_idx < n ? __ldg(items + it_idx) : make_uint4(0u, 0u, 0u, 0u);
+            if (threadIdx.x == 0) s_it[gi] = it;
+            if (it_idx < n) copy_words(&s_S[gi], &P.lf[it.w].S, (int)sizeof(DevStream));
+        }
+        __syncthreads();
+        for (int gi = 0; gi < G; gi++)
+            if (first + gi < n) load_tabs(s_S[gi], s_T[gi]);
+        __syncthreads();
+        for (int d = threadIdx.x; d < G * kDescPer; d += blockDim.x) {
+            const int gi = d / kDescPer, e = d - gi * kDescPer;
+            if (first + gi >= n) continue;
+            const uint4 it = s_it[gi];
+            if (!it.y) continue;
+            const DevStream &S = s_S[gi];
+            const LevelTabs &T = s_T[gi];
+            const int L = S.L;
+            if (e >= (L - 1) * 3 + 12) continue;
+            const Blk<BS> bk(S.B);
+            const int node = (int)(it.x / (uint32_t)S.nblocks), k = (int)(it.x - (uint32_t)node * S.nblocks);
+            const int a1 = node / T.gv[1], b1 = node - (node / T.gv[1]) * T.gv[1];
+            int l, a, b, c;
+            if (e < (L - 1) * 3) {
+                l = 1 + e / 3;
+                c = e - 3 * (l - 1);
+                a = a1 >> (l - 1);
+                b = b1 >> (l - 1);
+            } else {
+                const int q = (e - (L - 1) * 3) / 3;
+                c = (e - (L - 1) * 3) - 3 * q;
+                l = 0;
+                a = 2 * a1 + (q >> 1);
+                b = 2 * b1 + (q & 1);
+                if (!((it.y >> q) & 1u)) continue;
+            }
+            s_desc[d] = make_desc(S, T, bk, l, a, b, c, k % S.nbx, k / S.nbx);
+        }
+        __syncthreads();
+        for (int gi = 0; gi < G; gi++) {
+            if (first + gi >= n) continue;
+            const uint4 it = s_it[gi];
+            if (!it.y) continue;
+            const DevStream &S = s_S[gi];
+            const LevelTabs &T = s_T[gi];
+            const Blk<BS> bk(S.B);
+            const int B = bk.size(), B2 = B * B, L = S.L;
+            const size_t plane = (size_t)S.W * S.H;
+            const int node = (int)(it.x / (uint32_t)S.nblocks), k = (int)(it.x - (uint32_t)node * S.nblocks);
+            const int a1 = node / T.gv[1], b1 = node - (node / T.gv[1]) * T.gv[1];
+            const int bx = k % S.nbx, by = k / S.nbx;
+            const int bw = min(B, S.W - bx * B), bh = min(B, S.H - by * B);
+            const Desc *dd = s_desc + gi * kDescPer;
+            for (int p = threadIdx.x; p < B2; p += blockDim.x) {
+                const int yy = p / B, xx = p - yy * B;
+                const bool inside = xx < bw && yy < bh;
+                PixGeom g;
+                g.x = bx * B + min(xx, bw - 1);
+                g.y = by * B + min(yy, bh - 1);
+                g.blk = 0;
+                g.idx = (g.y - by * B) * bw + (g.x - bx * B);
+                g.toff = (g.y - by * B) * B + (g.x - bx * B);
+                const size_t rb =
+                    ((size_t)(a1 >> (L - 1)) * T.gv[L] + (b1 >> (L - 1))) * 3 * plane + (size_t)g.y * S.W + g.x;
+                int v[3] = {__ldg(S.roots + rb), __ldg(S.roots + rb + plane), __ldg(S.roots + rb + 2 * plane)};
+                for (int l = L - 1; l >= 1; l--) {
+                    const bool ref = is_ref(a1 >> (l - 1), b1 >> (l - 1));
+#pragma unroll
+                    for (int c = 0; c < 3; c++) v[c] += srv_desc(S, bk, dd[(l - 1) * 3 + c], ref, g);
+                }
+                uint32_t slot = it.z;
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    if (!((it.y >> q) & 1u)) continue;
+                    const int i = 2 * a1 + (q >> 1), j = 2 * b1 + (q & 1);
+                    const bool ref = is_ref(i, j);
+                    const Desc *d0 = dd + (L - 1) * 3 + q * 3;
+                    const int w0 = v[0] + srv_desc(S, bk, d0[0], ref, g);
+                    const int w1 = v[1] + srv_desc(S, bk, d0[1], ref, g);
+                    const int w2 = v[2] + srv_desc(S, bk, d0[2], ref, g);
+                    cache[(size_t)slot * B2 + p] = inside ? ycocg_to_rgb8(w0, w1, w2) : 0u;
+                    slot++;
+                }
+            }
+        }
+    }
+}
+
+// Persistent render: CTAs take (view, tile) items from an atomic counter.
+template <int BS, int TW, int TH>
+__global__ void __launch_bounds__(TW *TH) k_render_batch(const BatchPtrs P, const uint32_t *__restrict__ slotmap,
+                                                        const uint32_t *__restrict__ cache,
+                                                        unsigned int *__restrict__ work, float *__restrict__ out) {
+    __shared__ __align__(16) DevStream s_S;
+    __shared__ LevelTabs s_T;
+    __shared__ hmlfc_view s_V;
+    __shared__ int s_tile, s_local;
+    __shared__ int s_lf;
+    __shared__ long long s_key_off;
+    if (threadIdx.x == 0) s_lf = -1;
+    const int total = P.hdr->total_tiles, n_views = P.hdr->n_views;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int tile = (int)atomicAdd(work, 1u);
+            s_tile = tile;
+            if (tile < total) {
+                const int vi = find_view_dev(P.tile_start, n_views, tile);
+                s_V = P.views[vi];
+                s_local = tile - __ldg(P.tile_start + vi);
+            }
+        }
+        __syncthreads();
+        if (s_tile >= total) break;
+        const int lf = s_V.lf;
+        if (lf != s_lf) {                       // uniform: the whole CTA reloads the descriptor
+            __syncthreads();
+            copy_words(&s_S, &P.lf[lf].S, (int)sizeof(DevStream));
+            __syncthreads();
+            load_tabs(s_S, s_T);
+            if (threadIdx.x == 0) {
+                s_lf = lf;
+                s_key_off = P.lf[lf].key_off;
+            }
+            __syncthreads();
+        }
+        const DevStream &S = s_S;
+        const hmlfc_view &V = s_V;
+        const int tiles_x = (V.width + TW - 1) / TW;
+        const int px = (s_local % tiles_x) * TW + (int)threadIdx.x % TW;
+        const int py = (s_local / tiles_x) * TH + (int)threadIdx.x / TW;
+        if (px >= V.width || py >= V.height) continue;
+        const Blk<BS> bk(S.B);
+        const int B = bk.size();
+        Ray r;
+        ray_setup(V, S.nu, S.nv, S.W, S.H, px, py, r);
+        const uint32_t nv = (uint32_t)S.nv, nbl = (uint32_t)S.nblocks;
+        const uint32_t *sm = slotmap + s_key_off;
+        const uint32_t cam[4] = {(uint32_t)r.i0 * nv + r.j0, (uint32_t)r.i0 * nv + r.j1, (uint32_t)r.i1 * nv + r.j0,
+                                 (uint32_t)r.i1 * nv + r.j1};
+        const int bx[2] = {bk.div(r.x0), bk.div(r.x1)}, by[2] = {bk.div(r.y0), bk.div(r.y1)};
+        const uint32_t blk[4] = {(uint32_t)(by[0] * S.nbx + bx[0]), (uint32_t)(by[1] * S.nbx + bx[0]),
+                                 (uint32_t)(by[0] * S.nbx + bx[1]), (uint32_t)(by[1] * S.nbx + bx[1])};
+        const uint32_t off[4] = {(uint32_t)((r.y0 - by[0] * B) * B + (r.x0 - bx[0] * B)),
+                                 (uint32_t)((r.y1 - by[1] * B) * B + (r.x0 - bx[0] * B)),
+                                 (uint32_t)((r.y0 - by[0] * B) * B + (r.x1 - bx[1] * B)),
+                                 (uint32_t)((r.y1 - by[1] * B) * B + (r.x1 - bx[1] * B))};
+        uint32_t slot[16];
+        bool all = true;
+#pragma unroll
+        for (int q = 0; q < 16; q++) {
+            slot[q] = __ldg(sm + (size_t)cam[q >> 2] * nbl + blk[q & 3]);
+            all &= slot[q] != kNone;
+        }
+        float o[3];
+        if (all) {
+            uint32_t val[16];
+#pragma unroll
+            for (int q = 0; q < 16; q++) val[q] = __ldg(cache + (size_t)slot[q] * (uint32_t)(B * B) + off[q & 3]);
+            blend16(r, [&](int a, int b, int xs, int ys, int, int, int, int) { return val[a * 8 + b * 4 + xs * 2 + ys]; },
+                    o);
+        } else {
+            blend16(r, [&](int, int, int, int, int i, int j, int x, int y) { return sample_direct(S, s_T, bk, i, j, x, y); },
+                    o);
+        }
+        float *dst = out + V.out_offset + ((size_t)py * V.width + px) * 3;
+        dst[0] = o[0];
+        dst[1] = o[1];
+        dst[2] = o[2];
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1290,6 +1677,103 @@ cudaError_t launch_render_cached(const DevStream &ds, const LaunchViews &lv, int
     if (total_tiles <= 0) return cudaSuccess;
     HMLFC_DISPATCH_B(ds.B, (k_render_cached<BS, 16, 16><<<total_tiles, 256, 0, st>>>(ds, lv, slotmap, cache, d_out)));
     return cudaGetLastError();
+}
+
+cudaError_t launch_copy_blob(const void *src, int n, void *dst, cudaStream_t st) {
+    for (int o = 0; o < n; o += kBlobBytes) {
+        Blob b;
+        b.n = n - o < kBlobBytes ? n - o : kBlobBytes;
+        memcpy(b.b, static_cast<const unsigned char *>(src) + o, (size_t)b.n);
+        k_copy_blob<<<1, 256, 0, st>>>(b, static_cast<unsigned char *>(dst) + o);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+size_t batch_lf_bytes() { return sizeof(BatchLF); }
+size_t batch_hdr_bytes() { return sizeof(BatchHdr); }
+
+void batch_fill_lf(void *dst, const DevStream &ds, int64_t key_off, int64_t ck_off) {
+    BatchLF f;
+    memset(&f, 0, sizeof f);
+    f.S = ds;
+    f.key_off = key_off;
+    f.ck_off = ck_off;
+    memcpy(dst, &f, sizeof f);
+}
+
+void batch_fill_hdr(void *dst, int n_lf, int n_views, int total_tiles, int tile_w, int tile_h, int64_t n_keys,
+                    int64_t n_ck) {
+    BatchHdr h;
+    memset(&h, 0, sizeof h);
+    h.n_lf = n_lf;
+    h.n_views = n_views;
+    h.total_tiles = total_tiles;
+    h.tile_w = tile_w;
+    h.tile_h = tile_h;
+    h.n_keys = n_keys;
+    h.n_ck = n_ck;
+    memcpy(dst, &h, sizeof h);
+}
+
+namespace {
+
+template <int BS, int TW, int TH>
+cudaError_t batch_kernels(const BatchPtrs &P, int total_tiles, uint8_t *flags, uint32_t *slotmap, uint4 *items,
+                          unsigned long long *counters, unsigned int *work, uint32_t *cache, uint32_t capacity,
+                          int64_t n_ck, int group, int persistent_ctas, float *d_out, cudaEvent_t const *phase,
+                          cudaStream_t st) {
+    if (phase && phase[0]) cudaEventRecord(phase[0], st);
+    k_mark_batch<BS, TW, TH><<<(total_tiles + 127) / 128, 128, 0, st>>>(P, flags);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_assign_batch<<<(unsigned)((n_ck + 255) / 256), 256, 0, st>>>(P, flags, slotmap, items, counters, capacity);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (phase && phase[1]) cudaEventRecord(phase[1], st);
+    k_decode_batch<BS><<<persistent_ctas, 256, 0, st>>>(P, items, counters, cache, group);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (phase && phase[2]) cudaEventRecord(phase[2], st);
+    k_render_batch<BS, TW, TH><<<persistent_ctas, TW * TH, 0, st>>>(P, slotmap, cache, work, d_out);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (phase && phase[3]) cudaEventRecord(phase[3], st);
+    return cudaSuccess;
+}
+
+template <int BS>
+cudaError_t batch_tiles(int tile_shape, const BatchPtrs &P, int total_tiles, uint8_t *flags, uint32_t *slotmap,
+                        uint4 *items, unsigned long long *counters, unsigned int *work, uint32_t *cache,
+                        uint32_t capacity, int64_t n_ck, int group, int persistent_ctas, float *d_out,
+                        cudaEvent_t const *phase, cudaStream_t st) {
+    switch (tile_shape) {
+        case 1:
+            return batch_kernels<BS, 32, 8>(P, total_tiles, flags, slotmap, items, counters, work, cache, capacity,
+                                            n_ck, group, persistent_ctas, d_out, phase, st);
+        case 2:
+            return batch_kernels<BS, 8, 8>(P, total_tiles, flags, slotmap, items, counters, work, cache, capacity,
+                                           n_ck, group, persistent_ctas, d_out, phase, st);
+        default:
+            return batch_kernels<BS, 16, 16>(P, total_tiles, flags, slotmap, items, counters, work, cache, capacity,
+                                             n_ck, group, persistent_ctas, d_out, phase, st);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_batch(int B, int tile_shape, const void *image, const int *ptr_offsets, int total_tiles,
+                         uint8_t *flags, uint32_t *slotmap, uint4 *items, unsigned long long *counters,
+                         unsigned int *work, uint32_t *cache, uint32_t capacity, int64_t n_ck, int group,
+                         int persistent_ctas, float *d_out, cudaEvent_t const *phase, cudaStream_t st) {
+    BatchPtrs P;
+    const unsigned char *base = static_cast<const unsigned char *>(image);
+    P.hdr = reinterpret_cast<const BatchHdr *>(base + ptr_offsets[0]);
+    P.lf = reinterpret_cast<const BatchLF *>(base + ptr_offsets[1]);
+    P.views = reinterpret_cast<const hmlfc_view *>(base + ptr_offsets[2]);
+    P.tile_start = reinterpret_cast<const int *>(base + ptr_offsets[3]);
+    cudaError_t e = cudaSuccess;
+    HMLFC_DISPATCH_B(B, (e = batch_tiles<BS>(tile_shape, P, total_tiles, flags, slotmap, items, counters, work, cache,
+                                             capacity, n_ck, group, persistent_ctas, d_out, phase, st)));
+    return e;
 }
 
 cudaError_t launch_render_relaxed(const DevStream &ds, const LaunchViews &lv, int total_tiles, const float *coeff,

@@ -360,6 +360,20 @@ CONFIGS = {
 BATCHED_LFS = [(5, 256), (9, 384), (13, 512), (17, 512), (7, 768), (11, 640), (15, 320), (17, 1024)]
 
 
+def batched_views(seed: int, cfgs, n_views: int = 256, sizes=(256, 384, 512, 640, 768, 1024)) -> list:
+    """n_views random pinhole views spread over the light fields of `cfgs`,
+    square outputs of mixed resolution drawn from `sizes`."""
+    rng = np.random.default_rng(seed)
+    views = []
+    for k in range(n_views):
+        lf = int(rng.integers(0, len(cfgs)))
+        c = cfgs[lf]
+        geo = lf_geometry(c.nu, c.nv, c.width, c.height)
+        s = int(sizes[int(rng.integers(0, len(sizes)))])
+        views += random_views(int(rng.integers(0, 2 ** 31)), geo, 1, [(s, s)], lf=lf)
+    return views
+
+
 def batched_workload(seed: int = 4):
     """LFConfig list for the eight uneven light fields of the batched form;
     levels = clamp(ceil(log2 n), 3, 5)."""

@@ -247,3 +247,57 @@ def test_requantize_round_trip(H, torch_cuda, tiny_streams, tiny_cfg):
     new = H.requantize(st, co.cpu().numpy(), ro.cpu().numpy())
     a, b = O.Stream(data).decode_all(), O.Stream(new).decode_all()
     assert np.array_equal(a, b)
+
+
+def test_render_batch_matches_render_views(H, torch_cuda, tiny_streams, tiny_cfg, ragged_lf):
+    """The batched pass over several light fields (persistent decode and
+    render, every tuning candidate shape) is bitwise equal to render_views,
+    also when the decoded-block cache overflows."""
+    c = tiny_cfg
+    s1 = H.Stream(tiny_streams[c.qstep].stream)
+    s2 = H.Stream(O.encode(ragged_lf, 3, 8, 4, 2, t_ref=20, t_pred=30).stream)
+    geo1 = S.lf_geometry(c.nu, c.nv, c.width, c.height)
+    geo2 = S.lf_geometry(5, 3, 37, 29)
+    views = (S.random_views(51, geo1, 5, [(64, 64), (33, 17), (1, 1)]) +
+             S.random_views(52, geo2, 4, [(40, 31), (8, 70)], lf=1))
+    views = [views[k] for k in (0, 5, 1, 6, 2, 7, 3, 8, 4)]
+    arr = S.views_to_array(views)
+    want = _render_gpu(H, torch_cuda, [s1, s2], arr)
+    try:
+        for tile in (0, 1, 2):
+            for group in (1, 4, 8):
+                H.set_batch_tuning(tile, group, 2)
+                got = H.render_batch([s1, s2], arr)
+                torch_cuda.cuda.synchronize()
+                assert np.array_equal(got.cpu().numpy().astype(np.float64), want)
+        H.set_batch_tuning(0, 4, 4, 6 * 8 * 8 * 4)      # room for six blocks only
+        got = H.render_batch([s1, s2], arr)
+        torch_cuda.cuda.synchronize()
+        assert np.array_equal(got.cpu().numpy().astype(np.float64), want)
+    finally:
+        H.set_batch_tuning(0, 4, 8, 2 << 30)
+
+
+def test_render_batch_graph_replay(H, torch_cuda, tiny_streams, tiny_cfg):
+    """A captured batched render replays to the same output (no host memory
+    is read at replay)."""
+    torch = torch_cuda
+    c = tiny_cfg
+    st = H.Stream(tiny_streams[c.qstep].stream)
+    arr = S.views_to_array(_views_mix(c, 53, 6, [(64, 64), (40, 24)]))
+    want = _render_gpu(H, torch, [st], arr)
+    out = torch.zeros(H.out_size(arr), dtype=torch.float32, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        H.render_batch([st], arr, out)                  # warm-up outside the capture
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        H.render_batch([st], arr, out)
+    for _ in range(2):
+        out.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy().astype(np.float64), want)
