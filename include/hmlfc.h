@@ -222,6 +222,23 @@ int hmlfc_render_batch(const hmlfc_stream *const *streams, int n_streams, const 
 int hmlfc_set_batch_tuning(int tile_shape, int group, int ctas_per_sm, size_t cache_bytes);
 
 /*
+ * Serving form.  A server keeps a decoded-block cache of one stream resident
+ * on the device across render calls (cache_bytes of B * B * 4-byte slots, plus
+ * a slot map of 4 bytes per (camera, block) pair).  Each call marks the
+ * blocks its views reach, reuses the resident ones, decodes the others into
+ * slots not used by the call (oldest first), and blends every ray from the
+ * cache; results equal hmlfc_render_views.  Calls on one server must be
+ * ordered on one CUDA stream (they share its cache).  create and free are
+ * synchronous; render is asynchronous.  hmlfc_server_stats synchronises and
+ * writes {blocks decoded since creation, decode items, cache slots}.
+ */
+typedef struct hmlfc_server hmlfc_server;
+int hmlfc_server_create(const hmlfc_stream *s, size_t cache_bytes, void *cuda_stream, hmlfc_server **out);
+int hmlfc_server_render(hmlfc_server *sv, const hmlfc_view *h_views, int n_views, float *d_out, void *cuda_stream);
+int hmlfc_server_stats(const hmlfc_server *sv, void *cuda_stream, int64_t *out3);
+void hmlfc_server_free(hmlfc_server *sv);
+
+/*
  * Differentiable relaxation (for gradient-based refinement of the residuals):
  * the same render with real-valued coefficients -- exact bilinear weights
  * instead of the >> 4 rounding, YCoCg-R inverse with /2 instead of >> 1, no

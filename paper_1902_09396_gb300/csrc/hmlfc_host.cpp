@@ -685,6 +685,110 @@ int hmlfc_render_batch(const hmlfc_stream *const *streams, int n_streams, const 
     return e == cudaSuccess ? HMLFC_OK : cuda_fail(e, "batched render");
 }
 
+int hmlfc_server_create(const hmlfc_stream *s, size_t cache_bytes, void *cuda_stream, hmlfc_server **out) {
+    if (!s || !out) return fail(HMLFC_E_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    const Geometry &g = s->g;
+    DeviceGuard guard(s->device);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int64_t n_keys = (int64_t)g.nu * g.nv * g.nblocks;
+    const int64_t n_ck = (int64_t)g.gu[1] * g.gv[1] * g.nblocks;
+    const size_t blk = (size_t)g.B * g.B * 4;
+    const uint32_t capacity = (uint32_t)std::min<int64_t>(n_keys, (int64_t)(cache_bytes / blk));
+    if (capacity == 0) return fail(HMLFC_E_INVALID_ARG, "cache of %zu bytes holds no block", cache_bytes);
+    auto *sv = new (std::nothrow) hmlfc_server();
+    if (!sv) return fail(HMLFC_E_OOM, "host allocation");
+    sv->s = s;
+    sv->capacity = capacity;
+    sv->n_keys = n_keys;
+    sv->n_ck = n_ck;
+    const size_t o_flags = 0, o_slot = up256((size_t)n_keys), o_owner = up256(o_slot + (size_t)n_keys * 4),
+                 o_epoch = up256(o_owner + (size_t)capacity * 4), o_clock = up256(o_epoch + (size_t)capacity * 4),
+                 o_items = up256(o_clock + 64), o_cache = up256(o_items + (size_t)n_ck * 32),
+                 total = up256(o_cache + (size_t)capacity * blk);
+    cudaError_t e = cudaMalloc(&sv->d_mem, total);
+    if (e != cudaSuccess) {
+        delete sv;
+        cudaGetLastError();
+        return fail(HMLFC_E_OOM, "server allocation of %zu bytes", total);
+    }
+    uint8_t *b = static_cast<uint8_t *>(sv->d_mem);
+    sv->bytes = total;
+    sv->flags = b + o_flags;
+    sv->slotmap = reinterpret_cast<uint32_t *>(b + o_slot);
+    sv->owner = reinterpret_cast<uint32_t *>(b + o_owner);
+    sv->epoch = reinterpret_cast<uint32_t *>(b + o_epoch);
+    sv->clock = reinterpret_cast<uint32_t *>(b + o_clock);
+    sv->counters = reinterpret_cast<unsigned long long *>(b + o_clock + 8);
+    sv->totals = reinterpret_cast<unsigned long long *>(b + o_clock + 16);
+    sv->items = reinterpret_cast<uint4 *>(b + o_items);
+    sv->cache = reinterpret_cast<uint32_t *>(b + o_cache);
+    e = cudaMemsetAsync(sv->slotmap, 0xFF, (size_t)n_keys * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sv->owner, 0xFF, (size_t)capacity * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sv->epoch, 0, (size_t)capacity * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sv->clock, 0, 64, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        hmlfc_server_free(sv);
+        return cuda_fail(e, "server set-up");
+    }
+    *out = sv;
+    return HMLFC_OK;
+}
+
+void hmlfc_server_free(hmlfc_server *sv) {
+    if (!sv) return;
+    if (sv->d_mem) {
+        DeviceGuard guard(sv->s->device);
+        cudaFree(sv->d_mem);
+    }
+    delete sv;
+}
+
+int hmlfc_server_render(hmlfc_server *sv, const hmlfc_view *h_views, int n_views, float *d_out, void *cuda_stream) {
+    if (!sv) return fail(HMLFC_E_INVALID_ARG, "server is NULL");
+    const hmlfc_stream *s = sv->s;
+    int rc = check_views(&s, 1, h_views, n_views);
+    if (rc != HMLFC_OK) return rc;
+    if (n_views == 0) return HMLFC_OK;
+    if (!d_out) return fail(HMLFC_E_INVALID_ARG, "d_out is NULL");
+    DeviceGuard guard(s->device);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<LaunchViews> chunks;
+    std::vector<int> tiles;
+    rc = view_chunks(h_views, n_views, 0, chunks, tiles);
+    if (rc != HMLFC_OK) return rc;
+    const uint32_t cur = ++sv->call;
+    phase_mark(0, st);
+    cudaError_t e = cudaMemsetAsync(sv->flags, 0, (size_t)sv->n_keys, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sv->counters, 0, 8, st);
+    for (size_t c = 0; c < chunks.size() && e == cudaSuccess; c++) e = launch_mark(s->ds, chunks[c], tiles[c], sv->flags, st);
+    phase_mark(1, st);
+    if (e == cudaSuccess)
+        e = launch_resident(s->ds, sv->flags, sv->n_keys, sv->slotmap, sv->owner, sv->epoch, sv->clock, sv->capacity, cur,
+                            sv->items, sv->counters, sv->cache, sm_count(s->device) * 8, st);
+    phase_mark(2, st);
+    for (size_t c = 0; c < chunks.size() && e == cudaSuccess; c++)
+        e = launch_render_cached(s->ds, chunks[c], tiles[c], sv->slotmap, sv->cache, d_out, st);
+    phase_mark(3, st);
+    if (e == cudaSuccess) e = launch_accumulate(sv->counters, sv->totals, st);
+    return e == cudaSuccess ? HMLFC_OK : cuda_fail(e, "server render");
+}
+
+int hmlfc_server_stats(const hmlfc_server *sv, void *cuda_stream, int64_t *out3) {
+    if (!sv || !out3) return fail(HMLFC_E_INVALID_ARG, "NULL argument");
+    DeviceGuard guard(sv->s->device);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    unsigned long long t[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(t, sv->totals, 16, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "server stats");
+    out3[0] = (int64_t)t[0];           // blocks decoded (cache misses) since creation
+    out3[1] = (int64_t)t[1];           // decode items
+    out3[2] = (int64_t)sv->capacity;   // slots of the resident cache
+    return HMLFC_OK;
+}
+
 int hmlfc_render_views_relaxed(const hmlfc_stream *const *streams, int n_streams, const float *const *d_coeff,
                                const float *const *d_root, const hmlfc_view *h_views, int n_views, float *d_out,
                                void *cuda_stream) {

@@ -70,3 +70,17 @@ struct hmlfc_stream {
     int64_t n_tiles = 0;
     std::vector<uint32_t> ref_tab;   // host copy of the tile table
 };
+
+struct hmlfc_server {
+    const hmlfc_stream *s = nullptr;
+    uint32_t capacity = 0;
+    uint32_t call = 0;                 // epoch of the last render call
+    int64_t n_keys = 0, n_ck = 0;
+    void *d_mem = nullptr;
+    size_t bytes = 0;
+    uint8_t *flags = nullptr;
+    uint32_t *slotmap = nullptr, *owner = nullptr, *epoch = nullptr, *clock = nullptr;
+    unsigned long long *counters = nullptr, *totals = nullptr;
+    uint4 *items = nullptr;
+    uint32_t *cache = nullptr;
+};

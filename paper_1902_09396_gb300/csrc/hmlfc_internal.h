@@ -72,6 +72,14 @@ cudaError_t launch_decode_blocks(const DevStream &ds, const uint4 *items, const 
                                  uint32_t *cache, int grid, cudaStream_t st);
 cudaError_t launch_render_cached(const DevStream &ds, const LaunchViews &lv, int total_tiles, const uint32_t *slotmap,
                                  const uint32_t *cache, float *d_out, cudaStream_t st);
+// Serving form: resident decoded-block cache (hits, misses with eviction, decode).
+cudaError_t launch_resident(const DevStream &ds, const uint8_t *flags, int64_t n_keys, uint32_t *slotmap,
+                            uint32_t *owner, uint32_t *epoch, uint32_t *clock, uint32_t capacity, uint32_t cur,
+                            uint4 *items, unsigned long long *counters, uint32_t *cache, int decode_grid,
+                            cudaStream_t st);
+
+cudaError_t launch_accumulate(const unsigned long long *counters, unsigned long long *totals, cudaStream_t st);
+
 // Batched form (one pass over many light fields).
 cudaError_t launch_copy_blob(const void *src, int n, void *dst, cudaStream_t st);
 size_t batch_lf_bytes();

@@ -1611,6 +1611,153 @@ __global__ void __launch_bounds__(TW *TH) k_render_batch(const BatchPtrs P, cons
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Serving form: a decoded-block cache that stays resident across calls
+// ---------------------------------------------------------------------------
+//
+// Per slot: the (camera, block) key it holds (owner) and the call that last
+// used it (epoch).  A call marks its blocks, stamps the resident ones with
+// its epoch (hits), then claims slots for the rest by clock order (misses),
+// taking only slots not stamped by this call -- so nothing the call uses is
+// evicted -- and decodes the claimed blocks cluster by cluster.
+
+// Hits: every flagged key that already has a slot stamps it.
+__global__ void __launch_bounds__(256) k_resident_hits(const uint8_t *__restrict__ flags, int64_t n_keys,
+                                                       const uint32_t *__restrict__ slotmap,
+                                                       uint32_t *__restrict__ epoch, uint32_t cur) {
+    for (int64_t key = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; key < n_keys;
+         key += (int64_t)gridDim.x * blockDim.x) {
+        if (!flags[key]) continue;
+        const uint32_t s = slotmap[key];
+        if (s != kNone) epoch[s] = cur;
+    }
+}
+
+// Misses, one thread per (level-1 node, block): claim a slot for every
+// flagged camera without one; one decode item {cluster key, mask, -, -},
+// {slot of camera 0..3} per cluster with a claimed camera.
+__global__ void __launch_bounds__(256) k_resident_misses(const __grid_constant__ DevStream S,
+                                                         const uint8_t *__restrict__ flags,
+                                                         uint32_t *__restrict__ slotmap, uint32_t *__restrict__ owner,
+                                                         uint32_t *__restrict__ epoch, uint32_t *__restrict__ clock,
+                                                         uint32_t capacity, uint32_t cur, uint4 *__restrict__ items,
+                                                         unsigned long long *__restrict__ counters) {
+    const int64_t n_ck = (int64_t)S.gu[1] * S.gv[1] * S.nblocks;
+    const int64_t ck = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ck >= n_ck) return;
+    const int node = (int)(ck / S.nblocks), k = (int)(ck - (int64_t)node * S.nblocks);
+    const int a1 = node / S.gv[1], b1 = node - (node / S.gv[1]) * S.gv[1];
+    uint32_t mask = 0, slots[4] = {kNone, kNone, kNone, kNone};
+    for (int q = 0; q < 4; q++) {
+        const int i = 2 * a1 + (q >> 1), j = 2 * b1 + (q & 1);
+        if (i >= S.nu || j >= S.nv) continue;
+        const int64_t key = ((int64_t)i * S.nv + j) * S.nblocks + k;
+        if (!flags[key] || slotmap[key] != kNone) continue;
+        for (uint32_t tries = 0; tries < capacity; tries++) {
+            const uint32_t s = atomicAdd(clock, 1u) % capacity;
+            const uint32_t old = epoch[s];
+            if (old == cur || atomicCAS(&epoch[s], old, cur) != old) continue;
+            const uint32_t prev = owner[s];
+            if (prev != kNone) slotmap[prev] = kNone;      // not used by this call (its epoch was older)
+            owner[s] = (uint32_t)key;
+            slotmap[key] = s;
+            slots[q] = s;
+            mask |= 1u << q;
+            break;
+        }
+    }
+    if (!mask) return;
+    const unsigned long long old = atomicAdd(counters, (1ull << 32) | (unsigned long long)__popc(mask));
+    const uint32_t item = (uint32_t)(old >> 32);
+    items[2 * (size_t)item] = make_uint4((uint32_t)ck, mask, 0u, 0u);
+    items[2 * (size_t)item + 1] = make_uint4(slots[0], slots[1], slots[2], slots[3]);
+}
+
+// Decode the claimed blocks (as k_decode_blocks, with one slot per camera).
+template <int BS>
+__global__ void __launch_bounds__(256) k_decode_resident(const __grid_constant__ DevStream S,
+                                                        const uint4 *__restrict__ items,
+                                                        const unsigned long long *__restrict__ counters,
+                                                        uint32_t *__restrict__ cache) {
+    constexpr int kGroup = 4;
+    constexpr int kDescPer = (kMaxLevels - 1) * 3 + 4 * 3;
+    __shared__ LevelTabs T;
+    __shared__ Desc s_desc[kGroup * kDescPer];
+    load_tabs(S, T);
+    const Blk<BS> bk(S.B);
+    const int B = bk.size(), B2 = B * B;
+    const int L = S.L;
+    const uint32_t n = (uint32_t)(__ldg(counters) >> 32);
+    const size_t plane = (size_t)S.W * S.H;
+    const int nd = (L - 1) * 3 + 12;
+    __syncthreads();
+    for (uint32_t first = blockIdx.x * kGroup; first < n; first += gridDim.x * kGroup) {
+        for (int d = threadIdx.x; d < kGroup * nd; d += blockDim.x) {
+            const int gi = d / nd, e = d - gi * nd;
+            if (first + gi >= n) continue;
+            const uint4 it = __ldg(items + 2 * (size_t)(first + gi));
+            const int node = (int)(it.x / (uint32_t)S.nblocks), k = (int)(it.x - (uint32_t)node * S.nblocks);
+            const int a1 = node / T.gv[1], b1 = node - (node / T.gv[1]) * T.gv[1];
+            int l, a, b, c;
+            if (e < (L - 1) * 3) {
+                l = 1 + e / 3;
+                c = e - 3 * (l - 1);
+                a = a1 >> (l - 1);
+                b = b1 >> (l - 1);
+            } else {
+                const int q = (e - (L - 1) * 3) / 3;
+                c = (e - (L - 1) * 3) - 3 * q;
+                l = 0;
+                a = 2 * a1 + (q >> 1);
+                b = 2 * b1 + (q & 1);
+                if (!((it.y >> q) & 1u)) continue;
+            }
+            s_desc[d] = make_desc(S, T, bk, l, a, b, c, k % S.nbx, k / S.nbx);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < kGroup * B2; e += blockDim.x) {
+            const int gi = e / B2, p = e - gi * B2;
+            if (first + gi >= n) continue;
+            const uint4 it = __ldg(items + 2 * (size_t)(first + gi));
+            const uint4 sl = __ldg(items + 2 * (size_t)(first + gi) + 1);
+            const uint32_t slot[4] = {sl.x, sl.y, sl.z, sl.w};
+            const int node = (int)(it.x / (uint32_t)S.nblocks), k = (int)(it.x - (uint32_t)node * S.nblocks);
+            const int a1 = node / T.gv[1], b1 = node - (node / T.gv[1]) * T.gv[1];
+            const int bx = k % S.nbx, by = k / S.nbx;
+            const int yy = p / B, xx = p - yy * B;
+            const int bw = min(B, S.W - bx * B), bh = min(B, S.H - by * B);
+            const bool inside = xx < bw && yy < bh;
+            PixGeom g;
+            g.x = bx * B + min(xx, bw - 1);
+            g.y = by * B + min(yy, bh - 1);
+            g.blk = 0;
+            g.idx = (g.y - by * B) * bw + (g.x - bx * B);
+            g.toff = (g.y - by * B) * B + (g.x - bx * B);
+            const size_t rb = ((size_t)(a1 >> (L - 1)) * T.gv[L] + (b1 >> (L - 1))) * 3 * plane + (size_t)g.y * S.W + g.x;
+            int v[3] = {__ldg(S.roots + rb), __ldg(S.roots + rb + plane), __ldg(S.roots + rb + 2 * plane)};
+            const Desc *dd = s_desc + gi * nd;
+            for (int l = L - 1; l >= 1; l--) {
+                const bool ref = is_ref(a1 >> (l - 1), b1 >> (l - 1));
+#pragma unroll
+                for (int c = 0; c < 3; c++) v[c] += srv_desc(S, bk, dd[(l - 1) * 3 + c], ref, g);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                if (!((it.y >> q) & 1u)) continue;
+                const int i = 2 * a1 + (q >> 1), j = 2 * b1 + (q & 1);
+                const bool ref = is_ref(i, j);
+                const Desc *d0 = dd + (L - 1) * 3 + q * 3;
+                const int w0 = v[0] + srv_desc(S, bk, d0[0], ref, g);
+                const int w1 = v[1] + srv_desc(S, bk, d0[1], ref, g);
+                const int w2 = v[2] + srv_desc(S, bk, d0[2], ref, g);
+                cache[(size_t)slot[q] * B2 + p] = inside ? ycocg_to_rgb8(w0, w1, w2) : 0u;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1774,6 +1921,33 @@ cudaError_t launch_batch(int B, int tile_shape, const void *image, const int *pt
     HMLFC_DISPATCH_B(B, (e = batch_tiles<BS>(tile_shape, P, total_tiles, flags, slotmap, items, counters, work, cache,
                                              capacity, n_ck, group, persistent_ctas, d_out, phase, st)));
     return e;
+}
+
+__global__ void k_accumulate(const unsigned long long *__restrict__ counters, unsigned long long *__restrict__ totals) {
+    const unsigned long long c = counters[0];
+    totals[0] += c & 0xFFFFFFFFull;   // blocks decoded
+    totals[1] += c >> 32;             // decode items
+}
+
+cudaError_t launch_accumulate(const unsigned long long *counters, unsigned long long *totals, cudaStream_t st) {
+    k_accumulate<<<1, 1, 0, st>>>(counters, totals);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resident(const DevStream &ds, const uint8_t *flags, int64_t n_keys, uint32_t *slotmap,
+                            uint32_t *owner, uint32_t *epoch, uint32_t *clock, uint32_t capacity, uint32_t cur,
+                            uint4 *items, unsigned long long *counters, uint32_t *cache, int decode_grid,
+                            cudaStream_t st) {
+    const int64_t gk = (n_keys + 255) / 256;
+    k_resident_hits<<<(unsigned)(gk < 4096 ? gk : 4096), 256, 0, st>>>(flags, n_keys, slotmap, epoch, cur);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t n_ck = (int64_t)ds.gu[1] * ds.gv[1] * ds.nblocks;
+    k_resident_misses<<<(unsigned)((n_ck + 255) / 256), 256, 0, st>>>(ds, flags, slotmap, owner, epoch, clock,
+                                                                       capacity, cur, items, counters);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    HMLFC_DISPATCH_B(ds.B, (k_decode_resident<BS><<<decode_grid, 256, 0, st>>>(ds, items, counters, cache)));
+    return cudaGetLastError();
 }
 
 cudaError_t launch_render_relaxed(const DevStream &ds, const LaunchViews &lv, int total_tiles, const float *coeff,

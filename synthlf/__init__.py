@@ -166,12 +166,25 @@ def _render_view(scene: Scene, i: int, j: int) -> np.ndarray:
     return np.clip(np.floor(out + 0.5), 0, 255).astype(np.uint8)
 
 
-def render_lf(scene: Scene) -> np.ndarray:
-    """All camera views of the scene as ``uint8[nu][nv][H][W][3]``."""
+def render_lf(scene: Scene, threads: int = 0) -> np.ndarray:
+    """All camera views of the scene as ``uint8[nu][nv][H][W][3]``; views are
+    rendered on host threads (numpy releases the GIL), the bytes do not depend
+    on the thread count."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
     lf = np.empty((scene.nu, scene.nv, scene.height, scene.width, 3), np.uint8)
-    for i in range(scene.nu):
-        for j in range(scene.nv):
-            lf[i, j] = _render_view(scene, i, j)
+
+    def one(ij):
+        lf[ij[0], ij[1]] = _render_view(scene, ij[0], ij[1])
+
+    cams = [(i, j) for i in range(scene.nu) for j in range(scene.nv)]
+    n = threads or min(16, os.cpu_count() or 1)
+    if n <= 1 or len(cams) < 4:
+        for ij in cams:
+            one(ij)
+    else:
+        with ThreadPoolExecutor(n) as ex:
+            list(ex.map(one, cams))
     return lf
 
 
@@ -372,6 +385,42 @@ def batched_views(seed: int, cfgs, n_views: int = 256, sizes=(256, 384, 512, 640
         s = int(sizes[int(rng.integers(0, len(sizes)))])
         views += random_views(int(rng.integers(0, 2 ** 31)), geo, 1, [(s, s)], lf=lf)
     return views
+
+
+@dataclass
+class StereoRequest:
+    rid: int
+    arrival: float            # seconds after the start of the stream
+    left: View
+    right: View
+
+
+def stereo_requests(seed: int, geo: dict, n: int, rate: float,
+                    sizes=((512, 512), (1024, 1024), (1440, 1600)), ipd_frac: float = 0.02) -> list:
+    """A Poisson stream (rate per second) of stereo view pairs along a seeded
+    head-pose random walk in front of the (u,v) plane: the head moves by a
+    small random step per request and looks at a jittered point of the (s,t)
+    plane; the two eyes sit ipd_frac * grid extent apart along u."""
+    rng = np.random.default_rng(seed)
+    n_ext = max(geo["nu"], geo["nv"]) - 1
+    half_extent = 0.5 * geo["sigma"] * max(geo["width"], geo["height"])
+    head = np.array([geo["cu"], geo["cv"], -0.25 * geo["zf"]])
+    t = 0.0
+    out = []
+    for k in range(n):
+        t += float(rng.exponential(1.0 / rate))
+        head = head + np.array([rng.normal(0, 0.02 * n_ext), rng.normal(0, 0.02 * n_ext), rng.normal(0, 0.01 * geo["zf"])])
+        head[0] = min(max(head[0], geo["cu"] - 0.35 * n_ext), geo["cu"] + 0.35 * n_ext)
+        head[1] = min(max(head[1], geo["cv"] - 0.35 * n_ext), geo["cv"] + 0.35 * n_ext)
+        head[2] = min(max(head[2], -0.4 * geo["zf"]), -0.1 * geo["zf"])
+        w, h = sizes[int(rng.integers(0, len(sizes)))]
+        target = (geo["cu"] + rng.normal(0, 0.03 * n_ext), geo["cv"] + rng.normal(0, 0.03 * n_ext), geo["zf"])
+        half_fov = math.atan(half_extent / (geo["zf"] - head[2]))
+        d = 0.5 * ipd_frac * n_ext
+        left = pinhole_view(geo, head - np.array([d, 0, 0]), target, w, h, half_fov)
+        right = pinhole_view(geo, head + np.array([d, 0, 0]), target, w, h, half_fov)
+        out.append(StereoRequest(k, t, left, right))
+    return out
 
 
 def batched_workload(seed: int = 4):
