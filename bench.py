@@ -66,6 +66,16 @@ def make_workload(args):
     return c, lf, arr, size, tr, tp, t_gen
 
 
+def workload_config(c, qstep, tr, tp, size, n_views) -> dict:
+    """The `config` of both arms: the workload by what it is, with its sizes."""
+    return {
+        "workload": f"{c.name}: {c.nu}x{c.nv} grid of {c.width}x{c.height} RGB8 views, {c.n_planes} planes "
+                    f"0-{c.disp_max:g} px disparity, L={c.levels} B={c.block} quarter-pel MC Ws={c.search} "
+                    f"q={qstep} T=({tr},{tp}); step = {n_views}-pose circular path of {size}x{size} views",
+        "views_per_step": n_views,
+    }
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -178,8 +188,7 @@ def run_reference(args, rank, world):
         "value": rate, "unit": unit, "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * len(arr) / rate, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32 decode, f64 blend", "data": "synthetic",
-        "config": {"workload": f"{c.name}: {c.nu}x{c.nv}x{c.width}x{c.height} L={c.levels} B={c.block} "
-                               f"Ws={c.search} q={args.qstep}, {len(arr)}-pose path of {size}x{size} views"},
+        "config": workload_config(c, args.qstep, tr, tp, size, len(arr)),
         "cpu_baseline": {"value": rate, "unit": unit, "cores": os.cpu_count(), "kind": "oracle",
                          "sample": f"{per_step} random rays per step of the {len(arr)} views"},
         "e2e": {"value": rate, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -519,11 +528,7 @@ def main():
         "dtype": "int32 decode, fp32 blend",
         "data": "synthetic",
         "config": {
-            "workload": f"{c.name}: {c.nu}x{c.nv} grid of {c.width}x{c.height} RGB8 views, {c.n_planes} planes "
-                        f"0-{c.disp_max:g} px disparity, L={c.levels} B={c.block} quarter-pel MC Ws={c.search} "
-                        f"q={args.qstep} T=({tr},{tp}); step = {views_per_step}-pose circular path of "
-                        f"{size}x{size} views",
-            "views_per_step": views_per_step,
+            **workload_config(c, args.qstep, tr, tp, size, views_per_step),
             "l2": "flushed (256 MB write) before every timed step",
             "render_path": ["cached blocks", "direct per ray", "per-tile staging"][args.path],
         },
