@@ -975,31 +975,28 @@ __global__ void __launch_bounds__(128) k_mark(const __grid_constant__ DevStream 
         }
 }
 
-// Compact the flags into cache slots, cluster by cluster: a cluster key is a
-// (level-1 node, block) pair; its up to four cameras (the node's 2 x 2
-// children) get consecutive slots, and every cluster with a flagged camera
-// becomes one work item {cluster key, camera mask, first slot} of the decode.
+// Compact the flags into cache slots, super-item by super-item: a super key
+// is a (level-K node, block) pair, K = min(2, L); its up to (2^K)^2 cameras
+// get consecutive slots in camera order, and every super key with a flagged
+// camera becomes one decode item {super key, camera mask, first slot, 0}.
 // Keys beyond the capacity get no slot (kNone): their rays decode directly.
 __global__ void __launch_bounds__(256) k_assign(const __grid_constant__ DevStream S, const uint8_t *__restrict__ flags,
                                                 uint32_t *__restrict__ slotmap, uint4 *__restrict__ items,
                                                 unsigned long long *__restrict__ counters, uint32_t capacity) {
     __shared__ uint32_t s_warp[8][2];
     __shared__ uint32_t s_base[2];
-    const int64_t n_ck = (int64_t)S.gu[1] * S.gv[1] * S.nblocks;
-    const int64_t ck = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const int K = S.L < 2 ? S.L : 2, cpa = 1 << K;
+    const int64_t n_sk = (int64_t)S.gu[K] * S.gv[K] * S.nblocks;
+    const int64_t sk = (int64_t)blockIdx.x * 256 + threadIdx.x;
     uint32_t mask = 0;
-    int64_t keys[4];
-    if (ck < n_ck) {
-        const int node = (int)(ck / S.nblocks), k = (int)(ck - (int64_t)node * S.nblocks);
-        const int a1 = node / S.gv[1], b1 = node - (node / S.gv[1]) * S.gv[1];
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int i = 2 * a1 + (q >> 1), j = 2 * b1 + (q & 1);
-            keys[q] = -1;
-            if (i < S.nu && j < S.nv) {
-                keys[q] = ((int64_t)i * S.nv + j) * S.nblocks + k;
-                if (flags[keys[q]]) mask |= 1u << q;
-            }
+    int node = 0, k = 0;
+    if (sk < n_sk) {
+        node = (int)(sk / S.nblocks);
+        k = (int)(sk - (int64_t)node * S.nblocks);
+        const int aK = node / S.gv[K], bK = node - (node / S.gv[K]) * S.gv[K];
+        for (int q = 0; q < cpa * cpa; q++) {
+            const int i = aK * cpa + q / cpa, j = bK * cpa + q % cpa;
+            if (i < S.nu && j < S.nv && flags[((int64_t)i * S.nv + j) * S.nblocks + k]) mask |= 1u << q;
         }
     }
     const uint32_t nslot = __popc(mask), nitem = mask ? 1u : 0u;
@@ -1032,80 +1029,90 @@ __global__ void __launch_bounds__(256) k_assign(const __grid_constant__ DevStrea
         s_base[1] = (uint32_t)(old >> 32);
     }
     __syncthreads();
-    if (ck >= n_ck) return;
+    if (sk >= n_sk) return;
     const uint32_t slot0 = s_base[0] + s_warp[warp][0] + is - nslot;
     const uint32_t item = s_base[1] + s_warp[warp][1] + ii - nitem;
-    uint32_t slot = slot0;
     const bool fits = slot0 + nslot <= capacity;
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        if (keys[q] < 0) continue;
+    const int aK = node / S.gv[K], bK = node - (node / S.gv[K]) * S.gv[K];
+    uint32_t slot = slot0;
+    for (int q = 0; q < cpa * cpa; q++) {
+        const int i = aK * cpa + q / cpa, j = bK * cpa + q % cpa;
+        if (i >= S.nu || j >= S.nv) continue;
+        const int64_t key = ((int64_t)i * S.nv + j) * S.nblocks + k;
         if ((mask >> q) & 1u) {
-            slotmap[keys[q]] = fits ? slot : kNone;
+            slotmap[key] = fits ? slot : kNone;
             slot++;
         } else {
-            slotmap[keys[q]] = kNone;
+            slotmap[key] = kNone;
         }
     }
-    if (mask && fits) items[item] = make_uint4((uint32_t)ck, mask, slot0, 0u);
-    else if (mask) items[item] = make_uint4((uint32_t)ck, 0u, 0u, 0u);   // over capacity: nothing to decode
+    if (mask) items[item] = make_uint4((uint32_t)sk, fits ? mask : 0u, slot0, 0u);
 }
 
-// Decode the cached blocks, one (level-1 node, block) item at a time: the
-// level-1 reconstruction (root + SRV levels L-1 .. 1) of each pixel is shared
-// by the item's cameras, which then add their own level-0 SRV.  Persistent
-// CTAs; several items per pass when a block has fewer pixels than threads.
+// Decode the cached blocks, one super item ((level-K node, block), K =
+// min(2, L)) at a time: per pixel, the node's reconstruction (root + SRV
+// levels L-1 .. K) is evaluated once, level 1 once per active child node
+// (K = 2), and level 0 once per marked camera.  Persistent CTAs; several
+// items per pass so that one descriptor phase serves more pixel work.
 template <int BS>
 __global__ void __launch_bounds__(256) k_decode_blocks(const __grid_constant__ DevStream S,
                                                       const uint4 *__restrict__ items,
                                                       const unsigned long long *__restrict__ counters,
                                                       uint32_t *__restrict__ cache) {
-    constexpr int kMaxGroup = 16;                 // items per pass (B = 4)
-    constexpr int kMinGroup = 4;                  // items per pass at least (amortises the descriptor phase)
-    constexpr int kDescPer = (kMaxLevels - 1) * 3 + 4 * 3;
+    constexpr int kGroup = 4;                                   // items per pass
+    constexpr int kDescPer = (kMaxLevels - 2) * 3 + 4 * 3 + 16 * 3;
     __shared__ LevelTabs T;
-    __shared__ Desc s_desc[kMaxGroup * kDescPer];
+    __shared__ Desc s_desc[kGroup * kDescPer];
     load_tabs(S, T);
     const Blk<BS> bk(S.B);
     const int B = bk.size(), B2 = B * B;
-    const int G = max(B2 <= 256 ? kMinGroup : 1, min(kMaxGroup, (int)blockDim.x / B2));
-    const int L = S.L;
+    const int L = S.L, K = L < 2 ? L : 2, cpa = 1 << K;
+    const int n_sh = (L - K) * 3;                               // shared levels L-1 .. K
+    const int n_mid = K == 2 ? 12 : 0;                          // level 1 of the 4 child nodes
+    const int nd = n_sh + n_mid + cpa * cpa * 3;
     const uint32_t n = (uint32_t)(__ldg(counters) >> 32);
     const size_t plane = (size_t)S.W * S.H;
-    const int nd = (L - 1) * 3 + 12;              // descriptors per item
     __syncthreads();
-    for (uint32_t first = blockIdx.x * G; first < n; first += gridDim.x * G) {
-        for (int d = threadIdx.x; d < G * nd; d += blockDim.x) {
+    for (uint32_t first = blockIdx.x * kGroup; first < n; first += gridDim.x * kGroup) {
+        for (int d = threadIdx.x; d < kGroup * nd; d += blockDim.x) {
             const int gi = d / nd, e = d - gi * nd;
             if (first + gi >= n) continue;
             const uint4 it = __ldg(items + first + gi);
             if (!it.y) continue;
             const int node = (int)(it.x / (uint32_t)S.nblocks), k = (int)(it.x - (uint32_t)node * S.nblocks);
-            const int a1 = node / T.gv[1], b1 = node - (node / T.gv[1]) * T.gv[1];
+            const int aK = node / T.gv[K], bK = node - (node / T.gv[K]) * T.gv[K];
             int l, a, b, c;
-            if (e < (L - 1) * 3) {                // level l >= 1 of the shared path
-                l = 1 + e / 3;
-                c = e - 3 * (l - 1);
-                a = a1 >> (l - 1);
-                b = b1 >> (l - 1);
-            } else {                              // level 0 of camera q of the cluster
-                const int q = (e - (L - 1) * 3) / 3;
-                c = (e - (L - 1) * 3) - 3 * q;
+            if (e < n_sh) {
+                l = K + e / 3;
+                c = e - 3 * (l - K);
+                a = aK >> (l - K);
+                b = bK >> (l - K);
+            } else if (e < n_sh + n_mid) {
+                const int m = (e - n_sh) / 3;                   // child node m of level 1
+                c = (e - n_sh) - 3 * m;
+                l = 1;
+                a = 2 * aK + (m >> 1);
+                b = 2 * bK + (m & 1);
+                const uint32_t under = 0x33u << (8 * (m >> 1) + 2 * (m & 1));   // its 2x2 cameras in the 4x4 mask
+                if (!(it.y & under)) continue;
+            } else {
+                const int q = (e - n_sh - n_mid) / 3;
+                c = (e - n_sh - n_mid) - 3 * q;
                 l = 0;
-                a = 2 * a1 + (q >> 1);
-                b = 2 * b1 + (q & 1);
+                a = aK * cpa + q / cpa;
+                b = bK * cpa + q % cpa;
                 if (!((it.y >> q) & 1u)) continue;
             }
             s_desc[d] = make_desc(S, T, bk, l, a, b, c, k % S.nbx, k / S.nbx);
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < G * B2; e += blockDim.x) {
+        for (int e = threadIdx.x; e < kGroup * B2; e += blockDim.x) {
             const int gi = e / B2, p = e - gi * B2;
             if (first + gi >= n) continue;
             const uint4 it = __ldg(items + first + gi);
             if (!it.y) continue;
             const int node = (int)(it.x / (uint32_t)S.nblocks), k = (int)(it.x - (uint32_t)node * S.nblocks);
-            const int a1 = node / T.gv[1], b1 = node - (node / T.gv[1]) * T.gv[1];
+            const int aK = node / T.gv[K], bK = node - (node / T.gv[K]) * T.gv[K];
             const int bx = k % S.nbx, by = k / S.nbx;
             const int yy = p / B, xx = p - yy * B;
             const int bw = min(B, S.W - bx * B), bh = min(B, S.H - by * B);
@@ -1116,26 +1123,40 @@ __global__ void __launch_bounds__(256) k_decode_blocks(const __grid_constant__ D
             g.blk = 0;
             g.idx = (g.y - by * B) * bw + (g.x - bx * B);
             g.toff = (g.y - by * B) * B + (g.x - bx * B);
-            const size_t rb = ((size_t)(a1 >> (L - 1)) * T.gv[L] + (b1 >> (L - 1))) * 3 * plane + (size_t)g.y * S.W + g.x;
+            const size_t rb = ((size_t)(aK >> (L - K)) * T.gv[L] + (bK >> (L - K))) * 3 * plane + (size_t)g.y * S.W + g.x;
             int v[3] = {__ldg(S.roots + rb), __ldg(S.roots + rb + plane), __ldg(S.roots + rb + 2 * plane)};
             const Desc *dd = s_desc + gi * nd;
-            for (int l = L - 1; l >= 1; l--) {
-                const bool ref = is_ref(a1 >> (l - 1), b1 >> (l - 1));
+            for (int l = L - 1; l >= K; l--) {
+                const bool ref = is_ref(aK >> (l - K), bK >> (l - K));
 #pragma unroll
-                for (int c = 0; c < 3; c++) v[c] += srv_desc(S, bk, dd[(l - 1) * 3 + c], ref, g);
+                for (int c = 0; c < 3; c++) v[c] += srv_desc(S, bk, dd[(l - K) * 3 + c], ref, g);
             }
-            uint32_t slot = it.z;
+            const uint32_t mask = it.y;
+            const int nm = K == 2 ? 4 : 1;
+            for (int m = 0; m < nm; m++) {
+                int w[3] = {v[0], v[1], v[2]};
+                uint32_t cams = mask;                           // K = 1: the node's own cameras
+                if (K == 2) {
+                    const uint32_t under = 0x33u << (8 * (m >> 1) + 2 * (m & 1));
+                    cams = mask & under;
+                    if (!cams) continue;
+                    const bool ref = is_ref(2 * aK + (m >> 1), 2 * bK + (m & 1));
+                    const Desc *d1 = dd + n_sh + m * 3;
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                if (!((it.y >> q) & 1u)) continue;
-                const int i = 2 * a1 + (q >> 1), j = 2 * b1 + (q & 1);
-                const bool ref = is_ref(i, j);
-                const Desc *d0 = dd + (L - 1) * 3 + q * 3;
-                const int w0 = v[0] + srv_desc(S, bk, d0[0], ref, g);
-                const int w1 = v[1] + srv_desc(S, bk, d0[1], ref, g);
-                const int w2 = v[2] + srv_desc(S, bk, d0[2], ref, g);
-                cache[(size_t)slot * B2 + p] = inside ? ycocg_to_rgb8(w0, w1, w2) : 0u;
-                slot++;
+                    for (int c = 0; c < 3; c++) w[c] += srv_desc(S, bk, d1[c], ref, g);
+                }
+                while (cams) {
+                    const int q = __ffs(cams) - 1;
+                    cams &= cams - 1;
+                    const int i = aK * cpa + q / cpa, j = bK * cpa + q % cpa;
+                    const bool ref = is_ref(i, j);
+                    const Desc *d0 = dd + n_sh + n_mid + q * 3;
+                    const int z0 = w[0] + srv_desc(S, bk, d0[0], ref, g);
+                    const int z1 = w[1] + srv_desc(S, bk, d0[1], ref, g);
+                    const int z2 = w[2] + srv_desc(S, bk, d0[2], ref, g);
+                    const uint32_t slot = it.z + __popc(mask & ((1u << q) - 1u));
+                    cache[(size_t)slot * B2 + p] = inside ? ycocg_to_rgb8(z0, z1, z2) : 0u;
+                }
             }
         }
         __syncthreads();
@@ -1806,8 +1827,9 @@ cudaError_t launch_mark(const DevStream &ds, const LaunchViews &lv, int total_ti
 
 cudaError_t launch_assign(const DevStream &ds, const uint8_t *flags, uint32_t *slotmap, uint4 *items,
                           unsigned long long *counters, uint32_t capacity, cudaStream_t st) {
-    const int64_t n_ck = (int64_t)ds.gu[1] * ds.gv[1] * ds.nblocks;
-    const int64_t grid = (n_ck + 255) / 256;
+    const int K = ds.L < 2 ? ds.L : 2;
+    const int64_t n_sk = (int64_t)ds.gu[K] * ds.gv[K] * ds.nblocks;
+    const int64_t grid = (n_sk + 255) / 256;
     if (grid <= 0) return cudaSuccess;
     k_assign<<<(unsigned)grid, 256, 0, st>>>(ds, flags, slotmap, items, counters, capacity);
     return cudaGetLastError();
