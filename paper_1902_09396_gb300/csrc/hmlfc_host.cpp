@@ -235,6 +235,16 @@ int check_views(const hmlfc_stream *const *streams, int n_streams, const hmlfc_v
     return HMLFC_OK;
 }
 
+// Quotient multiplier for a view's tile index: floor((2^32 - 1) / d) + 1 (0
+// for d = 1), exact with __umulhi for n, d < 2^16; 1 (an impossible
+// multiplier) asks the kernel for a plain division when the view has 2^16
+// tiles or more.
+uint32_t tile_div_magic(const hmlfc_view &V) {
+    const int64_t d = (V.width + 15) / 16, n = d * ((V.height + 15) / 16);
+    if (n >= 65536) return 1u;
+    return d <= 1 ? 0u : (uint32_t)(0xFFFFFFFFull / (uint32_t)d) + 1u;
+}
+
 // The views of stream `lf`, in launch chunks that fit the by-value view table.
 int view_chunks(const hmlfc_view *views, int n_views, int lf, std::vector<LaunchViews> &chunks,
                 std::vector<int> &tiles) {
@@ -254,6 +264,7 @@ int view_chunks(const hmlfc_view *views, int n_views, int lf, std::vector<Launch
         for (size_t k = s; k < e; k++) {
             const hmlfc_view &V = views[idx[k]];
             lv.tile_start[k - s] = (int)t;
+            lv.tiles_x_magic[k - s] = tile_div_magic(V);
             lv.views[k - s] = V;
             t += (int64_t)((V.width + 15) / 16) * ((V.height + 15) / 16);
         }
@@ -278,6 +289,7 @@ int next_chunk(const hmlfc_view *views, int n_views, int lf, int *pos, LaunchVie
         (*pos)++;
         if (V.lf != lf || V.width <= 0 || V.height <= 0) continue;
         lv.tile_start[k] = (int)t;
+        lv.tiles_x_magic[k] = tile_div_magic(V);
         lv.views[k] = V;
         k++;
         t += (int64_t)((V.width + 15) / 16) * ((V.height + 15) / 16);

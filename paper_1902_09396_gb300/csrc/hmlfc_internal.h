@@ -46,6 +46,7 @@ struct LaunchViews {
     int n_views;
     int tile_w, tile_h;
     int tile_start[kMaxViewsPerLaunch + 1];
+    uint32_t tiles_x_magic[kMaxViewsPerLaunch];   // quotient multiplier of each view's tiles per row
     hmlfc_view views[kMaxViewsPerLaunch];
 };
 

@@ -316,9 +316,11 @@ __device__ __forceinline__ void ray_setup(const hmlfc_view &V, int nu, int nv, i
     r.ft = axis_nb(t, H, r.y0, r.y1);
 }
 
-// Byte k of a packed RGB8 sample as a float (exact: 2^23 + byte - 2^23).
+// Byte k of a packed RGB8 sample as a float: one byte permute builds the
+// float 2^23 + byte (exponent byte 0x4B, the sample byte in the low
+// mantissa), then 2^23 is subtracted (exact).
 __device__ __forceinline__ float byte_f(uint32_t p, int k) {
-    return __uint_as_float(0x4B000000u | ((p >> (8 * k)) & 0xFFu)) - 8388608.0f;
+    return __uint_as_float(__byte_perm(p, 0x4B000000u, 0x7440u + (uint32_t)k)) - 8388608.0f;
 }
 
 // Quadrilinear blend of the 16 samples, separably: the 2 x 2 pixels of each
@@ -678,10 +680,11 @@ __global__ void __launch_bounds__(TW *TH, 4) k_render(const __grid_constant__ De
         }
     }
     if (act) {
+        // write-streaming stores: the output must not evict the decode's working set from L2
         float *dst = out + V.out_offset + ((size_t)py * V.width + px) * 3;
-        dst[0] = o[0];
-        dst[1] = o[1];
-        dst[2] = o[2];
+        __stcs(dst, o[0]);
+        __stcs(dst + 1, o[1]);
+        __stcs(dst + 2, o[2]);
     }
 }
 
@@ -1185,12 +1188,15 @@ __global__ void __launch_bounds__(TW *TH) k_render_cached(const __grid_constant_
                                                          const __grid_constant__ LaunchViews LV,
                                                          const uint32_t *__restrict__ slotmap,
                                                          const uint32_t *__restrict__ cache, float *__restrict__ out) {
-    const int vi = find_view(LV, blockIdx.x);      // uniform over the CTA
+    int vi = 0;                                     // uniform over the CTA: one search per warp
+    if ((threadIdx.x & 31) == 0) vi = find_view(LV, blockIdx.x);
+    vi = __shfl_sync(0xFFFFFFFFu, vi, 0);
     const hmlfc_view &V = LV.views[vi];
-    const int tiles_x = (V.width + TW - 1) / TW;
     const int local = blockIdx.x - LV.tile_start[vi];
-    const int px = (local % tiles_x) * TW + (int)threadIdx.x % TW;
-    const int py = (local / tiles_x) * TH + (int)threadIdx.x / TW;
+    const uint32_t mag = LV.tiles_x_magic[vi];
+    const int ty = mag == 1u ? local / ((V.width + TW - 1) / TW) : qdiv(local, mag);
+    const int px = (local - ty * ((V.width + TW - 1) / TW)) * TW + (int)threadIdx.x % TW;
+    const int py = ty * TH + (int)threadIdx.x / TW;
     if (px >= V.width || py >= V.height) return;
     const Blk<BS> bk(S.B);
     const int B = bk.size();
@@ -1225,10 +1231,10 @@ __global__ void __launch_bounds__(TW *TH) k_render_cached(const __grid_constant_
     } else {
         blend_direct(S, bk, r, o);         // a sample beyond the cache capacity: decode this ray directly
     }
-    float *dst = out + V.out_offset + ((size_t)py * V.width + px) * 3;
-    dst[0] = o[0];
-    dst[1] = o[1];
-    dst[2] = o[2];
+    float *dst = out + V.out_offset + ((size_t)py * V.width + px) * 3;   // write-streaming (see above)
+    __stcs(dst, o[0]);
+    __stcs(dst + 1, o[1]);
+    __stcs(dst + 2, o[2]);
 }
 
 template <int BS>
@@ -1625,10 +1631,11 @@ __global__ void __launch_bounds__(TW *TH) k_render_batch(const BatchPtrs P, cons
             blend16(r, [&](int, int, int, int, int i, int j, int x, int y) { return sample_direct(S, s_T, bk, i, j, x, y); },
                     o);
         }
+        // write-streaming stores: the output must not evict the decode's working set from L2
         float *dst = out + V.out_offset + ((size_t)py * V.width + px) * 3;
-        dst[0] = o[0];
-        dst[1] = o[1];
-        dst[2] = o[2];
+        __stcs(dst, o[0]);
+        __stcs(dst + 1, o[1]);
+        __stcs(dst + 2, o[2]);
     }
 }
 
