@@ -287,6 +287,23 @@ int hmlfc_encode(const uint8_t *h_lf, int nu, int nv, int width, int height, con
                  void **h_out, size_t *nbytes);
 
 /*
+ * Encode on the GPU: the same stream, byte for byte, as hmlfc_encode with the
+ * same arguments (Sec. 4.3-4.7).  The closed loop runs top down, one grid per
+ * level and member class (references first, then the predictive members
+ * against them); the block search of Sec. 4.4 (Eq. 1-2, both signs, integer
+ * stage then quarter-pel refinement) runs one CTA per block.
+ * d_lf: device memory, uint8 [nu][nv][H][W][3] RGB, caller-owned, read only.
+ * The library allocates its device scratch (about 11x the light field's
+ * bytes) and frees it before returning; *h_out is host memory, released with
+ * hmlfc_free_host.  p->threads is ignored.  Work runs on cuda_stream, which is
+ * synchronised before the call returns.  Errors: as hmlfc_encode;
+ * HMLFC_E_UNSUPPORTED also for a search window above 32 with mc 1 or 3;
+ * HMLFC_E_OOM when the scratch cannot be allocated; HMLFC_E_CUDA.
+ */
+int hmlfc_encode_device(const uint8_t *d_lf, int nu, int nv, int width, int height, const hmlfc_encode_params *p,
+                        void *cuda_stream, void **h_out, size_t *nbytes);
+
+/*
  * Re-encode a stream with new coefficients (float [n_nc][H][W], host) and
  * roots (float [n_roots][3][H][W], host) at the same quantiser step, motion
  * vectors and signs: coefficients are rounded to the nearest multiple of q,

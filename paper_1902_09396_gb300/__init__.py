@@ -77,6 +77,7 @@ def lib() -> C.CDLL:
     L.hmlfc_render_backward.argtypes = [P, I, P, I, P, P, P, P]
     L.hmlfc_dequant.argtypes = [P, P, P, P]
     L.hmlfc_encode.argtypes = [P, I, I, I, I, C.POINTER(EncodeParams), C.POINTER(P), C.POINTER(SZ)]
+    L.hmlfc_encode_device.argtypes = [P, I, I, I, I, C.POINTER(EncodeParams), P, C.POINTER(P), C.POINTER(SZ)]
     L.hmlfc_requantize.argtypes = [P, P, P, C.POINTER(P), C.POINTER(SZ)]
     L.hmlfc_free_host.argtypes = [P]
     L.hmlfc_free_host.restype = None
@@ -267,6 +268,30 @@ def encode(lf: np.ndarray, levels: int, block: int, search: int, qstep: int, t_r
     out = C.c_void_p()
     n = C.c_size_t()
     _check(lib().hmlfc_encode(lf.ctypes.data_as(C.c_void_p), nu, nv, W, H, C.byref(prm), C.byref(out), C.byref(n)))
+    data = C.string_at(out, n.value)
+    lib().hmlfc_free_host(out)
+    return data
+
+
+def encode_device(lf, levels: int, block: int, search: int, qstep: int, t_ref: int = 0, t_pred: int = 0,
+                  mc: int = MC_QPEL, cuda_stream=None) -> bytes:
+    """Encode on the GPU; the same stream as encode().  lf: uint8
+    [nu][nv][H][W][3], a CUDA tensor (used in place) or a host array (copied
+    to the device first)."""
+    import torch
+    if not isinstance(lf, torch.Tensor):
+        lf = torch.from_numpy(np.ascontiguousarray(lf, np.uint8))
+    if not lf.is_cuda:
+        lf = lf.cuda()
+    if lf.dtype != torch.uint8 or lf.dim() != 5 or lf.shape[4] != 3:
+        raise ValueError("lf must be uint8 [nu][nv][H][W][3]")
+    lf = lf.contiguous()
+    nu, nv, H, W, _ = lf.shape
+    prm = EncodeParams(levels, block, search, qstep, t_ref, t_pred, mc, 0)
+    out = C.c_void_p()
+    n = C.c_size_t()
+    _check(lib().hmlfc_encode_device(_ptr(lf), nu, nv, W, H, C.byref(prm), _stream_handle(cuda_stream),
+                                     C.byref(out), C.byref(n)))
     data = C.string_at(out, n.value)
     lib().hmlfc_free_host(out)
     return data

@@ -17,7 +17,7 @@ CSRC = PKG / "csrc"
 OUT_DIR = PKG / "_build"
 LIB = OUT_DIR / "libhmlfc.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["hmlfc_kernels.cu", "hmlfc_host.cpp", "hmlfc_encode.cpp", "hmlfc_touched.cpp"]
+SOURCES = ["hmlfc_kernels.cu", "hmlfc_encode_gpu.cu", "hmlfc_host.cpp", "hmlfc_encode.cpp", "hmlfc_touched.cpp"]
 
 
 def _cuda_home() -> Path:

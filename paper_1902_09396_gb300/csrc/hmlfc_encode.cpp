@@ -264,7 +264,9 @@ int serialise(const Geometry &g, const std::vector<int16_t> &roots, const std::v
     return HMLFC_OK;
 }
 
-void fill_geometry(Geometry &g, int nu, int nv, int W, int H, int L, int B, int Ws, int q, int tr, int tp, int mc) {
+}  // namespace
+
+void hmlfc::fill_geometry(Geometry &g, int nu, int nv, int W, int H, int L, int B, int Ws, int q, int tr, int tp, int mc) {
     std::memset(&g, 0, sizeof g);
     g.nu = nu; g.nv = nv; g.W = W; g.H = H; g.L = L; g.B = B; g.Ws = Ws; g.q = q; g.t_ref = tr; g.t_pred = tp;
     g.mc = mc ? 1 : 0;
@@ -285,8 +287,6 @@ void fill_geometry(Geometry &g, int nu, int nv, int W, int H, int L, int B, int 
     g.n_nc = nc;
     g.n_roots = (int64_t)g.gu[L] * g.gv[L];
 }
-
-}  // namespace
 
 extern "C" int hmlfc_encode(const uint8_t *h_lf, int nu, int nv, int W, int H, const hmlfc_encode_params *p,
                             void **h_out, size_t *nbytes) {

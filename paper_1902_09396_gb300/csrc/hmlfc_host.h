@@ -55,6 +55,10 @@ inline void bise_choose(uint64_t range, int &mode, int &b) {
     else { mode = 2; b = bq; }
 }
 
+// Geometry of a stream about to be encoded (header fields, level grids and
+// breadth-first node-channel bases; no section offsets or counts).
+void fill_geometry(Geometry &g, int nu, int nv, int W, int H, int L, int B, int Ws, int q, int tr, int tp, int mc);
+
 // Run fn(item) for item in [0, n) on up to `threads` host threads.
 void parallel_for(int64_t n, int threads, const std::function<void(int64_t)> &fn);
 

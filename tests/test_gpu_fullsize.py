@@ -2,8 +2,8 @@
 benchmark times: 17x17 grid of 512x512 views, L=4, B=16, quarter-pel MC,
 q=4, thresholds (400, 800), the 64-pose circular path of 512x512 views.
 
-The stream is encoded by the oracle.  Checked: the product encoder writes the
-same bytes; 10^6 random samples decode bit-exactly; 30,000 sampled output
+The stream is encoded by the oracle.  Checked: the product's host and device
+encoders write the same bytes; 10^6 random samples decode bit-exactly; 30,000 sampled output
 pixels of the 64 views (rendered by the benchmark's cached path, the batched
 pass and the per-tile path) are within 1e-3 of the oracle's FP64
 random-access render of the same pixels.
@@ -34,6 +34,13 @@ def test_product_encoder_bytes_at_full_size(paper):
     import paper_1902_09396_gb300 as H
     torch, c, lf, data, _ = paper
     assert H.encode(lf, c.levels, c.block, c.search, c.qstep, t_ref=400, t_pred=800) == data
+
+
+def test_device_encoder_bytes_at_full_size(paper):
+    import paper_1902_09396_gb300 as H
+    torch, c, lf, data, _ = paper
+    d = torch.from_numpy(lf).cuda()
+    assert H.encode_device(d, c.levels, c.block, c.search, c.qstep, t_ref=400, t_pred=800) == data
 
 
 def test_million_samples_bit_exact(paper):
