@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU baseline sample")
     ap.add_argument("--traffic-json", default=os.path.join(ROOT, "profiles", "decode_traffic.json"))
     ap.add_argument("--path", type=int, default=0, help="render path: 0 cached blocks, 1 direct, 2 per-tile")
-    ap.add_argument("--form", default="plain", choices=["plain", "diff", "batched", "serve"],
+    ap.add_argument("--form", default="plain", choices=["plain", "diff", "batched", "serve", "encode"],
                     help="plain: the paper-scale render step (default); diff: 200 Adam steps of the "
                          "differentiable form")
     return ap.parse_args()
@@ -378,8 +378,112 @@ def run_serve(args):
     }), flush=True)
 
 
+def run_encode(args):
+    """Device encoder (hmlfc_encode_device) on the paper-scale light field:
+    one step encodes the whole 17x17x512^2 field, from the device-resident
+    RGB8 views to the stream's bytes in host memory, and is checked equal to
+    the host encoder's stream.  Roofline of the block-search passes: the
+    algorithmic integer operations of Eq. 1-2 (3 per integer-stage term:
+    difference, absolute value, accumulate; 13 per refinement term: the 4-tap
+    bilinear with its rounding, 9, then sign, difference, absolute value,
+    accumulate) over their event-timed duration, against the issue-limited
+    lane-operation rate (152 SMs x 4 schedulers x 32 lanes x SM clock)."""
+    import torch
+    import oracle
+    import paper_1902_09396_gb300 as H
+
+    c = synthlf.CONFIGS[args.config]
+    tr, tp = (WORKLOAD["t_ref"], WORKLOAD["t_pred"]) if args.config == "paper" else (0, 0)
+    lf = synthlf.make_lf(c.seed, c.nu, c.nv, c.width, c.height, c.n_planes, c.disp_max, c.texture)
+    n_views = c.nu * c.nv
+    view_units = n_views * c.width * c.height / (512.0 * 512.0)
+    prm = dict(t_ref=tr, t_pred=tp)
+    t0 = time.time()
+    host = H.encode(lf, c.levels, c.block, c.search, args.qstep, **prm)
+    t_host = time.time() - t0
+    d_lf = torch.from_numpy(lf).cuda()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * c.levels)]
+    st = {}
+    for _ in range(max(args.warmup, 3)):
+        out = H.encode_device(d_lf, c.levels, c.block, c.search, args.qstep, stats=st, **prm)
+    assert out == host, "device stream differs from the host encoder's"
+    steps = min(args.steps, 50)
+    H.set_encode_events(ev)
+    clocks = ClockSampler(torch.cuda.current_device())
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tot, search_ms = 0.0, 0.0
+    for _ in range(steps):
+        a.record(stream)
+        out = H.encode_device(d_lf, c.levels, c.block, c.search, args.qstep, **prm)
+        b.record(stream)
+        torch.cuda.synchronize()
+        tot += a.elapsed_time(b)
+        search_ms += sum(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(c.levels))
+    H.set_encode_events(None)
+    ck = clocks.stop()
+    ms = tot / steps
+    search_ms /= steps
+    # end to end: RGB8 views from pinned host memory, stream bytes back to the host
+    pinned = torch.from_numpy(lf).pin_memory()
+    e2e_ms = 0.0
+    for _ in range(min(steps, 10)):
+        torch.cuda.synchronize()
+        a.record(stream)
+        dl = pinned.cuda(non_blocking=True)
+        out = H.encode_device(dl, c.levels, c.block, c.search, args.qstep, **prm)
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms += a.elapsed_time(b)
+        del dl
+    e2e_ms /= min(steps, 10)
+    ops = 3 * st["int_terms"] + 13 * st["frac_terms"]
+    sm_mhz = (ck or {}).get("sm_max_mhz") or 2070.0
+    peak = 152 * 4 * 32 * sm_mhz * 1e6 / 1e9              # Gop/s, issue-limited
+    achieved = ops / (search_ms / 1000.0) / 1e9
+    # CPU baseline: the oracle's encoder on a crop of every view (all rows of
+    # the grid, the first 128 image rows), scaled to 512x512 view units
+    cpu = None
+    if not args.no_cpu_baseline:
+        rows = min(c.height, 128)
+        crop = np.ascontiguousarray(lf[:, :, :rows])
+        t0 = time.time()
+        oracle.encode(crop, c.levels, c.block, c.search, args.qstep, **prm)
+        t_cpu = time.time() - t0
+        units = n_views * c.width * rows / (512.0 * 512.0)
+        cpu = {"value": units / t_cpu, "unit": "512x512 views/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"oracle encoder on the first {rows} rows of all {n_views} views ({t_cpu:.1f} s, "
+                         f"{os.cpu_count()} threads)"}
+    n_px = n_views * c.width * c.height
+    print(json.dumps({
+        "metric": "light-field views encoded/s (device encoder, closed-loop HMLFC with quarter-pel search)",
+        "value": view_units / (ms / 1000.0), "unit": "512x512 views/s", "n_gpus": 1, "steps": steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"{c.name}: {c.nu}x{c.nv} grid of {c.width}x{c.height} RGB8 views, L={c.levels} "
+                               f"B={c.block} quarter-pel MC Ws={c.search} q={args.qstep} T=({tr},{tp}); step = "
+                               "encode of the whole field to host stream bytes",
+                   "l2": f"input {lf.nbytes / 1e6:.0f} MB > L2"},
+        "search_ms": search_ms, "host_encoder_s": t_host, "stream_bytes": len(out), "bpp": len(out) * 8.0 / n_px,
+        "stats": st,
+        "roofline": {"bound": "alu", "kernel": "k_enc_block (block-search passes)", "achieved": achieved,
+                     "peak": peak, "unit": "Gop/s", "frac": achieved / peak, "traffic": None,
+                     "algorithmic_ops_per_step": ops,
+                     "note": "peak = issue-limited lane operations (152 SMs x 4 x 32 x max SM clock); ops = 3 per "
+                             "integer-stage term + 13 per refinement term of Eq. 1-2"},
+        "e2e": {"value": view_units / (e2e_ms / 1000.0), "unit": "512x512 views/s",
+                "h2d_bytes_per_step": int(lf.nbytes), "d2h_bytes_per_step": len(out)},
+        "gpu_launches": steps * (1 + c.levels + 2 * c.levels + 3 + 3),
+        "clocks": ck, "cpu_baseline": cpu,
+    }), flush=True)
+
+
 def main():
     args = parse()
+    if args.form == "encode":
+        run_encode(args)
+        return
     if args.form == "serve":
         run_serve(args)
         return

@@ -286,6 +286,15 @@ typedef struct {
 int hmlfc_encode(const uint8_t *h_lf, int nu, int nv, int width, int height, const hmlfc_encode_params *p,
                  void **h_out, size_t *nbytes);
 
+/* Work done by one device encode (all counts over the whole light field). */
+typedef struct {
+    uint64_t blocks;            /* (node-channel, block) pairs coded */
+    uint64_t sig_blocks;        /* of which significant (a record in the stream) */
+    uint64_t blocks_searched;   /* predictive blocks run through the block search (mc 1 or 3) */
+    uint64_t int_terms;         /* |S - R| and |S + R| terms of the integer stage (Eq. 1-2), both signs */
+    uint64_t frac_terms;        /* |S -+ P| terms of the quarter-pel refinement, P bilinear (mc 1) */
+} hmlfc_encode_stats;
+
 /*
  * Encode on the GPU: the same stream, byte for byte, as hmlfc_encode with the
  * same arguments (Sec. 4.3-4.7).  The closed loop runs top down, one grid per
@@ -299,9 +308,19 @@ int hmlfc_encode(const uint8_t *h_lf, int nu, int nv, int width, int height, con
  * synchronised before the call returns.  Errors: as hmlfc_encode;
  * HMLFC_E_UNSUPPORTED also for a search window above 32 with mc 1 or 3;
  * HMLFC_E_OOM when the scratch cannot be allocated; HMLFC_E_CUDA.
+ * stats (may be NULL) receives the work counts of this call.
  */
 int hmlfc_encode_device(const uint8_t *d_lf, int nu, int nv, int width, int height, const hmlfc_encode_params *p,
-                        void *cuda_stream, void **h_out, size_t *nbytes);
+                        void *cuda_stream, void **h_out, size_t *nbytes, hmlfc_encode_stats *stats);
+
+/*
+ * Events (cudaEvent_t, caller-owned) that hmlfc_encode_device records on its
+ * stream around the block-search pass of each level, top level first:
+ * events[2 i] before and events[2 i + 1] after the pass of level L-1-i.
+ * n = 0 (events may be NULL) turns the recording off; n <= 32.  Process-wide
+ * setting, not thread-safe.
+ */
+int hmlfc_set_encode_events(void *const *events, int n);
 
 /*
  * Re-encode a stream with new coefficients (float [n_nc][H][W], host) and

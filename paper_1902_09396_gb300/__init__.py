@@ -55,6 +55,11 @@ class EncodeParams(C.Structure):
 _lib = None
 
 
+class EncodeStats(C.Structure):
+    _fields_ = [("blocks", C.c_uint64), ("sig_blocks", C.c_uint64), ("blocks_searched", C.c_uint64),
+                ("int_terms", C.c_uint64), ("frac_terms", C.c_uint64)]
+
+
 def lib() -> C.CDLL:
     """Load libhmlfc.so (building it first if it is missing or stale)."""
     global _lib
@@ -77,7 +82,9 @@ def lib() -> C.CDLL:
     L.hmlfc_render_backward.argtypes = [P, I, P, I, P, P, P, P]
     L.hmlfc_dequant.argtypes = [P, P, P, P]
     L.hmlfc_encode.argtypes = [P, I, I, I, I, C.POINTER(EncodeParams), C.POINTER(P), C.POINTER(SZ)]
-    L.hmlfc_encode_device.argtypes = [P, I, I, I, I, C.POINTER(EncodeParams), P, C.POINTER(P), C.POINTER(SZ)]
+    L.hmlfc_encode_device.argtypes = [P, I, I, I, I, C.POINTER(EncodeParams), P, C.POINTER(P), C.POINTER(SZ),
+                                      C.POINTER(EncodeStats)]
+    L.hmlfc_set_encode_events.argtypes = [P, I]
     L.hmlfc_requantize.argtypes = [P, P, P, C.POINTER(P), C.POINTER(SZ)]
     L.hmlfc_free_host.argtypes = [P]
     L.hmlfc_free_host.restype = None
@@ -251,8 +258,22 @@ def set_phase_events(events):
     if events is None:
         _check(lib().hmlfc_set_phase_events(None))
         return
+    for e in events:
+        e.record()            # torch creates the CUDA event at its first record
     arr = (C.c_void_p * 4)(*[int(e.cuda_event) for e in events])
     _check(lib().hmlfc_set_phase_events(arr))
+
+
+def set_encode_events(events):
+    """torch.cuda.Event list (2 per level, top level first) recorded around
+    the block-search passes of encode_device; None turns it off."""
+    if not events:
+        _check(lib().hmlfc_set_encode_events(None, 0))
+        return
+    for e in events:
+        e.record()            # torch creates the CUDA event at its first record
+    arr = (C.c_void_p * len(events))(*[int(e.cuda_event) for e in events])
+    _check(lib().hmlfc_set_encode_events(arr, len(events)))
 
 
 def set_block_cache_bytes(n: int):
@@ -274,10 +295,10 @@ def encode(lf: np.ndarray, levels: int, block: int, search: int, qstep: int, t_r
 
 
 def encode_device(lf, levels: int, block: int, search: int, qstep: int, t_ref: int = 0, t_pred: int = 0,
-                  mc: int = MC_QPEL, cuda_stream=None) -> bytes:
+                  mc: int = MC_QPEL, cuda_stream=None, stats: dict | None = None) -> bytes:
     """Encode on the GPU; the same stream as encode().  lf: uint8
     [nu][nv][H][W][3], a CUDA tensor (used in place) or a host array (copied
-    to the device first)."""
+    to the device first).  A dict passed as stats receives the work counts."""
     import torch
     if not isinstance(lf, torch.Tensor):
         lf = torch.from_numpy(np.ascontiguousarray(lf, np.uint8))
@@ -290,8 +311,11 @@ def encode_device(lf, levels: int, block: int, search: int, qstep: int, t_ref: i
     prm = EncodeParams(levels, block, search, qstep, t_ref, t_pred, mc, 0)
     out = C.c_void_p()
     n = C.c_size_t()
+    st = EncodeStats()
     _check(lib().hmlfc_encode_device(_ptr(lf), nu, nv, W, H, C.byref(prm), _stream_handle(cuda_stream),
-                                     C.byref(out), C.byref(n)))
+                                     C.byref(out), C.byref(n), C.byref(st)))
+    if stats is not None:
+        stats.update({k: int(getattr(st, k)) for k, _ in EncodeStats._fields_})
     data = C.string_at(out, n.value)
     lib().hmlfc_free_host(out)
     return data

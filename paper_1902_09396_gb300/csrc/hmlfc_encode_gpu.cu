@@ -42,6 +42,13 @@ struct EncItem {
 
 enum EncErr : int { kErrRange = 1, kErrGroup = 2 };
 
+constexpr int kCounters = 64;               // spread work counters over this many words
+
+// Events recorded around the predictive (block-search) pass of each level,
+// from the top level down: events[2 i] before and events[2 i + 1] after.
+cudaEvent_t g_enc_events[2 * kMaxLevels];
+int g_n_enc_events = 0;
+
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
 __device__ __forceinline__ int quant(int r, int q) {
@@ -140,7 +147,8 @@ __global__ void __launch_bounds__(kEncThreads) k_enc_block(
     const EncGeo G, const EncItem *__restrict__ items, const int16_t *__restrict__ child_lev,
     const int16_t *__restrict__ par_recon, const int16_t *__restrict__ rhat_in, int16_t *__restrict__ recon_out,
     int16_t *__restrict__ rhat_out, int16_t *__restrict__ lvbuf, uint32_t *__restrict__ hdr,
-    unsigned long long *__restrict__ val, uint32_t *__restrict__ mvsym, int *__restrict__ err) {
+    unsigned long long *__restrict__ val, uint32_t *__restrict__ mvsym, int *__restrict__ err,
+    unsigned long long *__restrict__ frac_terms) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long s_key[2];
     __shared__ int s_mv[3];
@@ -244,6 +252,13 @@ __global__ void __launch_bounds__(kEncThreads) k_enc_block(
                 }
                 best = warp_min_u64(best);
                 if (lane == 0) {
+                    // refinement terms evaluated for this sign (work counter)
+                    int vx = 0, vy = 0;
+                    for (int o = -3; o <= 3; o++) {
+                        vx += abs(cx + o) <= 4 * Ws;
+                        vy += abs(cy + o) <= 4 * Ws;
+                    }
+                    atomicAdd(frac_terms + (blockIdx.x & (kCounters - 1)), (unsigned long long)(vx * vy - 1) * n);
                     const uint32_t ic = (uint32_t)(s_key[warp] >> 32);
                     int rx = cx, ry = cy;
                     uint32_t bc = ic;
@@ -541,21 +556,30 @@ int enc_fail(cudaError_t e, const char *what) {
 template <bool PRED, int SEARCH, bool ZMV>
 cudaError_t launch_pass(const EncGeo &G, int n_items, const EncItem *items, const int16_t *child, const int16_t *par,
                         const int16_t *rhat_in, int16_t *recon, int16_t *rhat_out, int16_t *lvbuf, uint32_t *hdr,
-                        unsigned long long *val, uint32_t *mvsym, int *err, size_t smem, cudaStream_t st) {
+                        unsigned long long *val, uint32_t *mvsym, int *err, unsigned long long *frac,
+                        size_t smem, cudaStream_t st) {
     auto kern = k_enc_block<PRED, SEARCH, ZMV>;
     if (smem > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     kern<<<(unsigned)((int64_t)n_items * G.nblocks), kEncThreads, smem, st>>>(G, items, child, par, rhat_in, recon,
-                                                                            rhat_out, lvbuf, hdr, val, mvsym, err);
+                                                                            rhat_out, lvbuf, hdr, val, mvsym, err,
+                                                                            frac);
     return cudaGetLastError();
 }
 
 }  // namespace
 
+extern "C" int hmlfc_set_encode_events(void *const *events, int n) {
+    if (n < 0 || n > 2 * kMaxLevels || (n > 0 && !events)) return fail(HMLFC_E_INVALID_ARG, "encode events");
+    for (int i = 0; i < n; i++) g_enc_events[i] = static_cast<cudaEvent_t>(events[i]);
+    g_n_enc_events = n;
+    return HMLFC_OK;
+}
+
 extern "C" int hmlfc_encode_device(const uint8_t *d_lf, int nu, int nv, int W, int H, const hmlfc_encode_params *p,
-                                   void *cuda_stream, void **h_out, size_t *nbytes) {
+                                   void *cuda_stream, void **h_out, size_t *nbytes, hmlfc_encode_stats *stats) {
     if (!d_lf || !p || !h_out || !nbytes) return fail(HMLFC_E_INVALID_ARG, "NULL argument");
     if (nu < 1 || nv < 1 || W < 1 || H < 1 || nu > 65536 || nv > 65536 || W > 65536 || H > 65536)
         return fail(HMLFC_E_INVALID_ARG, "light-field size");
@@ -616,7 +640,8 @@ extern "C" int hmlfc_encode_device(const uint8_t *d_lf, int nu, int nv, int W, i
                  o_hdr = up(o_lvb + (size_t)nkeys * B * B * 2), o_val = up(o_hdr + (size_t)nkeys * 4),
                  o_pre = up(o_val + (size_t)nkeys * 8), o_part = up(o_pre + (size_t)nkeys * 8),
                  o_mv = up(o_part + (size_t)(nparts + 1) * 8), o_items = up(o_mv + (size_t)n_pred_mc * g.nblocks * 4),
-                 o_err = up(o_items + items.size() * sizeof(EncItem)), total_scratch = up(o_err + 16);
+                 o_err = up(o_items + items.size() * sizeof(EncItem)), o_cnt = up(o_err + 16),
+                 total_scratch = up(o_cnt + kCounters * 8);
     DevBuf scratch;
     cudaError_t e = cudaMalloc(&scratch.p, total_scratch);
     if (e != cudaSuccess) {
@@ -635,9 +660,11 @@ extern "C" int hmlfc_encode_device(const uint8_t *d_lf, int nu, int nv, int W, i
     uint32_t *mvsym = reinterpret_cast<uint32_t *>(base + o_mv);
     EncItem *d_items = reinterpret_cast<EncItem *>(base + o_items);
     int *d_err = reinterpret_cast<int *>(base + o_err);
+    unsigned long long *d_cnt = reinterpret_cast<unsigned long long *>(base + o_cnt);
 
     e = cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(EncItem), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, 16, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, kCounters * 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(rhat, 0, lvl0, st);
     if (e == cudaSuccess) {
         const int64_t n = n_views * plane;
@@ -667,27 +694,30 @@ extern "C" int hmlfc_encode_device(const uint8_t *d_lf, int nu, int nv, int W, i
             const int64_t i0 = item_first[l][0][0], ni = item_first[l][0][1] - i0;
             if (ni > 0)
                 e = launch_pass<false, 0, false>(G, (int)ni, d_items + i0, child, par, nullptr, out, rhat, lvbuf, hdr,
-                                                 val, mvsym, d_err, smem_base, st);
+                                                 val, mvsym, d_err, d_cnt, smem_base, st);
         }
         // pass 1: predictive members against the reference member's dequantised SRV
+        const int ev = 2 * (L - 1 - l);
+        if (e == cudaSuccess && ev + 1 < g_n_enc_events) e = cudaEventRecord(g_enc_events[ev], st);
         if (e == cudaSuccess) {
             G.thr = g.t_pred;
             const int64_t i0 = item_first[l][1][0], ni = item_first[l][1][1] - i0;
             if (ni > 0) {
                 if (p->mc == 0)
                     e = launch_pass<true, 0, false>(G, (int)ni, d_items + i0, child, par, rhat, out, nullptr, lvbuf,
-                                                    hdr, val, mvsym, d_err, smem_base, st);
+                                                    hdr, val, mvsym, d_err, d_cnt, smem_base, st);
                 else if (p->mc == 2)
                     e = launch_pass<true, 0, true>(G, (int)ni, d_items + i0, child, par, rhat, out, nullptr, lvbuf,
-                                                   hdr, val, mvsym, d_err, smem_base, st);
+                                                   hdr, val, mvsym, d_err, d_cnt, smem_base, st);
                 else if (search_mode == 1)
                     e = launch_pass<true, 1, false>(G, (int)ni, d_items + i0, child, par, rhat, out, nullptr, lvbuf,
-                                                    hdr, val, mvsym, d_err, smem_search, st);
+                                                    hdr, val, mvsym, d_err, d_cnt, smem_search, st);
                 else
                     e = launch_pass<true, 2, false>(G, (int)ni, d_items + i0, child, par, rhat, out, nullptr, lvbuf,
-                                                    hdr, val, mvsym, d_err, smem_search, st);
+                                                    hdr, val, mvsym, d_err, d_cnt, smem_search, st);
             }
         }
+        if (e == cudaSuccess && ev + 1 < g_n_enc_events) e = cudaEventRecord(g_enc_events[ev + 1], st);
         par = out;
     }
     // exclusive scan of (record words, significance) over the breadth-first blocks
@@ -697,9 +727,10 @@ extern "C" int hmlfc_encode_device(const uint8_t *d_lf, int nu, int nv, int W, i
         k_scan_apply<<<(unsigned)nparts, kEncThreads, 0, st>>>(val, nkeys, part, pre);
         e = cudaGetLastError();
     }
-    unsigned long long tot = 0;
+    unsigned long long tot = 0, cnt[kCounters] = {0};
     int herr = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&tot, part + nparts, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, d_cnt, sizeof cnt, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, d_err, 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return enc_fail(e, "device encoder");
@@ -776,6 +807,17 @@ extern "C" int hmlfc_encode_device(const uint8_t *d_lf, int nu, int nv, int W, i
     h[22] = (uint32_t)o_groups; h[23] = (uint32_t)o_offs; h[24] = (uint32_t)o_recs; h[25] = (uint32_t)o_mvs;
     h[26] = (uint32_t)total;
     std::memcpy(hs, h, sizeof h);
+    if (stats) {
+        std::memset(stats, 0, sizeof *stats);
+        const bool searched = p->mc == 1 || p->mc == 3;
+        int64_t n_pred_items = 0;
+        for (int l = 0; l < L; l++) n_pred_items += item_first[l][1][1] - item_first[l][1][0];
+        stats->blocks_searched = searched ? (uint64_t)n_pred_items * g.nblocks : 0;
+        stats->int_terms = searched ? (uint64_t)n_pred_items * 2ull * nside * nside * (uint64_t)plane : 0;
+        for (int i = 0; i < kCounters; i++) stats->frac_terms += cnt[i];
+        stats->sig_blocks = nsig;
+        stats->blocks = (uint64_t)nkeys;
+    }
     *h_out = hs;
     *nbytes = (size_t)total;
     return HMLFC_OK;

@@ -70,3 +70,34 @@ def test_device_encoder_refuses_wide_search(torch_cuda, tiny_lf):
     assert ei.value.code == H.E_UNSUPPORTED
     # no search: any window is fine
     assert H.encode_device(tiny_lf, 2, 8, 40, 4, mc=O.MC_ZERO) == O.encode(tiny_lf, 2, 8, 40, 4, mc=O.MC_ZERO).stream
+
+
+def test_device_encoder_work_counts_and_events(torch_cuda, tiny_lf, tiny_cfg):
+    """Work counts: the integer stage evaluates (2 Ws + 1)^2 candidates for
+    both signs at every pixel of every predictive node-channel; the
+    refinement at most 48 per sign; significant blocks = the stream's
+    records.  The per-level search events bracket positive times."""
+    torch = torch_cuda
+    import paper_1902_09396_gb300 as H
+    c = tiny_cfg
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * c.levels)]
+    H.set_encode_events(ev)
+    try:
+        st = {}
+        data = H.encode_device(tiny_lf, c.levels, c.block, c.search, c.qstep, stats=st)
+    finally:
+        H.set_encode_events(None)
+    ms = [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(c.levels)]
+    assert all(m > 0 for m in ms)
+    info = H.Stream(data).info
+    px = c.width * c.height
+    # reference members of level l: one per 2x2 cluster = the node count of level l + 1
+    n_pred_nc = info["n_nc"] - 3 * sum(((c.nu + (2 << l) - 1) >> (l + 1)) * ((c.nv + (2 << l) - 1) >> (l + 1))
+                                       for l in range(c.levels))
+    assert st["int_terms"] == n_pred_nc * 2 * (2 * c.search + 1) ** 2 * px
+    assert 0 < st["frac_terms"] <= n_pred_nc * 96 * px
+    assert st["sig_blocks"] == info["n_sig"]
+    assert st["blocks_searched"] == n_pred_nc * ((c.width + c.block - 1) // c.block) * ((c.height + c.block - 1) // c.block)
+    st0 = {}
+    H.encode_device(tiny_lf, c.levels, c.block, c.search, c.qstep, mc=O.MC_ZERO, stats=st0)
+    assert st0["blocks_searched"] == 0 and st0["int_terms"] == 0 and st0["frac_terms"] == 0
