@@ -27,10 +27,12 @@ namespace {
 
 constexpr int kEncThreads = 256;
 constexpr int kMaxEncSearch = 32;           // window (2 Ws + 1)^2 candidates kept in shared memory
+constexpr int kMaxPlaneBlock = 32;          // largest block whose refinement phase planes fit in shared memory
 
 struct EncGeo {
     int W, H, B, nbx, nblocks, Ws, q, thr, side;
     int gv, pv;                              // node-grid widths of this level and of its parent level
+    int planes;                              // refinement through precomputed phase planes (B <= 32)
 };
 
 // One node-channel of a pass: e = (a * gv + b) * 3 + c within the level, its
@@ -91,9 +93,9 @@ __device__ __forceinline__ int warp_sum(int v) {
 
 // Quarter-pel bilinear prediction (weights sum to 16, +8 >> 4) at block pixel
 // (lx, ly) for motion (mx, my) in quarter units, from a window whose (0, 0)
-// is the clamped reference pixel (x0 - Ws, y0 - Ws).
+// is the clamped reference pixel (x0 - Ws - 1, y0 - Ws - 1).
 __device__ __forceinline__ int qpel_win(const int16_t *win, int ww, int Ws, int lx, int ly, int mx, int my) {
-    const int xi = lx + (mx >> 2) + Ws, yi = ly + (my >> 2) + Ws;
+    const int xi = lx + (mx >> 2) + Ws + 1, yi = ly + (my >> 2) + Ws + 1;
     const int fx = mx & 3, fy = my & 3;
     const int16_t *w = win + yi * ww + xi;
     const int s = (4 - fx) * (4 - fy) * (int)w[0] + fx * (4 - fy) * (int)w[1] + (4 - fx) * fy * (int)w[ww] +
@@ -143,7 +145,7 @@ __global__ void k_enc_rkv(const int16_t *__restrict__ lo, int16_t *__restrict__ 
 // (prediction from the reference member's dequantised SRV), else reference
 // member.  ZMV: predictive with motion forced to (0, 0), sign +.
 template <bool PRED, int SEARCH, bool ZMV>
-__global__ void __launch_bounds__(kEncThreads) k_enc_block(
+__global__ void __launch_bounds__(kEncThreads, 6) k_enc_block(
     const EncGeo G, const EncItem *__restrict__ items, const int16_t *__restrict__ child_lev,
     const int16_t *__restrict__ par_recon, const int16_t *__restrict__ rhat_in, int16_t *__restrict__ recon_out,
     int16_t *__restrict__ rhat_out, int16_t *__restrict__ lvbuf, uint32_t *__restrict__ hdr,
@@ -153,6 +155,8 @@ __global__ void __launch_bounds__(kEncThreads) k_enc_block(
     __shared__ unsigned long long s_key[2];
     __shared__ int s_mv[3];
     __shared__ int s_red[4][kEncThreads / 32];
+    __shared__ short s_valid[98];
+    __shared__ int s_nvalid;
 
     const int B = G.B, B2 = B * B;
     const int item = (int)(blockIdx.x / (unsigned)G.nblocks);
@@ -166,13 +170,14 @@ __global__ void __launch_bounds__(kEncThreads) k_enc_block(
     const int16_t *par = par_recon + ((int64_t)((a >> 1) * G.pv + (b >> 1)) * 3 + c) * plane;
     const int16_t *R = PRED ? rhat_in + ((int64_t)((a & ~1) * G.gv + (b & ~1)) * 3 + c) * plane : nullptr;
 
-    int *s_S = reinterpret_cast<int *>(smem);                  // S = child - parent, [n]
-    int *s_pr = s_S + B2;                                       // prediction, [n]
     const int Ws = G.Ws, nside = 2 * Ws + 1, ncand = nside * nside;
-    const int ww = B + 2 * Ws + 1;
-    uint32_t *s_cost = reinterpret_cast<uint32_t *>(s_pr + B2);   // [2][ncand] integer, then [2][49] refinement
-    int16_t *s_win = reinterpret_cast<int16_t *>(s_cost + 2 * max(ncand, 49));
-
+    const int ww = B + 2 * Ws + 3;                              // window pitch (one spare pixel each side)
+    const int HW = B + 1, psz = HW * HW;                        // phase planes: (B+1)^2 positions from -1
+    int *s_S = reinterpret_cast<int *>(smem);                  // S = child - parent, [n]
+    uint32_t *s_cost = reinterpret_cast<uint32_t *>(s_S + B2);    // [2][ncand] integer, then [2][49] refinement
+    int16_t *s_P = reinterpret_cast<int16_t *>(s_cost + 2 * max(ncand, 49));   // [2][16][psz] (planes only)
+    int *s_pr = reinterpret_cast<int *>(s_P);                   // prediction [n], after the search (same space)
+    int16_t *s_win = s_P + max(G.planes ? 2 * 16 * psz : 0, 2 * B2);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int ly = i / bw, lx = i - ly * bw;
         const int64_t o = (int64_t)(y0 + ly) * G.W + x0 + lx;
@@ -181,29 +186,53 @@ __global__ void __launch_bounds__(kEncThreads) k_enc_block(
     if (SEARCH > 0) {
         for (int i = threadIdx.x; i < ww * ww; i += blockDim.x) {
             const int ly = i / ww, lx = i - ly * ww;
-            const int X = clampi(x0 - Ws + lx, 0, G.W - 1), Y = clampi(y0 - Ws + ly, 0, G.H - 1);
+            const int X = clampi(x0 - Ws - 1 + lx, 0, G.W - 1), Y = clampi(y0 - Ws - 1 + ly, 0, G.H - 1);
             s_win[i] = R[(int64_t)Y * G.W + X];
         }
         for (int i = threadIdx.x; i < 2 * ncand; i += blockDim.x) s_cost[i] = 0u;
+        if (threadIdx.x == 0) s_nvalid = 0;
     }
     __syncthreads();
 
     int mvx = 0, mvy = 0, sign = 1;
     if (SEARCH > 0) {
-        // integer stage: costs of every (dx, dy) for both signs, one (row, candidate) per work item
-        for (int t = threadIdx.x; t < ncand * bh; t += blockDim.x) {
-            const int row = t / ncand, cand = t - row * ncand;
-            const int dy = cand / nside - Ws, dx = cand - (cand / nside) * nside - Ws;
-            const int *srow = s_S + row * bw;
-            const int16_t *wrow = s_win + (row + dy + Ws) * ww + dx + Ws;
-            int cp = 0, cm = 0;
-            for (int x = 0; x < bw; x++) {
-                const int s = srow[x], r = wrow[x];
-                cp += abs(s - r);
-                cm += abs(s + r);
+        // integer stage: costs of every (dx, dy) for both signs.  A work item is
+        // (row pair, dy, three consecutive dx): the three candidates slide over
+        // one window row held in registers.
+        {
+            const int ngx = (nside + 2) / 3, nrg = (bh + 1) >> 1;
+            for (int t = threadIdx.x; t < nrg * nside * ngx; t += blockDim.x) {
+                const int gx = t % ngx, rest = t / ngx, dyi = rest % nside, rg = rest / nside;
+                const int dy = dyi - Ws, dx0 = 3 * gx - Ws;
+                int cp0 = 0, cm0 = 0, cp1 = 0, cm1 = 0, cp2 = 0, cm2 = 0;
+                for (int row = 2 * rg; row < min(2 * rg + 2, bh); row++) {
+                    const int *srow = s_S + row * bw;
+                    const int16_t *wrow = s_win + (row + dy + Ws + 1) * ww + dx0 + Ws + 1;
+                    int w0 = wrow[0], w1 = wrow[1];
+                    for (int x = 0; x < bw; x++) {
+                        const int w2 = wrow[x + 2], sv = srow[x];
+                        cp0 += abs(sv - w0);
+                        cm0 += abs(sv + w0);
+                        cp1 += abs(sv - w1);
+                        cm1 += abs(sv + w1);
+                        cp2 += abs(sv - w2);
+                        cm2 += abs(sv + w2);
+                        w0 = w1;
+                        w1 = w2;
+                    }
+                }
+                const int c0 = dyi * nside + 3 * gx;
+                atomicAdd(&s_cost[c0], (uint32_t)cp0);
+                atomicAdd(&s_cost[ncand + c0], (uint32_t)cm0);
+                if (3 * gx + 1 < nside) {
+                    atomicAdd(&s_cost[c0 + 1], (uint32_t)cp1);
+                    atomicAdd(&s_cost[ncand + c0 + 1], (uint32_t)cm1);
+                }
+                if (3 * gx + 2 < nside) {
+                    atomicAdd(&s_cost[c0 + 2], (uint32_t)cp2);
+                    atomicAdd(&s_cost[ncand + c0 + 2], (uint32_t)cm2);
+                }
             }
-            atomicAdd(&s_cost[cand], (uint32_t)cp);
-            atomicAdd(&s_cost[ncand + cand], (uint32_t)cm);
         }
         __syncthreads();
         // per sign: minimum of (cost, |dx| + |dy|, raster index)
@@ -222,26 +251,73 @@ __global__ void __launch_bounds__(kEncThreads) k_enc_block(
         __syncthreads();
         if (SEARCH == 2) {
             // quarter-pel refinement: the 7x7 quarter offsets around each sign's integer winner
+            const int cs0 = (int)(s_key[0] & 0xFFFFu), cs1 = (int)(s_key[1] & 0xFFFFu);
             for (int i = threadIdx.x; i < 2 * 49; i += blockDim.x) s_cost[i] = 0u;
+            if (G.planes) {
+                // Offsets (ox, oy) in [-3, 3]^2 around (4 dx, 4 dy) use phase (ox & 3, oy & 3) at integer
+                // base (dx + (ox >> 2), dy + (oy >> 2)): the 16 phase planes of the (B+1)^2 positions from
+                // -1 cover every candidate.  Separable and exact: H = (4 - fx) a + fx b per row, then
+                // P = ((4 - fy) H + fy H' + 8) >> 4.
+                const int nps = cs0 == cs1 ? 1 : 2;
+                for (int t = threadIdx.x; t < nps * 16 * HW; t += blockDim.x) {      // one plane row per thread
+                    const int ps = t / (16 * HW), r = t - ps * 16 * HW, f = r / HW, v = r - f * HW;
+                    const int fx = f & 3, fy = f >> 2;
+                    const int cc = ps ? cs1 : cs0;
+                    const int dx = cc % nside - Ws, dy = cc / nside - Ws;
+                    const int16_t *top = s_win + (v + dy + Ws) * ww + dx + Ws, *bot = top + ww;
+                    const int w00 = (4 - fx) * (4 - fy), w01 = fx * (4 - fy), w10 = (4 - fx) * fy, w11 = fx * fy;
+                    int16_t *pp = s_P + (ps * 16 + f) * psz + v * HW;
+                    int a0 = top[0], c0 = bot[0];
+                    for (int u = 0; u < HW; u++) {
+                        const int a1 = top[u + 1], c1 = bot[u + 1];
+                        pp[u] = (int16_t)((w00 * a0 + w01 * a1 + w10 * c0 + w11 * c1 + 8) >> 4);
+                        a0 = a1;
+                        c0 = c1;
+                    }
+                }
+            }
+            if (threadIdx.x < 98) {
+                const int sg = threadIdx.x / 49, o = threadIdx.x - sg * 49;
+                const int cc = sg ? cs1 : cs0;
+                const int mx = 4 * (cc % nside - Ws) + o % 7 - 3, my = 4 * (cc / nside - Ws) + o / 7 - 3;
+                if (o != 24 && abs(mx) <= 4 * Ws && abs(my) <= 4 * Ws) s_valid[atomicAdd(&s_nvalid, 1)] = (short)threadIdx.x;
+            }
             __syncthreads();
-            for (int t = threadIdx.x; t < 2 * 49 * bh; t += blockDim.x) {
-                const int row = t / 98, j = t - row * 98, s = j / 49, o = j - s * 49;
-                if (o == 24) continue;                                   // the integer winner itself
-                const int cand = (int)(s_key[s] & 0xFFFFu);
-                const int cx = 4 * (cand % nside - Ws), cy = 4 * (cand / nside - Ws);
-                const int mx = cx + o % 7 - 3, my = cy + o / 7 - 3;
-                if (abs(mx) > 4 * Ws || abs(my) > 4 * Ws) continue;
-                const int sg = s == 0 ? 1 : -1;
-                const int *srow = s_S + row * bw;
+            const int nvalid = s_nvalid;
+            const bool same = cs0 == cs1;
+            const int rpg = (bh + 3) >> 2;                      // rows per work item (4 items per candidate)
+            for (int t = threadIdx.x; t < 4 * nvalid; t += blockDim.x) {
+                const int so = s_valid[t >> 2], r0 = (t & 3) * rpg, r1 = min(bh, r0 + rpg);
+                const int sg = so >= 49, o = so - 49 * sg;
+                const int ox = o % 7 - 3, oy = o / 7 - 3;
                 int acc = 0;
-                for (int x = 0; x < bw; x++) acc += abs(srow[x] - sg * qpel_win(s_win, ww, Ws, x, row, mx, my));
-                atomicAdd(&s_cost[s * 49 + o], (uint32_t)acc);
+                if (G.planes) {
+                    const int f = (oy & 3) * 4 + (ox & 3);
+                    const int16_t *pl = s_P + ((same ? 0 : sg) * 16 + f) * psz + (1 + (oy >> 2)) * HW + 1 + (ox >> 2);
+                    for (int row = r0; row < r1; row++) {
+                        const int *srow = s_S + row * bw;
+                        const int16_t *prow = pl + row * HW;
+                        if (sg == 0)
+                            for (int x = 0; x < bw; x++) acc += abs(srow[x] - (int)prow[x]);
+                        else
+                            for (int x = 0; x < bw; x++) acc += abs(srow[x] + (int)prow[x]);
+                    }
+                } else {
+                    const int cc = sg ? cs1 : cs0;
+                    const int mx = 4 * (cc % nside - Ws) + ox, my = 4 * (cc / nside - Ws) + oy;
+                    const int m = sg ? -1 : 1;
+                    for (int row = r0; row < r1; row++) {
+                        const int *srow = s_S + row * bw;
+                        for (int x = 0; x < bw; x++) acc += abs(srow[x] - m * qpel_win(s_win, ww, Ws, x, row, mx, my));
+                    }
+                }
+                atomicAdd(&s_cost[so], (uint32_t)acc);
             }
             __syncthreads();
             if (warp < 2) {
                 // a fractional candidate replaces the integer winner only at a strictly lower cost;
                 // among fractional candidates: (cost, |mv|_1 in quarter units, raster order)
-                const int cand = (int)(s_key[warp] & 0xFFFFu);
+                const int cand = warp ? cs1 : cs0;
                 const int cx = 4 * (cand % nside - Ws), cy = 4 * (cand / nside - Ws);
                 unsigned long long best = ~0ull;
                 for (int o = lane; o < 49; o += 32) {
@@ -681,11 +757,16 @@ extern "C" int hmlfc_encode_device(const uint8_t *d_lf, int nu, int nv, int W, i
     const int16_t *par = lev + lev_off[L];
     const int Ws = p->search, nside = 2 * Ws + 1;
     const int search_mode = p->mc == 1 ? 2 : p->mc == 3 ? 1 : 0;
-    const size_t smem_base = (size_t)2 * B * B * 4;
+    // shared memory: S [B^2] int, costs, planes [2][16][(B+1)^2] int16 sharing their space with the
+    // prediction [B^2] int, window [(B + 2 Ws + 3)^2] int16
+    const int planes = B <= kMaxPlaneBlock ? 1 : 0;
+    const size_t smem_base = (size_t)B * B * 4 + (size_t)2 * std::max(nside * nside, 49) * 4 + (size_t)B * B * 4;
     const size_t smem_search =
-        smem_base + (size_t)2 * std::max(nside * nside, 49) * 4 + (size_t)(B + 2 * Ws + 1) * (B + 2 * Ws + 1) * 2;
+        (size_t)B * B * 4 + (size_t)2 * std::max(nside * nside, 49) * 4 +
+        std::max<size_t>(planes ? (size_t)2 * 16 * (B + 1) * (B + 1) * 2 : 0, (size_t)B * B * 4) +
+        (size_t)(B + 2 * Ws + 3) * (B + 2 * Ws + 3) * 2;
     for (int l = L - 1; l >= 0 && e == cudaSuccess; l--) {
-        EncGeo G{W, H, B, g.nbx, g.nblocks, Ws, g.q, 0, g.side, g.gv[l], g.gv[l + 1]};
+        EncGeo G{W, H, B, g.nbx, g.nblocks, Ws, g.q, 0, g.side, g.gv[l], g.gv[l + 1], planes};
         int16_t *out = rec[l & 1];
         const int16_t *child = lev + lev_off[l];
         // pass 0: reference members; their dequantised SRVs go to rhat
