@@ -439,6 +439,14 @@ def run_encode(args):
         del dl
     e2e_ms /= min(steps, 10)
     ops = 3 * st["int_terms"] + 13 * st["frac_terms"]
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "encode_traffic.json")) as f:
+            tj = json.load(f)
+        if tj.get("encoder_version") == H.ENCODER_VERSION and args.config == "paper":
+            traffic = tj["dram_bytes_per_step_scaled"]
+    except (OSError, ValueError, KeyError):
+        pass
     sm_mhz = (ck or {}).get("sm_max_mhz") or 2070.0
     peak = 152 * 4 * 32 * sm_mhz * 1e6 / 1e9              # Gop/s, issue-limited
     achieved = ops / (search_ms / 1000.0) / 1e9
@@ -468,10 +476,11 @@ def run_encode(args):
         "search_ms": search_ms, "host_encoder_s": t_host, "stream_bytes": len(out), "bpp": len(out) * 8.0 / n_px,
         "stats": st,
         "roofline": {"bound": "alu", "kernel": "k_enc_block (block-search passes)", "achieved": achieved,
-                     "peak": peak, "unit": "Gop/s", "frac": achieved / peak, "traffic": None,
+                     "peak": peak, "unit": "Gop/s", "frac": achieved / peak, "traffic": traffic,
                      "algorithmic_ops_per_step": ops,
-                     "note": "peak = issue-limited lane operations (152 SMs x 4 x 32 x max SM clock); ops = 3 per "
-                             "integer-stage term + 13 per refinement term of Eq. 1-2"},
+                     "note": "all 4 search passes of a step; peak = issue-limited lane operations (152 SMs x 4 x 32 "
+                             "x max SM clock); ops = 3 per integer-stage term + 13 per refinement term of Eq. 1-2; "
+                             "traffic = DRAM bytes of the captured level-1 pass scaled by node-channels (855/168)"},
         "e2e": {"value": view_units / (e2e_ms / 1000.0), "unit": "512x512 views/s",
                 "h2d_bytes_per_step": int(lf.nbytes), "d2h_bytes_per_step": len(out)},
         "gpu_launches": steps * (1 + c.levels + 2 * c.levels + 3 + 3),
