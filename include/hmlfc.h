@@ -151,6 +151,19 @@ int hmlfc_decode_pixels(const hmlfc_stream *s, const int32_t *d_coords, int64_t 
                         void *cuda_stream);
 
 /*
+ * Progressive decoding (Sec. 1 and Sec. 4: the tree's upper levels hold what
+ * the views share, the lower levels their detail, and the breadth-first
+ * stream orders them top down): as hmlfc_decode_pixels, but the sum of
+ * Sec. 4.8.1 stops at `level` (0 <= level <= L): sample (i, j, x, y) is the
+ * reconstruction of the level-`level` node (i >> level, j >> level), i.e.
+ * root + SRV levels L-1 .. level, through the inverse YCoCg-R and clamp.
+ * level 0 is hmlfc_decode_pixels; level L gives the stored roots.  Errors: as
+ * hmlfc_decode_pixels; HMLFC_E_INVALID_ARG for a level outside 0..L.
+ */
+int hmlfc_decode_pixels_lod(const hmlfc_stream *s, const int32_t *d_coords, int64_t n, int level, uint8_t *d_rgb,
+                            void *cuda_stream);
+
+/*
  * Synchronise `cuda_stream` and report (then clear) the stream object's
  * status word: HMLFC_OK, or HMLFC_E_INVALID_ARG if a decode on it met an
  * out-of-range coordinate since the last check.
@@ -167,6 +180,18 @@ int hmlfc_check_status(const hmlfc_stream *s, void *cuda_stream);
  */
 int hmlfc_render_views(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views, int n_views,
                        float *d_out, void *cuda_stream);
+
+/*
+ * Level-of-detail render: as hmlfc_render_views with every sample decoded
+ * progressively to `level` (see hmlfc_decode_pixels_lod): the 16 samples of
+ * a ray come from the level-`level` reconstructions of its cameras' nodes,
+ * so the work per call falls with the level (fewer SRV levels and one
+ * decoded block per node instead of per camera).  level must lie in 0..L of
+ * every stream (HMLFC_E_INVALID_ARG otherwise).  The per-tile staging of
+ * hmlfc_set_render_path(2) is replaced by the per-ray path for level > 0.
+ */
+int hmlfc_render_views_lod(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views, int n_views,
+                           int level, float *d_out, void *cuda_stream);
 
 /*
  * hmlfc_render_views without any memory allocation (the paper has no
@@ -349,6 +374,12 @@ int hmlfc_touched_bytes(const hmlfc_stream *const *streams, int n_streams, const
  * pairs that hold a reached sample. */
 int hmlfc_touched_bytes_union(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views,
                               int n_views, double *h_total, double *h_cam_blocks);
+
+/* The same count for a level-of-detail render at `level` (0..L): samples
+ * are keyed by their level-`level` node, only levels L-1 .. level are reached,
+ * and h_cam_blocks counts (node, block) pairs. */
+int hmlfc_touched_bytes_union_lod(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views,
+                                  int n_views, int level, double *h_total, double *h_cam_blocks);
 
 /*
  * Render strategy (process-wide).  0 (default): decode every (camera, block)

@@ -97,6 +97,9 @@ def _bind(L):
     L.orc_close.argtypes = [P]
     L.orc_stream_info.argtypes = [P, P]
     L.orc_decode_samples.argtypes = [P, P, I64, P, P]
+    L.orc_decode_samples_lod.argtypes = [P, P, I64, I, P, P]
+    L.orc_render_pixels_lod.argtypes = [P, P, I, P, I64, I, P]
+    L.orc_touched_bytes_lod.argtypes = [P, P, I, I, P]
     L.orc_decode_all.argtypes = [P, P, P]
     L.orc_block_info.argtypes = [P, I64, I, P]
     L.orc_dequant.argtypes = [P, P, P]
@@ -286,12 +289,13 @@ class Stream:
     __del__ = close
 
     # -- decoding -----------------------------------------------------------
-    def decode_samples(self, coords: np.ndarray, with_ycocg: bool = False):
-        """Random-access decoding (Sec. 4.8.1) of samples (i, j, x, y) -> RGB8."""
+    def decode_samples(self, coords: np.ndarray, with_ycocg: bool = False, level: int = 0):
+        """Random-access decoding (Sec. 4.8.1) of samples (i, j, x, y) -> RGB8;
+        level > 0: progressive decoding down to that level."""
         c = np.ascontiguousarray(coords, np.int32).reshape(-1, 4)
         rgb = np.zeros((len(c), 3), np.uint8)
         ycc = np.zeros((len(c), 3), np.int32) if with_ycocg else None
-        _check(lib().orc_decode_samples(self._h, _p(c), len(c), _p(rgb), _p(ycc) if with_ycocg else None),
+        _check(lib().orc_decode_samples_lod(self._h, _p(c), len(c), level, _p(rgb), _p(ycc) if with_ycocg else None),
                "decode_samples")
         return (rgb, ycc) if with_ycocg else rgb
 
@@ -316,12 +320,13 @@ class Stream:
         return co, ro
 
     # -- rendering ----------------------------------------------------------
-    def render_pixels(self, views, pix: np.ndarray) -> np.ndarray:
-        """FP64 render of selected (view, px, py) by random-access decoding."""
+    def render_pixels(self, views, pix: np.ndarray, level: int = 0) -> np.ndarray:
+        """FP64 render of selected (view, px, py) by random-access decoding
+        (down to `level`)."""
         v = _views(views)
         p = np.ascontiguousarray(pix, np.int32).reshape(-1, 3)
         out = np.zeros((len(p), 3), np.float64)
-        _check(lib().orc_render_pixels(self._h, _p(v), len(v), _p(p), len(p), _p(out)), "render_pixels")
+        _check(lib().orc_render_pixels_lod(self._h, _p(v), len(v), _p(p), len(p), level, _p(out)), "render_pixels")
         return out
 
     def relax_render(self, coeff: np.ndarray, roots: np.ndarray, views) -> np.ndarray:
@@ -340,10 +345,10 @@ class Stream:
         _check(lib().orc_relax_adjoint(self._h, _p(v), len(v), _p(g), _p(gc), _p(gr)), "relax_adjoint")
         return gc, gr
 
-    def touched_bytes(self, views) -> np.ndarray:
+    def touched_bytes(self, views, level: int = 0) -> np.ndarray:
         v = _views(views)
         out = np.zeros(len(v), np.float64)
-        _check(lib().orc_touched_bytes(self._h, _p(v), len(v), _p(out)), "touched_bytes")
+        _check(lib().orc_touched_bytes_lod(self._h, _p(v), len(v), level, _p(out)), "touched_bytes")
         return out
 
 

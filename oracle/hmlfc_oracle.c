@@ -23,7 +23,9 @@
  *   BISE         Sec. 4.6   values in [0, N-1], N in {2^b, 3*2^b, 5*2^b}
  *   stream       Sec. 4.7   breadth-first from the top of the tree
  *   decode       Sec. 4.8.1 roots + per-level SRV blocks + motion
- *                           re-compensation, random access per sample
+ *                           re-compensation, random access per sample;
+ *                           progressive decoding (Sec. 1, Sec. 4) stops the
+ *                           sum at a level k: the level-k node's image
  *   render       Sec. 2.1, Sec. 5  two-plane (u,v,s,t) rays, quadrilinear
  *                           interpolation of the 16 neighbouring samples
  *
@@ -902,29 +904,35 @@ static int srv_at(const orc_stream *s, int l, int a, int b, int c, int x, int y)
     return sign * pred + r;
 }
 
-/* YCoCg value of LF sample (i, j, x, y): root + sum over levels (Sec. 4.8.1). */
-static void sample_ycocg(const orc_stream *s, int i, int j, int x, int y, int v[3]) {
+/* YCoCg value of LF sample (i, j, x, y): root + sum over levels (Sec. 4.8.1).
+ * Progressive decoding (Sec. 1, Sec. 4: the upper levels carry what the views
+ * share, the lower ones their detail) stops the sum at level lod: the value is
+ * then the reconstruction of the level-lod node (i >> lod, j >> lod). */
+static void sample_ycocg(const orc_stream *s, int i, int j, int x, int y, int lod, int v[3]) {
     const geom *g = &s->g;
     int L = g->L;
     size_t plane = (size_t)g->W * g->H;
     int ra = i >> L, rb = j >> L;
     for (int c = 0; c < 3; c++) v[c] = s->roots[(((size_t)ra * g->gv[L] + rb) * 3 + c) * plane + (size_t)y * g->W + x];
-    for (int l = 0; l < L; l++)
+    for (int l = lod; l < L; l++)
         for (int c = 0; c < 3; c++) v[c] += srv_at(s, l, i >> l, j >> l, c, x, y);
 }
 
-static void sample_rgb(const orc_stream *s, int i, int j, int x, int y, int rgb[3]) {
+static void sample_rgb(const orc_stream *s, int i, int j, int x, int y, int lod, int rgb[3]) {
     int v[3], r, g, b;
-    sample_ycocg(s, i, j, x, y, v);
+    sample_ycocg(s, i, j, x, y, lod, v);
     orc_ycocg_to_rgb(v[0], v[1], v[2], &r, &g, &b);
     rgb[0] = clampi(r, 0, 255);
     rgb[1] = clampi(g, 0, 255);
     rgb[2] = clampi(b, 0, 255);
 }
 
-/* coords [n][4] = (i, j, x, y); rgb [n][3]; ycocg [n][3] (optional). */
-int orc_decode_samples(const orc_stream *s, const int32_t *coords, int64_t n, uint8_t *rgb, int32_t *ycocg) {
+/* coords [n][4] = (i, j, x, y); rgb [n][3]; ycocg [n][3] (optional); decoded
+ * down to level lod (0 = full decode, L = roots only). */
+int orc_decode_samples_lod(const orc_stream *s, const int32_t *coords, int64_t n, int lod, uint8_t *rgb,
+                           int32_t *ycocg) {
     const geom *g = &s->g;
+    if (lod < 0 || lod > g->L) return ORC_E_ARG;
     for (int64_t k = 0; k < n; k++) {
         const int32_t *c = coords + 4 * k;
         if (c[0] < 0 || c[0] >= g->nu || c[1] < 0 || c[1] >= g->nv || c[2] < 0 || c[2] >= g->W || c[3] < 0 ||
@@ -934,7 +942,7 @@ int orc_decode_samples(const orc_stream *s, const int32_t *coords, int64_t n, ui
     for (int64_t k = 0; k < n; k++) {
         const int32_t *c = coords + 4 * k;
         int v[3], o[3];
-        sample_ycocg(s, c[0], c[1], c[2], c[3], v);
+        sample_ycocg(s, c[0], c[1], c[2], c[3], lod, v);
         if (ycocg) { ycocg[3 * k] = v[0]; ycocg[3 * k + 1] = v[1]; ycocg[3 * k + 2] = v[2]; }
         int r, gg, b;
         orc_ycocg_to_rgb(v[0], v[1], v[2], &r, &gg, &b);
@@ -942,6 +950,10 @@ int orc_decode_samples(const orc_stream *s, const int32_t *coords, int64_t n, ui
         for (int t = 0; t < 3; t++) rgb[3 * k + t] = (uint8_t)o[t];
     }
     return ORC_OK;
+}
+
+int orc_decode_samples(const orc_stream *s, const int32_t *coords, int64_t n, uint8_t *rgb, int32_t *ycocg) {
+    return orc_decode_samples_lod(s, coords, n, 0, rgb, ycocg);
 }
 
 /* ------------------------------------------------------------------ */
@@ -1154,9 +1166,10 @@ int orc_render_dense(const uint8_t *lf, int nu, int nv, int W, int H, const orc_
 
 /* Render selected pixels straight from the stream by random-access decoding
  * of their 16 samples.  pix [n][3] = (view index, px, py); out [n][3]. */
-int orc_render_pixels(const orc_stream *s, const orc_view *views, int nviews, const int32_t *pix, int64_t n,
-                      double *out) {
+int orc_render_pixels_lod(const orc_stream *s, const orc_view *views, int nviews, const int32_t *pix, int64_t n,
+                          int lod, double *out) {
     const geom *g = &s->g;
+    if (lod < 0 || lod > g->L) return ORC_E_ARG;
     for (int64_t k = 0; k < n; k++) {
         const int32_t *p = pix + 3 * k;
         if (p[0] < 0 || p[0] >= nviews || p[1] < 0 || p[1] >= views[p[0]].width || p[2] < 0 ||
@@ -1174,12 +1187,17 @@ int orc_render_pixels(const orc_stream *s, const orc_view *views, int nviews, co
                     for (int ys = 0; ys < 2; ys++) {
                         double w = r.wu[a] * r.wv[b] * r.ws[xs] * r.wt[ys];
                         int rgb[3];
-                        sample_rgb(s, r.i[a], r.j[b], r.x[xs], r.y[ys], rgb);
+                        sample_rgb(s, r.i[a], r.j[b], r.x[xs], r.y[ys], lod, rgb);
                         for (int c = 0; c < 3; c++) acc[c] += w * rgb[c];
                     }
         for (int c = 0; c < 3; c++) out[3 * k + c] = acc[c] / 255.0;
     }
     return ORC_OK;
+}
+
+int orc_render_pixels(const orc_stream *s, const orc_view *views, int nviews, const int32_t *pix, int64_t n,
+                      double *out) {
+    return orc_render_pixels_lod(s, views, nviews, pix, n, 0, out);
 }
 
 /* ------------------------------------------------------------------ */
@@ -1322,8 +1340,11 @@ int orc_relax_adjoint(const orc_stream *s, const orc_view *views, int nviews, co
  * predictive block (16 per unique group entry, 2 + 4*record words if
  * significant, MV bits/8) + per unique touched significant reference block
  * (B*B*2 resident tile + 4 table entry). */
-int orc_touched_bytes(const orc_stream *s, const orc_view *views, int nviews, double *bytes) {
+/* Compulsory bytes of each view decoded down to level lod: a sample of camera
+ * (i, j) stands for its level-lod node (keyed by the node's first camera). */
+int orc_touched_bytes_lod(const orc_stream *s, const orc_view *views, int nviews, int lod, double *bytes) {
     const geom *g = &s->g;
+    if (lod < 0 || lod > g->L) return ORC_E_ARG;
     size_t plane = (size_t)g->W * g->H;
     size_t nroot = (size_t)g->gu[g->L] * g->gv[g->L];
     size_t nb_all = (size_t)g->n_nc * g->nblocks;
@@ -1344,11 +1365,11 @@ int orc_touched_bytes(const orc_stream *s, const orc_view *views, int nviews, do
                     for (int b = 0; b < 2; b++)
                         for (int xs = 0; xs < 2; xs++)
                             for (int ys = 0; ys < 2; ys++) {
-                                int i = r.i[a], j = r.j[b], x = r.x[xs], y = r.y[ys];
+                                int i = (r.i[a] >> lod) << lod, j = (r.j[b] >> lod) << lod, x = r.x[xs], y = r.y[ys];
                                 size_t rp = ((size_t)(i >> g->L) * g->gv[g->L] + (j >> g->L)) * plane + (size_t)y * g->W + x;
                                 if (!root_seen[rp]) { root_seen[rp] = 1; acc += 6.0; }
                                 int k = (y / g->B) * g->nbx + x / g->B;
-                                for (int l = 0; l < g->L; l++) {
+                                for (int l = lod; l < g->L; l++) {
                                     int na = i >> l, nb = j >> l;
                                     for (int c = 0; c < 3; c++) {
                                         int64_t nc = nc_of(g, l, na, nb, c);
@@ -1397,6 +1418,10 @@ int orc_touched_bytes(const orc_stream *s, const orc_view *views, int nviews, do
         free(root_seen); free(blk_seen); free(grp_seen);
     }
     return ORC_OK;
+}
+
+int orc_touched_bytes(const orc_stream *s, const orc_view *views, int nviews, double *bytes) {
+    return orc_touched_bytes_lod(s, views, nviews, 0, bytes);
 }
 
 int orc_version(void) { return (int)ORC_VERSION; }

@@ -77,6 +77,9 @@ def lib() -> C.CDLL:
     L.hmlfc_free_stream.restype = None
     L.hmlfc_stream_info.argtypes = [P, C.POINTER(StreamInfo)]
     L.hmlfc_decode_pixels.argtypes = [P, P, I64, P, P]
+    L.hmlfc_decode_pixels_lod.argtypes = [P, P, I64, I, P, P]
+    L.hmlfc_render_views_lod.argtypes = [P, I, P, I, I, P, P]
+    L.hmlfc_touched_bytes_union_lod.argtypes = [P, I, P, I, I, P, P]
     L.hmlfc_check_status.argtypes = [P, P]
     L.hmlfc_render_views.argtypes = [P, I, P, I, P, P]
     L.hmlfc_render_views_relaxed.argtypes = [P, I, P, P, P, I, P, P]
@@ -157,14 +160,19 @@ class Stream:
 
     __del__ = free
 
-    def decode_pixels(self, coords, out=None, cuda_stream=None):
-        """coords: int32 CUDA tensor [n, 4] = (i, j, x, y) -> uint8 [n, 3]."""
+    def decode_pixels(self, coords, out=None, cuda_stream=None, level: int = 0):
+        """coords: int32 CUDA tensor [n, 4] = (i, j, x, y) -> uint8 [n, 3];
+        level > 0: progressive decode down to that level only."""
         import torch
         assert coords.dtype == torch.int32 and coords.is_cuda and coords.is_contiguous()
         n = coords.shape[0]
         if out is None:
             out = torch.empty((n, 3), dtype=torch.uint8, device=coords.device)
-        _check(lib().hmlfc_decode_pixels(self.handle, _ptr(coords), n, _ptr(out), _stream_handle(cuda_stream)))
+        if level:
+            _check(lib().hmlfc_decode_pixels_lod(self.handle, _ptr(coords), n, level, _ptr(out),
+                                                 _stream_handle(cuda_stream)))
+        else:
+            _check(lib().hmlfc_decode_pixels(self.handle, _ptr(coords), n, _ptr(out), _stream_handle(cuda_stream)))
         return out
 
     def check_status(self, cuda_stream=None):
@@ -197,14 +205,19 @@ def out_size(views) -> int:
     return max((v.out_offset + v.width * v.height * 3 for v in views), default=0)
 
 
-def render_views(streams, views, out=None, cuda_stream=None):
-    """Fused decode + render of novel views (float32 [sum H*W*3] CUDA tensor)."""
+def render_views(streams, views, out=None, cuda_stream=None, level: int = 0):
+    """Fused decode + render of novel views (float32 [sum H*W*3] CUDA tensor);
+    level > 0 renders from the progressive decode at that level."""
     import torch
     va = _views_array(views)
     if out is None:
         out = torch.empty(out_size(views), dtype=torch.float32, device=torch.device("cuda", streams[0].device))
-    _check(lib().hmlfc_render_views(_streams_array(streams), len(streams), va, len(va), _ptr(out),
-                                    _stream_handle(cuda_stream)))
+    if level:
+        _check(lib().hmlfc_render_views_lod(_streams_array(streams), len(streams), va, len(va), level, _ptr(out),
+                                            _stream_handle(cuda_stream)))
+    else:
+        _check(lib().hmlfc_render_views(_streams_array(streams), len(streams), va, len(va), _ptr(out),
+                                        _stream_handle(cuda_stream)))
     return out
 
 
@@ -334,14 +347,15 @@ def requantize(stream: Stream, coeff: np.ndarray, root: np.ndarray) -> bytes:
     return data
 
 
-def touched_bytes_union(streams, views, with_blocks: bool = False):
+def touched_bytes_union(streams, views, with_blocks: bool = False, level: int = 0):
     """Compulsory bytes of a whole call: distinct items counted once; with
-    with_blocks also the number of distinct (camera, block) pairs reached."""
+    with_blocks also the number of distinct (camera, block) pairs reached
+    ((node, block) pairs at a progressive level > 0)."""
     va = _views_array(views)
     out = C.c_double()
     nb = C.c_double()
-    _check(lib().hmlfc_touched_bytes_union(_streams_array(streams), len(streams), va, len(va), C.byref(out),
-                                           C.byref(nb)))
+    _check(lib().hmlfc_touched_bytes_union_lod(_streams_array(streams), len(streams), va, len(va), level,
+                                               C.byref(out), C.byref(nb)))
     return (out.value, nb.value) if with_blocks else out.value
 
 

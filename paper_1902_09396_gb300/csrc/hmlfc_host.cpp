@@ -331,8 +331,10 @@ int sm_count(int device) {
 // those blocks once, then blend every ray from the cache.  Returns 1 (and
 // launches nothing) when the scratch cannot be had, so the caller falls back.
 int render_cached(const hmlfc_stream *s, const std::vector<LaunchViews> &chunks, const std::vector<int> &tiles,
-                  float *d_out, cudaStream_t st) {
+                  float *d_out, cudaStream_t st, int lod = 0) {
     const Geometry &g = s->g;
+    DevStream ds = s->ds;
+    ds.lod = lod;
     const int64_t n_keys = (int64_t)g.nu * g.nv * g.nblocks;
     const size_t blk_bytes = (size_t)g.B * g.B * 4;
     const uint32_t capacity = (uint32_t)std::min<int64_t>(n_keys, (int64_t)(g_cache_bytes / blk_bytes));
@@ -355,13 +357,13 @@ int render_cached(const hmlfc_stream *s, const std::vector<LaunchViews> &chunks,
     phase_mark(0, st);
     cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)n_keys, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 8, st);
-    for (size_t c = 0; c < chunks.size() && e == cudaSuccess; c++) e = launch_mark(s->ds, chunks[c], tiles[c], flags, st);
-    if (e == cudaSuccess) e = launch_assign(s->ds, flags, slotmap, items, counters, capacity, st);
+    for (size_t c = 0; c < chunks.size() && e == cudaSuccess; c++) e = launch_mark(ds, chunks[c], tiles[c], flags, st);
+    if (e == cudaSuccess) e = launch_assign(ds, flags, slotmap, items, counters, capacity, st);
     phase_mark(1, st);
-    if (e == cudaSuccess) e = launch_decode_blocks(s->ds, items, counters, cache, sm_count(s->device) * 8, st);
+    if (e == cudaSuccess) e = launch_decode_blocks(ds, items, counters, cache, sm_count(s->device) * 8, st);
     phase_mark(2, st);
     for (size_t c = 0; c < chunks.size() && e == cudaSuccess; c++)
-        e = launch_render_cached(s->ds, chunks[c], tiles[c], slotmap, cache, d_out, st);
+        e = launch_render_cached(ds, chunks[c], tiles[c], slotmap, cache, d_out, st);
     phase_mark(3, st);
     const cudaError_t ef = cudaFreeAsync(base, st);
     if (e == cudaSuccess) e = ef;
@@ -502,14 +504,22 @@ int hmlfc_stream_info(const hmlfc_stream *s, hmlfc_stream_info_t *out) {
     return HMLFC_OK;
 }
 
-int hmlfc_decode_pixels(const hmlfc_stream *s, const int32_t *d_coords, int64_t n, uint8_t *d_rgb, void *cuda_stream) {
+int hmlfc_decode_pixels_lod(const hmlfc_stream *s, const int32_t *d_coords, int64_t n, int level, uint8_t *d_rgb,
+                            void *cuda_stream) {
     if (!s) return fail(HMLFC_E_INVALID_ARG, "stream is NULL");
     if (n < 0) return fail(HMLFC_E_INVALID_ARG, "negative count");
+    if (level < 0 || level > s->g.L) return fail(HMLFC_E_INVALID_ARG, "level %d outside 0..%d", level, s->g.L);
     if (n == 0) return HMLFC_OK;
     if (!d_coords || !d_rgb) return fail(HMLFC_E_INVALID_ARG, "NULL buffer");
     DeviceGuard guard(s->device);
-    const cudaError_t e = launch_decode_pixels(s->ds, d_coords, n, d_rgb, static_cast<cudaStream_t>(cuda_stream));
+    DevStream ds = s->ds;
+    ds.lod = level;
+    const cudaError_t e = launch_decode_pixels(ds, d_coords, n, d_rgb, static_cast<cudaStream_t>(cuda_stream));
     return e == cudaSuccess ? HMLFC_OK : cuda_fail(e, "decode_pixels launch");
+}
+
+int hmlfc_decode_pixels(const hmlfc_stream *s, const int32_t *d_coords, int64_t n, uint8_t *d_rgb, void *cuda_stream) {
+    return hmlfc_decode_pixels_lod(s, d_coords, n, 0, d_rgb, cuda_stream);
 }
 
 int hmlfc_check_status(const hmlfc_stream *s, void *cuda_stream) {
@@ -528,8 +538,16 @@ int hmlfc_check_status(const hmlfc_stream *s, void *cuda_stream) {
 
 int hmlfc_render_views(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views, int n_views,
                        float *d_out, void *cuda_stream) {
+    return hmlfc_render_views_lod(streams, n_streams, h_views, n_views, 0, d_out, cuda_stream);
+}
+
+int hmlfc_render_views_lod(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views, int n_views,
+                           int level, float *d_out, void *cuda_stream) {
     int rc = check_views(streams, n_streams, h_views, n_views);
     if (rc != HMLFC_OK) return rc;
+    for (int k = 0; k < n_streams; k++)
+        if (level < 0 || level > streams[k]->g.L)
+            return fail(HMLFC_E_INVALID_ARG, "level %d outside 0..%d of stream %d", level, streams[k]->g.L, k);
     if (n_views > 0 && !d_out) return fail(HMLFC_E_INVALID_ARG, "d_out is NULL");
     if (n_views == 0) return HMLFC_OK;
     DeviceGuard guard(streams[0]->device);
@@ -542,13 +560,16 @@ int hmlfc_render_views(const hmlfc_stream *const *streams, int n_streams, const 
         if (chunks.empty()) continue;
         int path = g_render_path;
         if (path == 0) {
-            rc = render_cached(streams[lf], chunks, tiles, d_out, st);
+            rc = render_cached(streams[lf], chunks, tiles, d_out, st, level);
             if (rc == HMLFC_OK) continue;
             if (rc != 1) return rc;
             path = 2;   // no scratch: per-tile staging needs none
         }
+        if (level > 0) path = 1;   // the per-tile staging decodes every level; the direct walk stops at `level`
+        DevStream ds = streams[lf]->ds;
+        ds.lod = level;
         for (size_t c = 0; c < chunks.size(); c++) {
-            const cudaError_t e = launch_render(streams[lf]->ds, chunks[c], tiles[c], d_out, path == 1 ? 1 : 0, st);
+            const cudaError_t e = launch_render(ds, chunks[c], tiles[c], d_out, path == 1 ? 1 : 0, st);
             if (e != cudaSuccess) return cuda_fail(e, "render launch");
         }
     }

@@ -37,6 +37,7 @@ struct DevStream {
     const uint32_t *ref_tab;        // [n_ref_nc][nblocks] tile index, 0 = the zero tile
     const int16_t *tiles;           // [n_tiles + 1][B * B]
     uint32_t *status;               // bit 0: an out-of-range coordinate was seen
+    int lod;                        // progressive decode: levels below lod are left out (0 = full decode)
 };
 
 // Views of one launch, by value (kernel parameter space).

@@ -215,7 +215,9 @@ __device__ __forceinline__ uint32_t ycocg_to_rgb8(int Y, int Co, int Cg) {
     return (uint32_t)clampi(R, 0, 255) | ((uint32_t)clampi(G, 0, 255) << 8) | ((uint32_t)clampi(Bc, 0, 255) << 16);
 }
 
-// Full random-access decoding of one sample (Sec. 4.8.1).
+// Random-access decoding of one sample (Sec. 4.8.1): root + SRV levels
+// L-1 .. lod.  lod > 0 is the progressive decode: the sample of camera (i, j)
+// is then its level-lod node's reconstruction.
 template <int BS>
 __device__ uint32_t sample_direct(const DevStream &S, const LevelTabs &T, const Blk<BS> &bk, int i, int j, int x,
                                   int y) {
@@ -223,7 +225,7 @@ __device__ uint32_t sample_direct(const DevStream &S, const LevelTabs &T, const 
     const size_t plane = (size_t)S.W * S.H;
     const size_t rbase = ((size_t)(i >> L) * T.gv[L] + (j >> L)) * 3 * plane + (size_t)y * S.W + x;
     int v0 = __ldg(S.roots + rbase), v1 = __ldg(S.roots + rbase + plane), v2 = __ldg(S.roots + rbase + 2 * plane);
-    for (int l = 0; l < L; l++) {
+    for (int l = S.lod; l < L; l++) {
         const int a = i >> l, b = j >> l;
         v0 += srv_direct(S, T, bk, l, a, b, 0, x, y);
         v1 += srv_direct(S, T, bk, l, a, b, 1, x, y);
@@ -961,7 +963,8 @@ __global__ void __launch_bounds__(128) k_mark(const __grid_constant__ DevStream 
             for (int px = x0; px <= x1; px++) {
                 Ray r;
                 ray_setup(V, S.nu, S.nv, S.W, S.H, px, py, r);
-                const int ci[2] = {r.i0, r.i1}, cj[2] = {r.j0, r.j1};
+                const int ci[2] = {(r.i0 >> S.lod) << S.lod, (r.i1 >> S.lod) << S.lod};
+                const int cj[2] = {(r.j0 >> S.lod) << S.lod, (r.j1 >> S.lod) << S.lod};
                 const int kb[4] = {bk.div(r.y0) * S.nbx + bk.div(r.x0), bk.div(r.y0) * S.nbx + bk.div(r.x1),
                                    bk.div(r.y1) * S.nbx + bk.div(r.x0), bk.div(r.y1) * S.nbx + bk.div(r.x1)};
                 for (int q = 0; q < 16; q++)
@@ -970,8 +973,9 @@ __global__ void __launch_bounds__(128) k_mark(const __grid_constant__ DevStream 
         return;
     }
     const int bx0 = bk.div(bl[2]), bx1 = bk.div(bh[2]), by0 = bk.div(bl[3]), by1 = bk.div(bh[3]);
-    for (int i = bl[0]; i <= bh[0]; i++)
-        for (int j = bl[1]; j <= bh[1]; j++) {
+    const int step = 1 << S.lod;            // progressive decode: one representative camera per level-lod node
+    for (int i = (bl[0] >> S.lod) << S.lod; i <= bh[0]; i += step)
+        for (int j = (bl[1] >> S.lod) << S.lod; j <= bh[1]; j += step) {
             uint8_t *f = flags + ((size_t)i * S.nv + j) * S.nblocks;
             for (int by = by0; by <= by1; by++)
                 for (int bx = bx0; bx <= bx1; bx++) f[by * S.nbx + bx] = 1;
@@ -1129,7 +1133,8 @@ __global__ void __launch_bounds__(256) k_decode_blocks(const __grid_constant__ D
             const size_t rb = ((size_t)(aK >> (L - K)) * T.gv[L] + (bK >> (L - K))) * 3 * plane + (size_t)g.y * S.W + g.x;
             int v[3] = {__ldg(S.roots + rb), __ldg(S.roots + rb + plane), __ldg(S.roots + rb + 2 * plane)};
             const Desc *dd = s_desc + gi * nd;
-            for (int l = L - 1; l >= K; l--) {
+            const int lod = S.lod;                              // progressive decode: stop at level lod
+            for (int l = L - 1; l >= max(K, lod); l--) {
                 const bool ref = is_ref(aK >> (l - K), bK >> (l - K));
 #pragma unroll
                 for (int c = 0; c < 3; c++) v[c] += srv_desc(S, bk, dd[(l - K) * 3 + c], ref, g);
@@ -1143,20 +1148,25 @@ __global__ void __launch_bounds__(256) k_decode_blocks(const __grid_constant__ D
                     const uint32_t under = 0x33u << (8 * (m >> 1) + 2 * (m & 1));
                     cams = mask & under;
                     if (!cams) continue;
-                    const bool ref = is_ref(2 * aK + (m >> 1), 2 * bK + (m & 1));
-                    const Desc *d1 = dd + n_sh + m * 3;
+                    if (lod <= 1) {
+                        const bool ref = is_ref(2 * aK + (m >> 1), 2 * bK + (m & 1));
+                        const Desc *d1 = dd + n_sh + m * 3;
 #pragma unroll
-                    for (int c = 0; c < 3; c++) w[c] += srv_desc(S, bk, d1[c], ref, g);
+                        for (int c = 0; c < 3; c++) w[c] += srv_desc(S, bk, d1[c], ref, g);
+                    }
                 }
                 while (cams) {
                     const int q = __ffs(cams) - 1;
                     cams &= cams - 1;
-                    const int i = aK * cpa + q / cpa, j = bK * cpa + q % cpa;
-                    const bool ref = is_ref(i, j);
-                    const Desc *d0 = dd + n_sh + n_mid + q * 3;
-                    const int z0 = w[0] + srv_desc(S, bk, d0[0], ref, g);
-                    const int z1 = w[1] + srv_desc(S, bk, d0[1], ref, g);
-                    const int z2 = w[2] + srv_desc(S, bk, d0[2], ref, g);
+                    int z0 = w[0], z1 = w[1], z2 = w[2];
+                    if (lod == 0) {
+                        const int i = aK * cpa + q / cpa, j = bK * cpa + q % cpa;
+                        const bool ref = is_ref(i, j);
+                        const Desc *d0 = dd + n_sh + n_mid + q * 3;
+                        z0 += srv_desc(S, bk, d0[0], ref, g);
+                        z1 += srv_desc(S, bk, d0[1], ref, g);
+                        z2 += srv_desc(S, bk, d0[2], ref, g);
+                    }
                     const uint32_t slot = it.z + __popc(mask & ((1u << q) - 1u));
                     cache[(size_t)slot * B2 + p] = inside ? ycocg_to_rgb8(z0, z1, z2) : 0u;
                 }
@@ -1204,8 +1214,10 @@ __global__ void __launch_bounds__(TW *TH) k_render_cached(const __grid_constant_
     ray_setup(V, S.nu, S.nv, S.W, S.H, px, py, r);
     // slots of the 16 samples first (independent loads), then their values
     const uint32_t nv = (uint32_t)S.nv, nbl = (uint32_t)S.nblocks, nbx = (uint32_t)S.nbx;
-    const uint32_t cam[4] = {(uint32_t)r.i0 * nv + r.j0, (uint32_t)r.i0 * nv + r.j1, (uint32_t)r.i1 * nv + r.j0,
-                             (uint32_t)r.i1 * nv + r.j1};
+    const int sh = S.lod;                          // progressive decode: representative camera of the level-lod node
+    const uint32_t i0 = (uint32_t)((r.i0 >> sh) << sh), i1 = (uint32_t)((r.i1 >> sh) << sh);
+    const uint32_t j0 = (uint32_t)((r.j0 >> sh) << sh), j1 = (uint32_t)((r.j1 >> sh) << sh);
+    const uint32_t cam[4] = {i0 * nv + j0, i0 * nv + j1, i1 * nv + j0, i1 * nv + j1};
     const int bx[2] = {bk.div(r.x0), bk.div(r.x1)}, by[2] = {bk.div(r.y0), bk.div(r.y1)};
     const uint32_t blk[4] = {(uint32_t)(by[0] * S.nbx + bx[0]), (uint32_t)(by[1] * S.nbx + bx[0]),
                              (uint32_t)(by[0] * S.nbx + bx[1]), (uint32_t)(by[1] * S.nbx + bx[1])};
@@ -1352,7 +1364,8 @@ __global__ void __launch_bounds__(128) k_mark_batch(const BatchPtrs P, uint8_t *
             for (int px = x0; px <= x1; px++) {
                 Ray r;
                 ray_setup(V, nu, nv, W, Hh, px, py, r);
-                const int ci[2] = {r.i0, r.i1}, cj[2] = {r.j0, r.j1};
+                const int ci[2] = {(r.i0 >> S.lod) << S.lod, (r.i1 >> S.lod) << S.lod};
+                const int cj[2] = {(r.j0 >> S.lod) << S.lod, (r.j1 >> S.lod) << S.lod};
                 const int kb[4] = {bk.div(r.y0) * nbx + bk.div(r.x0), bk.div(r.y0) * nbx + bk.div(r.x1),
                                    bk.div(r.y1) * nbx + bk.div(r.x0), bk.div(r.y1) * nbx + bk.div(r.x1)};
                 for (int q = 0; q < 16; q++) fl[((size_t)ci[q >> 3] * nv + cj[(q >> 2) & 1]) * nblocks + kb[q & 3]] = 1;
@@ -1360,8 +1373,9 @@ __global__ void __launch_bounds__(128) k_mark_batch(const BatchPtrs P, uint8_t *
         return;
     }
     const int bx0 = bk.div(bl[2]), bx1 = bk.div(bh[2]), by0 = bk.div(bl[3]), by1 = bk.div(bh[3]);
-    for (int i = bl[0]; i <= bh[0]; i++)
-        for (int j = bl[1]; j <= bh[1]; j++) {
+    const int step = 1 << S.lod;            // progressive decode: one representative camera per level-lod node
+    for (int i = (bl[0] >> S.lod) << S.lod; i <= bh[0]; i += step)
+        for (int j = (bl[1] >> S.lod) << S.lod; j <= bh[1]; j += step) {
             uint8_t *f = fl + ((size_t)i * nv + j) * nblocks;
             for (int by = by0; by <= by1; by++)
                 for (int bx = bx0; bx <= bx1; bx++) f[by * nbx + bx] = 1;

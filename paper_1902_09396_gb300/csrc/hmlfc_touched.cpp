@@ -99,8 +99,11 @@ struct Seen {
           blk((size_t)g.n_nc * g.nblocks), grp((size_t)g.n_nc * g.ngroups) {}
 };
 
-// Bytes first reached by view V (all of its bytes when `seen` is fresh).
-double count_view(const Counter &C, const hmlfc_view &V, Seen &seen, bool with_output = true) {
+// Bytes first reached by view V (all of its bytes when `seen` is fresh).  At
+// a progressive-decode level lod a sample of camera (i, j) is its level-lod
+// node's reconstruction: the representative camera stands for it and only
+// levels L-1 .. lod are reached.
+double count_view(const Counter &C, const hmlfc_view &V, Seen &seen, int lod = 0, bool with_output = true) {
     const Geometry &g = C.g;
     const size_t plane = (size_t)g.W * g.H;
     double acc = with_output ? (double)V.width * V.height * 12.0 : 0.0;
@@ -126,13 +129,14 @@ double count_view(const Counter &C, const hmlfc_view &V, Seen &seen, bool with_o
             nb(s, g.W, xx[0], xx[1], f);
             nb(t, g.H, yy[0], yy[1], f);
             for (int q = 0; q < 16; q++) {
-                const int i = ii[q >> 3], j = jj[(q >> 2) & 1], x = xx[(q >> 1) & 1], y = yy[q & 1];
+                const int i = (ii[q >> 3] >> lod) << lod, j = (jj[(q >> 2) & 1] >> lod) << lod;
+                const int x = xx[(q >> 1) & 1], y = yy[q & 1];
                 const size_t sk = ((size_t)i * g.nv + j) * plane + (size_t)y * g.W + x;
                 if (!seen.sample.set(sk)) continue;
                 const size_t rp = ((size_t)(i >> g.L) * g.gv[g.L] + (j >> g.L)) * plane + (size_t)y * g.W + x;
                 if (seen.root.set(rp)) acc += 6.0;
                 const int k = (y / g.B) * g.nbx + x / g.B;
-                for (int l = 0; l < g.L; l++) {
+                for (int l = lod; l < g.L; l++) {
                     const int a = i >> l, b = j >> l;
                     const bool ref = (a % 2 == 0) && (b % 2 == 0);
                     for (int c = 0; c < 3; c++) {
@@ -194,9 +198,18 @@ extern "C" int hmlfc_touched_bytes(const hmlfc_stream *const *streams, int n_str
 
 extern "C" int hmlfc_touched_bytes_union(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views,
                                          int n_views, double *h_total, double *h_cam_blocks) {
+    return hmlfc_touched_bytes_union_lod(streams, n_streams, h_views, n_views, 0, h_total, h_cam_blocks);
+}
+
+extern "C" int hmlfc_touched_bytes_union_lod(const hmlfc_stream *const *streams, int n_streams,
+                                             const hmlfc_view *h_views, int n_views, int level, double *h_total,
+                                             double *h_cam_blocks) {
     if (!streams || n_streams < 1 || n_streams > HMLFC_MAX_STREAMS || n_views < 0 || !h_total ||
         (n_views && !h_views))
         return fail(HMLFC_E_INVALID_ARG, "bad arguments");
+    for (int k = 0; k < n_streams; k++)
+        if (streams[k] && (level < 0 || level > streams[k]->g.L))
+            return fail(HMLFC_E_INVALID_ARG, "level %d outside 0..%d", level, streams[k]->g.L);
     std::vector<Counter> counters;
     std::vector<std::unique_ptr<Seen>> seen;
     for (int k = 0; k < n_streams; k++) {
@@ -209,7 +222,7 @@ extern "C" int hmlfc_touched_bytes_union(const hmlfc_stream *const *streams, int
             return fail(HMLFC_E_INVALID_ARG, "view %d", v);
     std::vector<double> part(n_views, 0.0);
     parallel_for(n_views, 0, [&](int64_t v) {
-        part[v] = count_view(counters[h_views[v].lf], h_views[v], *seen[h_views[v].lf]);
+        part[v] = count_view(counters[h_views[v].lf], h_views[v], *seen[h_views[v].lf], level);
     });
     double t = 0.0;
     for (double p : part) t += p;

@@ -39,6 +39,8 @@ MUTANTS = {
     "touched_root_bytes": ("if (!root_seen[rp]) { root_seen[rp] = 1; acc += 6.0; }",
                            "if (!root_seen[rp]) { root_seen[rp] = 1; acc += 3.0; }",
                            ["touched"]),
+    "progressive_one_level_too_deep": ("for (int l = lod; l < L; l++)", "for (int l = lod > 0 ? lod - 1 : 0; l < L; l++)",
+                                       ["progressive"]),
 }
 
 
@@ -71,6 +73,8 @@ def _run(name, tiny_lf, tiny_cfg, ragged_lf):
         pins.test_adjoint_dot_product((st, views))
     elif name == "touched":
         pins.test_touched_bytes_closed_form(tiny_cfg)
+    elif name == "progressive":
+        pins.test_progressive_lossless_equals_level_images(tiny_lf, tiny_cfg, ragged_lf, O.MC_QPEL)
     else:
         raise KeyError(name)
 

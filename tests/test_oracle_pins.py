@@ -602,3 +602,102 @@ def test_touched_bytes_closed_form(tiny_cfg):
     mv_bits = O.bise_bits(mode, b, 15) / 15.0
     want = 64 * 64 * 12 + 64 * 64 * 6 + 3 * 3 * 2 * 16 + 3 * 3 * 64 * mv_bits / 8.0
     assert abs(st.touched_bytes(v)[0] - want) < 1e-6
+
+
+# --------------------------------------------------------------------------
+# progressive decoding (Sec. 1, Sec. 4: the upper levels of the tree carry
+# what the views share, the lower levels their detail)
+# --------------------------------------------------------------------------
+
+def _level_images(lf, L):
+    """Level images I_0..I_L of the input in YCoCg-R, straight from their
+    definition: I_0 = the views, I_{l+1} = the rounded mean of each 2x2
+    cluster of I_l (1, 2 or 4 members at the edges; Sec. 4.3).  Shape of
+    I_l: [gu_l][gv_l][3][H][W]."""
+    r, g, b = (lf[..., k].astype(np.int64) for k in range(3))
+    co = r - b
+    t = b + (co >> 1)
+    cg = g - t
+    y = t + (cg >> 1)
+    levels = [np.stack([y, co, cg], axis=2)]
+    for _ in range(L):
+        P = levels[-1]
+        pu, pv = (P.shape[0] + 1) // 2, (P.shape[1] + 1) // 2
+        N = np.zeros((pu, pv) + P.shape[2:], np.int64)
+        for A in range(pu):
+            for Bn in range(pv):
+                m = P[2 * A:2 * A + 2, 2 * Bn:2 * Bn + 2]
+                k = m.shape[0] * m.shape[1]
+                N[A, Bn] = np.floor_divide(m.sum(axis=(0, 1)) + k // 2, k)
+        levels.append(N)
+    return levels
+
+
+def _all_coords(nu, nv, W, H):
+    return np.stack(np.meshgrid(np.arange(nu), np.arange(nv), np.arange(W), np.arange(H), indexing="ij"),
+                    -1).reshape(-1, 4).astype(np.int32)
+
+
+@pytest.mark.parametrize("mc", [O.MC_OFF, O.MC_QPEL])
+def test_progressive_lossless_equals_level_images(tiny_lf, tiny_cfg, ragged_lf, mc):
+    """With q = 1 and zero thresholds the closed loop reconstructs every
+    level exactly, so decoding sample (i, j, x, y) down to level k gives
+    I_k at node (i >> k, j >> k); level L gives the stored roots."""
+    c = tiny_cfg
+    for lf, L, B in [(tiny_lf, c.levels, c.block), (ragged_lf, 3, 16)]:
+        nu, nv, H, W, _ = lf.shape
+        st = O.Stream(O.encode(lf, L, B, c.search, 1, mc=mc).stream)
+        I = _level_images(lf, L)
+        co = _all_coords(nu, nv, W, H)
+        for k in range(L + 1):
+            _, ycc = st.decode_samples(co, with_ycocg=True, level=k)
+            want = I[k][co[:, 0] >> k, co[:, 1] >> k, :, co[:, 3], co[:, 2]]
+            assert np.array_equal(ycc, want), (L, k)
+
+
+@pytest.mark.parametrize("q", [4, 8])
+def test_progressive_closed_loop_bound(tiny_lf, tiny_cfg, ragged_lf, q):
+    """Closed loop at every level: with zero thresholds the level-k
+    reconstruction differs from I_k by at most floor(q/2) per channel."""
+    c = tiny_cfg
+    for lf, L, B in [(tiny_lf, c.levels, c.block), (ragged_lf, 3, 8)]:
+        nu, nv, H, W, _ = lf.shape
+        st = O.Stream(O.encode(lf, L, B, c.search, q).stream)
+        I = _level_images(lf, L)
+        co = _all_coords(nu, nv, W, H)
+        for k in range(L):
+            _, ycc = st.decode_samples(co, with_ycocg=True, level=k)
+            want = I[k][co[:, 0] >> k, co[:, 1] >> k, :, co[:, 3], co[:, 2]]
+            assert np.max(np.abs(ycc - want)) <= q // 2, (L, k)
+
+
+def test_progressive_render_equals_dense_render_of_level_field(tiny_streams, tiny_cfg):
+    """Rendering at level k by random access equals the dense FP64 render of
+    the light field whose view (i, j) is its level-k node's reconstruction."""
+    c = tiny_cfg
+    st = O.Stream(tiny_streams[c.qstep].stream)
+    geo = S.lf_geometry(c.nu, c.nv, c.width, c.height)
+    views = S.views_to_array(S.random_views(12, geo, 2, [(24, 20)]))
+    pix = np.array([[v, x, y] for v in range(2) for y in range(20) for x in range(24)], np.int32)
+    co = _all_coords(c.nu, c.nv, c.width, c.height)
+    for k in range(1, c.levels + 1):
+        rgb = st.decode_samples(co, level=k)
+        lf_k = np.zeros((c.nu, c.nv, c.height, c.width, 3), np.uint8)
+        lf_k[co[:, 0], co[:, 1], co[:, 3], co[:, 2]] = rgb
+        assert np.array_equal(st.render_pixels(views, pix, level=k).reshape(-1), O.render_dense(lf_k, views))
+
+
+def test_progressive_touched_bytes_closed_form(tiny_cfg):
+    """The identical-views case of test_touched_bytes_closed_form decoded to
+    level 1 or 2: cameras {0,1}x{0,1} share the level-1 node (0, 0), a
+    reference node without significant blocks, so only the output and the
+    root pixels remain: 12 + 6 bytes per pixel."""
+    c = tiny_cfg
+    one = S.make_lf(7, 1, 1, 64, 64, 3, 0.0, "noise_gradient")[0, 0]
+    lf = np.broadcast_to(one, (4, 4, 64, 64, 3)).copy()
+    st = O.Stream(O.encode(lf, c.levels, c.block, c.search, 4).stream)
+    v = _one(S.grid_view(0.0, 0.0, 0.0, 0.0, 64, 64))
+    for k in (1, 2):
+        assert abs(st.touched_bytes(v, level=k)[0] - 64 * 64 * 18) < 1e-6
+    with pytest.raises(Exception):
+        st.touched_bytes(v, level=3)
