@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU baseline sample")
     ap.add_argument("--traffic-json", default=os.path.join(ROOT, "profiles", "decode_traffic.json"))
     ap.add_argument("--path", type=int, default=0, help="render path: 0 cached blocks, 1 direct, 2 per-tile")
-    ap.add_argument("--form", default="plain", choices=["plain", "diff", "batched", "serve", "encode"],
+    ap.add_argument("--form", default="plain", choices=["plain", "diff", "batched", "serve", "encode", "lod"],
                     help="plain: the paper-scale render step (default); diff: 200 Adam steps of the "
                          "differentiable form")
     return ap.parse_args()
@@ -378,6 +378,77 @@ def run_serve(args):
     }), flush=True)
 
 
+def run_lod(args):
+    """Level-of-detail render (progressive decoding): the paper-scale step
+    (64 poses of 512x512 over the 17x17x512^2 stream) rendered from the
+    level-k reconstructions, k = 0..L.  Per level: views/s, phase times,
+    the decode kernel's roofline (its algorithmic bytes: the compressed bytes
+    the step reaches at that level + the decoded-block cache it writes), and
+    the PSNR of the level-k views against the full decode's.  The headline
+    is level 1: a quarter of the cameras decoded, one SRV level fewer."""
+    import torch
+    import paper_1902_09396_gb300 as H
+
+    c, lf, arr, size, tr, tp, _ = make_workload(args)
+    data = H.encode(lf, c.levels, c.block, c.search, args.qstep, t_ref=tr, t_pred=tp)
+    del lf
+    st = H.Stream(data)
+    stream = torch.cuda.current_stream()
+    out = torch.empty(H.out_size(arr), dtype=torch.float32, device="cuda")
+    full = torch.empty_like(out)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    hbm, src = peaks()
+    steps = min(args.steps, 200)
+    H.render_views([st], arr, full)
+    clocks = ClockSampler(torch.cuda.current_device())
+    levels = {}
+    for k in range(c.levels + 1):
+        for _ in range(max(args.warmup, 3)):
+            H.render_views([st], arr, out, level=k)
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        phases = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+        for evs in phases:
+            for e in evs:
+                e.record(stream)
+        torch.cuda.synchronize()
+        for i in range(steps):
+            flush.zero_()
+            H.set_phase_events(phases[i])
+            starts[i].record(stream)
+            H.render_views([st], arr, out, level=k)
+            ends[i].record(stream)
+        H.set_phase_events(None)
+        torch.cuda.synchronize()
+        ms = sum(starts[i].elapsed_time(ends[i]) for i in range(steps)) / steps
+        dec = sum(phases[i][1].elapsed_time(phases[i][2]) for i in range(steps)) / steps
+        blend = sum(phases[i][2].elapsed_time(phases[i][3]) for i in range(steps)) / steps
+        total, blocks = H.touched_bytes_union([st], arr, with_blocks=True, level=k)
+        out_bytes = float(H.out_size(arr)) * 4.0
+        alg = (total - out_bytes) + blocks * c.block * c.block * 4.0
+        mse = float(torch.mean((out.double() - full.double()) ** 2))
+        levels[str(k)] = {"views_per_s": len(arr) / (ms / 1000.0), "ms_per_step": ms, "decode_ms": dec,
+                          "blend_ms": blend, "decoded_blocks": blocks, "compulsory_bytes": total,
+                          "decode_roofline": {"bound": "hbm", "achieved": alg / (dec / 1000.0) / 1e9, "peak": hbm,
+                                              "unit": "GB/s", "frac": alg / (dec / 1000.0) / 1e9 / hbm,
+                                              "algorithmic_bytes": alg},
+                          "psnr_db_vs_full": float("inf") if mse == 0 else 10.0 * math.log10(1.0 / mse)}
+    ck = clocks.stop()
+    head = levels["1"]
+    print(json.dumps({
+        "metric": "512x512 novel views/s at progressive level 1 (level-of-detail render)",
+        "value": head["views_per_s"], "unit": "512x512 views/s", "n_gpus": 1, "steps": steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32 decode, fp32 blend", "data": "synthetic",
+        "config": dict(workload_config(c, args.qstep, tr, tp, size, len(arr)), l2="flushed before every timed step"),
+        "levels": levels,
+        "roofline": dict(head["decode_roofline"], kernel="k_decode_blocks", traffic=None,
+                         note=f"peak {src} HBM copy bandwidth; level-1 step"),
+        "gpu_launches": steps * (c.levels + 1) * 4, "clocks": ck,
+    }), flush=True)
+
+
 def run_encode(args):
     """Device encoder (hmlfc_encode_device) on the paper-scale light field:
     one step encodes the whole 17x17x512^2 field, from the device-resident
@@ -492,6 +563,9 @@ def main():
     args = parse()
     if args.form == "encode":
         run_encode(args)
+        return
+    if args.form == "lod":
+        run_lod(args)
         return
     if args.form == "serve":
         run_serve(args)
