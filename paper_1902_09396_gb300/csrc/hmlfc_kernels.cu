@@ -467,6 +467,54 @@ __device__ __forceinline__ int srv_desc(const DevStream &S, const Blk<BS> &bk, c
     return ((D.d0.z >> 20) & 1u) ? r - pred : r + pred;
 }
 
+// SRVs of one node-channel at two horizontally adjacent pixels (x, y) and
+// (x + 1, y) of a block, from its staged descriptor.  Both share the motion
+// vector, so their six distinct taps (columns x0, x0 + 1, x0 + 2 of rows y0
+// and y0 + 1) are read once.  idx1 / toff1 of the second pixel must be in
+// range even where that pixel is outside the block (its value is then
+// discarded); `inb` says whether its taps lie in the block's tap window.
+template <int BS>
+__device__ __forceinline__ void srv_desc2(const DevStream &S, const Blk<BS> &bk, const Desc &D, bool ref,
+                                          const PixGeom &g, int idx1, int toff1, bool inb, int &o0, int &o1) {
+    const int B = bk.size();
+    if (ref) {
+        const int16_t *t = S.tiles + (size_t)D.d1.x * (B * B);
+        o0 = __ldg(t + g.toff);
+        o1 = __ldg(t + toff1);
+        return;
+    }
+    int r0 = 0, r1 = 0;
+    if (D.d0.x != kNone) {
+        const int m = (int)(int16_t)(D.d0.y & 0xFFFFu);
+        const uint32_t *w = S.recs + D.d0.x + 1;
+        const uint32_t mode = (D.d0.y >> 21) & 3u, b = (D.d0.y >> 16) & 31u;
+        r0 = S.q * (m + (int)bise_get_small(w, mode, b, (uint32_t)g.idx));
+        r1 = S.q * (m + (int)bise_get_small(w, mode, b, (uint32_t)idx1));
+    }
+    if (!S.mc) {
+        o0 = r0;
+        o1 = r1;
+        return;
+    }
+    const int mvx = (int)(D.d0.z & 1023u) - 512, mvy = (int)((D.d0.z >> 10) & 1023u) - 512;
+    const int X = 4 * g.x + mvx, Y = 4 * g.y + mvy;
+    const int x0 = X >> 2, y0 = Y >> 2, fx = X & 3, fy = Y & 3;
+    const int c0 = clampi(x0, 0, S.W - 1), c1 = clampi(x0 + 1, 0, S.W - 1);
+    const int c2 = inb ? clampi(x0 + 2, 0, S.W - 1) : c1;
+    const int ya = clampi(y0, 0, S.H - 1), yb = clampi(y0 + 1, 0, S.H - 1);
+    const int cx = (int)(D.d0.w & 0xFFFFu), cy = (int)(D.d0.w >> 16);
+    const int a0 = tap(S, bk, D.d1, cx, cy, c0, ya), a1 = tap(S, bk, D.d1, cx, cy, c1, ya);
+    const int a2 = tap(S, bk, D.d1, cx, cy, c2, ya);
+    const int b0 = tap(S, bk, D.d1, cx, cy, c0, yb), b1 = tap(S, bk, D.d1, cx, cy, c1, yb);
+    const int b2 = tap(S, bk, D.d1, cx, cy, c2, yb);
+    const int w00 = (4 - fx) * (4 - fy), w10 = fx * (4 - fy), w01 = (4 - fx) * fy, w11 = fx * fy;
+    const int p0 = (w00 * a0 + w10 * a1 + w01 * b0 + w11 * b1 + 8) >> 4;
+    const int p1 = (w00 * a1 + w10 * a2 + w01 * b1 + w11 * b2 + 8) >> 4;
+    const bool neg = (D.d0.z >> 20) & 1u;
+    o0 = neg ? r0 - p0 : r0 + p0;
+    o1 = neg ? r1 - p1 : r1 + p1;
+}
+
 template <int BS>
 __device__ __forceinline__ const Desc &desc_at(const Desc *desc, const Footprint &F, int l, int a, int b, int c,
                                               int blk) {
@@ -1060,7 +1108,7 @@ __global__ void __launch_bounds__(256) k_assign(const __grid_constant__ DevStrea
 // (K = 2), and level 0 once per marked camera.  Persistent CTAs; several
 // items per pass so that one descriptor phase serves more pixel work.
 template <int BS>
-__global__ void __launch_bounds__(256) k_decode_blocks(const __grid_constant__ DevStream S,
+__global__ void __launch_bounds__(256, 4) k_decode_blocks(const __grid_constant__ DevStream S,
                                                       const uint4 *__restrict__ items,
                                                       const unsigned long long *__restrict__ counters,
                                                       uint32_t *__restrict__ cache) {
@@ -1111,36 +1159,53 @@ __global__ void __launch_bounds__(256) k_decode_blocks(const __grid_constant__ D
             s_desc[d] = make_desc(S, T, bk, l, a, b, c, k % S.nbx, k / S.nbx);
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < kGroup * B2; e += blockDim.x) {
-            const int gi = e / B2, p = e - gi * B2;
+        // two horizontally adjacent pixels per thread: (xx, yy) and (xx + 1, yy)
+        const int hp = (B + 1) >> 1, npair = B * hp;
+        for (int e = threadIdx.x; e < kGroup * npair; e += blockDim.x) {
+            const int gi = e / npair, pp = e - gi * npair;
             if (first + gi >= n) continue;
             const uint4 it = __ldg(items + first + gi);
             if (!it.y) continue;
             const int node = (int)(it.x / (uint32_t)S.nblocks), k = (int)(it.x - (uint32_t)node * S.nblocks);
             const int aK = node / T.gv[K], bK = node - (node / T.gv[K]) * T.gv[K];
             const int bx = k % S.nbx, by = k / S.nbx;
-            const int yy = p / B, xx = p - yy * B;
+            const int yy = pp / hp, xx = 2 * (pp - yy * hp);
             const int bw = min(B, S.W - bx * B), bh = min(B, S.H - by * B);
-            const bool inside = xx < bw && yy < bh;
+            const bool in0 = xx < bw && yy < bh, in1 = xx + 1 < bw && yy < bh;
+            const bool tile1 = xx + 1 < B;                      // second pixel inside the B x B tile
             PixGeom g;
             g.x = bx * B + min(xx, bw - 1);
             g.y = by * B + min(yy, bh - 1);
             g.blk = 0;
             g.idx = (g.y - by * B) * bw + (g.x - bx * B);
             g.toff = (g.y - by * B) * B + (g.x - bx * B);
-            const size_t rb = ((size_t)(aK >> (L - K)) * T.gv[L] + (bK >> (L - K))) * 3 * plane + (size_t)g.y * S.W + g.x;
-            int v[3] = {__ldg(S.roots + rb), __ldg(S.roots + rb + plane), __ldg(S.roots + rb + 2 * plane)};
+            const bool inb = in1;                               // second pixel's taps inside the tap window
+            const int idx1 = in1 ? g.idx + 1 : g.idx, toff1 = in1 ? g.toff + 1 : g.toff;
+            const int x1 = in1 ? g.x + 1 : g.x;
+            const size_t rb = ((size_t)(aK >> (L - K)) * T.gv[L] + (bK >> (L - K))) * 3 * plane + (size_t)g.y * S.W;
+            int v0[3], v1[3];
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                v0[c] = __ldg(S.roots + rb + c * plane + g.x);
+                v1[c] = __ldg(S.roots + rb + c * plane + x1);
+            }
             const Desc *dd = s_desc + gi * nd;
             const int lod = S.lod;                              // progressive decode: stop at level lod
             for (int l = L - 1; l >= max(K, lod); l--) {
                 const bool ref = is_ref(aK >> (l - K), bK >> (l - K));
 #pragma unroll
-                for (int c = 0; c < 3; c++) v[c] += srv_desc(S, bk, dd[(l - K) * 3 + c], ref, g);
+                for (int c = 0; c < 3; c++) {
+                    int s0, s1;
+                    srv_desc2(S, bk, dd[(l - K) * 3 + c], ref, g, idx1, toff1, inb, s0, s1);
+                    v0[c] += s0;
+                    v1[c] += s1;
+                }
             }
             const uint32_t mask = it.y;
             const int nm = K == 2 ? 4 : 1;
+            const size_t o0 = (size_t)yy * B + xx;
             for (int m = 0; m < nm; m++) {
-                int w[3] = {v[0], v[1], v[2]};
+                int w0[3] = {v0[0], v0[1], v0[2]}, w1[3] = {v1[0], v1[1], v1[2]};
                 uint32_t cams = mask;                           // K = 1: the node's own cameras
                 if (K == 2) {
                     const uint32_t under = 0x33u << (8 * (m >> 1) + 2 * (m & 1));
@@ -1150,23 +1215,33 @@ __global__ void __launch_bounds__(256) k_decode_blocks(const __grid_constant__ D
                         const bool ref = is_ref(2 * aK + (m >> 1), 2 * bK + (m & 1));
                         const Desc *d1 = dd + n_sh + m * 3;
 #pragma unroll
-                        for (int c = 0; c < 3; c++) w[c] += srv_desc(S, bk, d1[c], ref, g);
+                        for (int c = 0; c < 3; c++) {
+                            int s0, s1;
+                            srv_desc2(S, bk, d1[c], ref, g, idx1, toff1, inb, s0, s1);
+                            w0[c] += s0;
+                            w1[c] += s1;
+                        }
                     }
                 }
                 while (cams) {
                     const int q = __ffs(cams) - 1;
                     cams &= cams - 1;
-                    int z0 = w[0], z1 = w[1], z2 = w[2];
+                    int z0[3] = {w0[0], w0[1], w0[2]}, z1[3] = {w1[0], w1[1], w1[2]};
                     if (lod == 0) {
                         const int i = aK * cpa + q / cpa, j = bK * cpa + q % cpa;
                         const bool ref = is_ref(i, j);
                         const Desc *d0 = dd + n_sh + n_mid + q * 3;
-                        z0 += srv_desc(S, bk, d0[0], ref, g);
-                        z1 += srv_desc(S, bk, d0[1], ref, g);
-                        z2 += srv_desc(S, bk, d0[2], ref, g);
+#pragma unroll
+                        for (int c = 0; c < 3; c++) {
+                            int s0, s1;
+                            srv_desc2(S, bk, d0[c], ref, g, idx1, toff1, inb, s0, s1);
+                            z0[c] += s0;
+                            z1[c] += s1;
+                        }
                     }
-                    const uint32_t slot = it.z + __popc(mask & ((1u << q) - 1u));
-                    cache[(size_t)slot * B2 + p] = inside ? ycocg_to_rgb8(z0, z1, z2) : 0u;
+                    uint32_t *dst = cache + (size_t)(it.z + __popc(mask & ((1u << q) - 1u))) * B2 + o0;
+                    dst[0] = in0 ? ycocg_to_rgb8(z0[0], z0[1], z0[2]) : 0u;
+                    if (tile1) dst[1] = in1 ? ycocg_to_rgb8(z1[0], z1[1], z1[2]) : 0u;
                 }
             }
         }
