@@ -360,7 +360,7 @@ int render_cached(const hmlfc_stream *s, const std::vector<LaunchViews> &chunks,
     for (size_t c = 0; c < chunks.size() && e == cudaSuccess; c++) e = launch_mark(ds, chunks[c], tiles[c], flags, st);
     if (e == cudaSuccess) e = launch_assign(ds, flags, slotmap, items, counters, capacity, st);
     phase_mark(1, st);
-    if (e == cudaSuccess) e = launch_decode_blocks(ds, items, counters, cache, sm_count(s->device) * 8, st);
+    if (e == cudaSuccess) e = launch_decode_blocks(ds, items, counters, cache, sm_count(s->device) * 32, st);
     phase_mark(2, st);
     for (size_t c = 0; c < chunks.size() && e == cudaSuccess; c++)
         e = launch_render_cached(ds, chunks[c], tiles[c], slotmap, cache, d_out, st);

@@ -1112,7 +1112,7 @@ __global__ void __launch_bounds__(256, 4) k_decode_blocks(const __grid_constant_
                                                       const uint4 *__restrict__ items,
                                                       const unsigned long long *__restrict__ counters,
                                                       uint32_t *__restrict__ cache) {
-    constexpr int kGroup = 4;                                   // items per pass
+    constexpr int kGroup = 2;                                   // items per pass
     constexpr int kDescPer = (kMaxLevels - 2) * 3 + 4 * 3 + 16 * 3;
     __shared__ LevelTabs T;
     __shared__ Desc s_desc[kGroup * kDescPer];
@@ -1273,7 +1273,7 @@ __device__ __noinline__ float3 blend_direct(const DevStream &S, const hmlfc_view
 }
 
 template <int BS, int TW, int TH>
-__global__ void __launch_bounds__(TW *TH, 4) k_render_cached(const __grid_constant__ DevStream S,
+__global__ void __launch_bounds__(TW *TH, 6) k_render_cached(const __grid_constant__ DevStream S,
                                                          const __grid_constant__ LaunchViews LV,
                                                          const uint32_t *__restrict__ slotmap,
                                                          const uint32_t *__restrict__ cache, float *__restrict__ out) {
