@@ -1191,57 +1191,80 @@ __global__ void __launch_bounds__(256, 4) k_decode_blocks(const __grid_constant_
             }
             const Desc *dd = s_desc + gi * nd;
             const int lod = S.lod;                              // progressive decode: stop at level lod
-            for (int l = L - 1; l >= max(K, lod); l--) {
-                const bool ref = is_ref(aK >> (l - K), bK >> (l - K));
-#pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    int s0, s1;
-                    srv_desc2(S, bk, dd[(l - K) * 3 + c], ref, g, idx1, toff1, inb, s0, s1);
-                    v0[c] += s0;
-                    v1[c] += s1;
-                }
-            }
             const uint32_t mask = it.y;
             const int nm = K == 2 ? 4 : 1;
             const size_t o0 = (size_t)yy * B + xx;
-            for (int m = 0; m < nm; m++) {
-                int w0[3] = {v0[0], v0[1], v0[2]}, w1[3] = {v1[0], v1[1], v1[2]};
-                uint32_t cams = mask;                           // K = 1: the node's own cameras
-                if (K == 2) {
-                    const uint32_t under = 0x33u << (8 * (m >> 1) + 2 * (m & 1));
-                    cams = mask & under;
+            // One evaluation site for every (node, 3 channels) step, so that the loop body stays small:
+            // phase 0 the shared levels L-1 .. max(K, lod) into v; phase 1 the next child node m with a
+            // marked camera, its level 1 into w = v + SRV (K = 2, lod <= 1); phase 2 its marked cameras,
+            // level 0 into z = w + SRV (lod = 0), each stored to its slot.
+            int w0[3] = {0, 0, 0}, w1[3] = {0, 0, 0};
+            int l = L - 1, m = -1, phase = 0, q = 0;
+            uint32_t cams = 0;
+            for (;;) {
+                const Desc *d = nullptr;
+                bool ref = false;
+                if (phase == 0) {
+                    if (l >= max(K, lod)) {
+                        d = dd + (l - K) * 3;
+                        ref = is_ref(aK >> (l - K), bK >> (l - K));
+                        l--;
+                    } else {
+                        phase = 1;
+                        continue;
+                    }
+                } else if (phase == 1) {
+                    if (++m >= nm) break;
+                    cams = K == 2 ? mask & (0x33u << (8 * (m >> 1) + 2 * (m & 1))) : mask;
                     if (!cams) continue;
-                    if (lod <= 1) {
-                        const bool ref = is_ref(2 * aK + (m >> 1), 2 * bK + (m & 1));
-                        const Desc *d1 = dd + n_sh + m * 3;
 #pragma unroll
-                        for (int c = 0; c < 3; c++) {
-                            int s0, s1;
-                            srv_desc2(S, bk, d1[c], ref, g, idx1, toff1, inb, s0, s1);
-                            w0[c] += s0;
-                            w1[c] += s1;
-                        }
+                    for (int c = 0; c < 3; c++) {
+                        w0[c] = v0[c];
+                        w1[c] = v1[c];
+                    }
+                    phase = 2;
+                    if (K == 2 && lod <= 1) {
+                        d = dd + n_sh + m * 3;
+                        ref = is_ref(2 * aK + (m >> 1), 2 * bK + (m & 1));
+                    } else {
+                        continue;
+                    }
+                } else {
+                    if (!cams) {
+                        phase = 1;
+                        continue;
+                    }
+                    q = __ffs(cams) - 1;
+                    cams &= cams - 1;
+                    if (lod == 0) {
+                        d = dd + n_sh + n_mid + q * 3;
+                        ref = is_ref(aK * cpa + q / cpa, bK * cpa + q % cpa);
+                    } else {
+                        uint32_t *dst = cache + (size_t)(it.z + __popc(mask & ((1u << q) - 1u))) * B2 + o0;
+                        dst[0] = in0 ? ycocg_to_rgb8(w0[0], w0[1], w0[2]) : 0u;
+                        if (tile1) dst[1] = in1 ? ycocg_to_rgb8(w1[0], w1[1], w1[2]) : 0u;
+                        continue;
                     }
                 }
-                while (cams) {
-                    const int q = __ffs(cams) - 1;
-                    cams &= cams - 1;
-                    int z0[3] = {w0[0], w0[1], w0[2]}, z1[3] = {w1[0], w1[1], w1[2]};
-                    if (lod == 0) {
-                        const int i = aK * cpa + q / cpa, j = bK * cpa + q % cpa;
-                        const bool ref = is_ref(i, j);
-                        const Desc *d0 = dd + n_sh + n_mid + q * 3;
+                int s0[3], s1[3];
 #pragma unroll
-                        for (int c = 0; c < 3; c++) {
-                            int s0, s1;
-                            srv_desc2(S, bk, d0[c], ref, g, idx1, toff1, inb, s0, s1);
-                            z0[c] += s0;
-                            z1[c] += s1;
-                        }
+                for (int c = 0; c < 3; c++) srv_desc2(S, bk, d[c], ref, g, idx1, toff1, inb, s0[c], s1[c]);
+                if (phase == 0) {
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        v0[c] += s0[c];
+                        v1[c] += s1[c];
                     }
+                } else if (d == dd + n_sh + m * 3 && K == 2) {     // the child node's level 1
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        w0[c] += s0[c];
+                        w1[c] += s1[c];
+                    }
+                } else {                                            // a camera's level 0
                     uint32_t *dst = cache + (size_t)(it.z + __popc(mask & ((1u << q) - 1u))) * B2 + o0;
-                    dst[0] = in0 ? ycocg_to_rgb8(z0[0], z0[1], z0[2]) : 0u;
-                    if (tile1) dst[1] = in1 ? ycocg_to_rgb8(z1[0], z1[1], z1[2]) : 0u;
+                    dst[0] = in0 ? ycocg_to_rgb8(w0[0] + s0[0], w0[1] + s0[1], w0[2] + s0[2]) : 0u;
+                    if (tile1) dst[1] = in1 ? ycocg_to_rgb8(w1[0] + s1[0], w1[1] + s1[1], w1[2] + s1[2]) : 0u;
                 }
             }
         }
