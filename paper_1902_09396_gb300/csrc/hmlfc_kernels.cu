@@ -1570,6 +1570,73 @@ __device__ __forceinline__ void copy_words(void *dst, const void *src, int bytes
         reinterpret_cast<uint32_t *>(dst)[t] = __ldg(reinterpret_cast<const uint32_t *>(src) + t);
 }
 
+// One pixel pair (pair pp: row pp / ceil(B/2), columns 2 (pp % ceil(B/2)) and
+// + 1) of a cluster item (level-1 node, block) with a mask over its 2 x 2
+// cameras: root + levels L-1 .. 1 once, level 0 per marked camera, both
+// pixels through one evaluation site (as k_decode_blocks); slot_of(q) is
+// camera q's cache slot.
+template <int BS, class SlotOf>
+__device__ __forceinline__ void decode_pair_l1(const DevStream &S, const LevelTabs &T, const Blk<BS> &bk,
+                                               const Desc *dd, uint32_t key, uint32_t mask, int pp, SlotOf slot_of,
+                                               uint32_t *__restrict__ cache) {
+    const int B = bk.size(), B2 = B * B, L = S.L, hp = (B + 1) >> 1;
+    const size_t plane = (size_t)S.W * S.H;
+    const int node = (int)(key / (uint32_t)S.nblocks), k = (int)(key - (uint32_t)node * S.nblocks);
+    const int a1 = node / T.gv[1], b1 = node - (node / T.gv[1]) * T.gv[1];
+    const int bx = k % S.nbx, by = k / S.nbx;
+    const int yy = pp / hp, xx = 2 * (pp - yy * hp);
+    const int bw = min(B, S.W - bx * B), bh = min(B, S.H - by * B);
+    const bool in0 = xx < bw && yy < bh, in1 = xx + 1 < bw && yy < bh, tile1 = xx + 1 < B;
+    PixGeom g;
+    g.x = bx * B + min(xx, bw - 1);
+    g.y = by * B + min(yy, bh - 1);
+    g.blk = 0;
+    g.idx = (g.y - by * B) * bw + (g.x - bx * B);
+    g.toff = (g.y - by * B) * B + (g.x - bx * B);
+    const int idx1 = in1 ? g.idx + 1 : g.idx, toff1 = in1 ? g.toff + 1 : g.toff, x1 = in1 ? g.x + 1 : g.x;
+    const size_t rb = ((size_t)(a1 >> (L - 1)) * T.gv[L] + (b1 >> (L - 1))) * 3 * plane + (size_t)g.y * S.W;
+    int v0[3], v1[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        v0[c] = __ldg(S.roots + rb + c * plane + g.x);
+        v1[c] = __ldg(S.roots + rb + c * plane + x1);
+    }
+    const size_t o0 = (size_t)yy * B + xx;
+    int l = L - 1;
+    uint32_t cams = mask;
+    for (;;) {
+        const Desc *d;
+        bool ref;
+        int q = -1;
+        if (l >= 1) {
+            d = dd + (l - 1) * 3;
+            ref = is_ref(a1 >> (l - 1), b1 >> (l - 1));
+            l--;
+        } else if (cams) {
+            q = __ffs(cams) - 1;
+            cams &= cams - 1;
+            d = dd + (L - 1) * 3 + q * 3;
+            ref = is_ref(2 * a1 + (q >> 1), 2 * b1 + (q & 1));
+        } else {
+            break;
+        }
+        int s0[3], s1[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) srv_desc2(S, bk, d[c], ref, g, idx1, toff1, in1, s0[c], s1[c]);
+        if (q < 0) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                v0[c] += s0[c];
+                v1[c] += s1[c];
+            }
+        } else {
+            uint32_t *dst = cache + (size_t)slot_of(q) * B2 + o0;
+            dst[0] = in0 ? ycocg_to_rgb8(v0[0] + s0[0], v0[1] + s0[1], v0[2] + s0[2]) : 0u;
+            if (tile1) dst[1] = in1 ? ycocg_to_rgb8(v1[0] + s1[0], v1[1] + s1[1], v1[2] + s1[2]) : 0u;
+        }
+    }
+}
+
 // Persistent decode of every light field's items, G items per pass.
 template <int BS>
 __global__ void __launch_bounds__(256) k_decode_batch(const BatchPtrs P, const uint4 *__restrict__ items,
@@ -1624,51 +1691,16 @@ __global__ void __launch_bounds__(256) k_decode_batch(const BatchPtrs P, const u
             s_desc[d] = make_desc(S, T, bk, l, a, b, c, k % S.nbx, k / S.nbx);
         }
         __syncthreads();
-        for (int gi = 0; gi < G; gi++) {
+        const int Bc = BS > 0 ? BS : s_S[0].B;                  // one block size per call
+        const int npair = Bc * ((Bc + 1) >> 1);
+        for (int e = threadIdx.x; e < G * npair; e += blockDim.x) {
+            const int gi = e / npair, pp = e - gi * npair;
             if (first + gi >= n) continue;
             const uint4 it = s_it[gi];
             if (!it.y) continue;
-            const DevStream &S = s_S[gi];
-            const LevelTabs &T = s_T[gi];
-            const Blk<BS> bk(S.B);
-            const int B = bk.size(), B2 = B * B, L = S.L;
-            const size_t plane = (size_t)S.W * S.H;
-            const int node = (int)(it.x / (uint32_t)S.nblocks), k = (int)(it.x - (uint32_t)node * S.nblocks);
-            const int a1 = node / T.gv[1], b1 = node - (node / T.gv[1]) * T.gv[1];
-            const int bx = k % S.nbx, by = k / S.nbx;
-            const int bw = min(B, S.W - bx * B), bh = min(B, S.H - by * B);
-            const Desc *dd = s_desc + gi * kDescPer;
-            for (int p = threadIdx.x; p < B2; p += blockDim.x) {
-                const int yy = p / B, xx = p - yy * B;
-                const bool inside = xx < bw && yy < bh;
-                PixGeom g;
-                g.x = bx * B + min(xx, bw - 1);
-                g.y = by * B + min(yy, bh - 1);
-                g.blk = 0;
-                g.idx = (g.y - by * B) * bw + (g.x - bx * B);
-                g.toff = (g.y - by * B) * B + (g.x - bx * B);
-                const size_t rb =
-                    ((size_t)(a1 >> (L - 1)) * T.gv[L] + (b1 >> (L - 1))) * 3 * plane + (size_t)g.y * S.W + g.x;
-                int v[3] = {__ldg(S.roots + rb), __ldg(S.roots + rb + plane), __ldg(S.roots + rb + 2 * plane)};
-                for (int l = L - 1; l >= 1; l--) {
-                    const bool ref = is_ref(a1 >> (l - 1), b1 >> (l - 1));
-#pragma unroll
-                    for (int c = 0; c < 3; c++) v[c] += srv_desc(S, bk, dd[(l - 1) * 3 + c], ref, g);
-                }
-                uint32_t slot = it.z;
-#pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    if (!((it.y >> q) & 1u)) continue;
-                    const int i = 2 * a1 + (q >> 1), j = 2 * b1 + (q & 1);
-                    const bool ref = is_ref(i, j);
-                    const Desc *d0 = dd + (L - 1) * 3 + q * 3;
-                    const int w0 = v[0] + srv_desc(S, bk, d0[0], ref, g);
-                    const int w1 = v[1] + srv_desc(S, bk, d0[1], ref, g);
-                    const int w2 = v[2] + srv_desc(S, bk, d0[2], ref, g);
-                    cache[(size_t)slot * B2 + p] = inside ? ycocg_to_rgb8(w0, w1, w2) : 0u;
-                    slot++;
-                }
-            }
+            const Blk<BS> bk(s_S[gi].B);
+            decode_pair_l1(s_S[gi], s_T[gi], bk, s_desc + gi * kDescPer, it.x, it.y, pp,
+                           [&](int q) { return it.z + __popc(it.y & ((1u << q) - 1u)); }, cache);
         }
     }
 }
@@ -1833,10 +1865,9 @@ __global__ void __launch_bounds__(256) k_decode_resident(const __grid_constant__
     __shared__ Desc s_desc[kGroup * kDescPer];
     load_tabs(S, T);
     const Blk<BS> bk(S.B);
-    const int B = bk.size(), B2 = B * B;
+    const int B = bk.size();
     const int L = S.L;
     const uint32_t n = (uint32_t)(__ldg(counters) >> 32);
-    const size_t plane = (size_t)S.W * S.H;
     const int nd = (L - 1) * 3 + 12;
     __syncthreads();
     for (uint32_t first = blockIdx.x * kGroup; first < n; first += gridDim.x * kGroup) {
@@ -1863,43 +1894,14 @@ __global__ void __launch_bounds__(256) k_decode_resident(const __grid_constant__
             s_desc[d] = make_desc(S, T, bk, l, a, b, c, k % S.nbx, k / S.nbx);
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < kGroup * B2; e += blockDim.x) {
-            const int gi = e / B2, p = e - gi * B2;
+        const int npair = B * ((B + 1) >> 1);
+        for (int e = threadIdx.x; e < kGroup * npair; e += blockDim.x) {
+            const int gi = e / npair, pp = e - gi * npair;
             if (first + gi >= n) continue;
             const uint4 it = __ldg(items + 2 * (size_t)(first + gi));
             const uint4 sl = __ldg(items + 2 * (size_t)(first + gi) + 1);
-            const uint32_t slot[4] = {sl.x, sl.y, sl.z, sl.w};
-            const int node = (int)(it.x / (uint32_t)S.nblocks), k = (int)(it.x - (uint32_t)node * S.nblocks);
-            const int a1 = node / T.gv[1], b1 = node - (node / T.gv[1]) * T.gv[1];
-            const int bx = k % S.nbx, by = k / S.nbx;
-            const int yy = p / B, xx = p - yy * B;
-            const int bw = min(B, S.W - bx * B), bh = min(B, S.H - by * B);
-            const bool inside = xx < bw && yy < bh;
-            PixGeom g;
-            g.x = bx * B + min(xx, bw - 1);
-            g.y = by * B + min(yy, bh - 1);
-            g.blk = 0;
-            g.idx = (g.y - by * B) * bw + (g.x - bx * B);
-            g.toff = (g.y - by * B) * B + (g.x - bx * B);
-            const size_t rb = ((size_t)(a1 >> (L - 1)) * T.gv[L] + (b1 >> (L - 1))) * 3 * plane + (size_t)g.y * S.W + g.x;
-            int v[3] = {__ldg(S.roots + rb), __ldg(S.roots + rb + plane), __ldg(S.roots + rb + 2 * plane)};
-            const Desc *dd = s_desc + gi * nd;
-            for (int l = L - 1; l >= 1; l--) {
-                const bool ref = is_ref(a1 >> (l - 1), b1 >> (l - 1));
-#pragma unroll
-                for (int c = 0; c < 3; c++) v[c] += srv_desc(S, bk, dd[(l - 1) * 3 + c], ref, g);
-            }
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                if (!((it.y >> q) & 1u)) continue;
-                const int i = 2 * a1 + (q >> 1), j = 2 * b1 + (q & 1);
-                const bool ref = is_ref(i, j);
-                const Desc *d0 = dd + (L - 1) * 3 + q * 3;
-                const int w0 = v[0] + srv_desc(S, bk, d0[0], ref, g);
-                const int w1 = v[1] + srv_desc(S, bk, d0[1], ref, g);
-                const int w2 = v[2] + srv_desc(S, bk, d0[2], ref, g);
-                cache[(size_t)slot[q] * B2 + p] = inside ? ycocg_to_rgb8(w0, w1, w2) : 0u;
-            }
+            decode_pair_l1(S, T, bk, s_desc + gi * nd, it.x, it.y, pp,
+                           [&](int q) { return q == 0 ? sl.x : q == 1 ? sl.y : q == 2 ? sl.z : sl.w; }, cache);
         }
         __syncthreads();
     }
