@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU baseline sample")
     ap.add_argument("--traffic-json", default=os.path.join(ROOT, "profiles", "decode_traffic.json"))
     ap.add_argument("--path", type=int, default=0, help="render path: 0 cached blocks, 1 direct, 2 per-tile")
-    ap.add_argument("--form", default="plain", choices=["plain", "diff", "batched", "serve", "encode", "lod"],
+    ap.add_argument("--form", default="plain", choices=["plain", "diff", "batched", "serve", "encode", "lod", "study"],
                     help="plain: the paper-scale render step (default); diff: 200 Adam steps of the "
                          "differentiable form")
     return ap.parse_args()
@@ -449,6 +449,98 @@ def run_lod(args):
     }), flush=True)
 
 
+def run_study(args):
+    """Rate/quality study on the paper-scale synthetic field (the analogue of
+    the paper's comparisons against hierarchical coding without motion
+    compensation and of its block-size and search-window tables): every
+    point is a device encode (hmlfc_encode_device, byte-identical to the
+    oracle's encoder) and a device decode of all samples for the PSNR.
+    Headline: the bitrate of coding without motion compensation, over that
+    of quarter-pel HMLFC, at the PSNR HMLFC reaches with q = 4 (log-bpp
+    interpolated along the q sweep)."""
+    import torch
+    import paper_1902_09396_gb300 as H
+
+    c = synthlf.CONFIGS[args.config]
+    lf = synthlf.make_lf(c.seed, c.nu, c.nv, c.width, c.height, c.n_planes, c.disp_max, c.texture)
+    d_lf = torch.from_numpy(lf).cuda()
+    ref = d_lf.reshape(-1, 3).float()
+    n_px = c.nu * c.nv * c.width * c.height
+    co = torch.stack(torch.meshgrid(torch.arange(c.nu), torch.arange(c.nv), torch.arange(c.height),
+                                    torch.arange(c.width), indexing="ij"), -1).reshape(-1, 4)
+    coords = co[:, [0, 1, 3, 2]].to(torch.int32).contiguous().cuda()     # (i, j, x, y) in [i][j][y][x] order
+
+    def point(mc, q, L=c.levels, B=c.block, Ws=c.search, tr=0, tp=0):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        data = H.encode_device(d_lf, L, B, Ws, q, t_ref=tr, t_pred=tp, mc=mc)
+        t_enc = time.perf_counter() - t0
+        st = H.Stream(data)
+        out = st.decode_pixels(coords).float()
+        mse = float(torch.mean((out - ref) ** 2))
+        info = st.info
+        return {"mc": mc, "q": q, "L": L, "B": B, "Ws": Ws, "T": [tr, tp], "bpp": len(data) * 8.0 / n_px,
+                "psnr_db": float("inf") if mse == 0 else 10.0 * math.log10(255.0 ** 2 / mse),
+                "encode_s": t_enc, "sig_blocks": info["n_sig"], "ref_tile_bytes": info["device_bytes"]}
+
+    rd = {name: [point(mc, q) for q in (2, 4, 8, 16)]
+          for name, mc in (("no_mc", 0), ("integer_pel", 3), ("quarter_pel", 1))}
+    target = next(p["psnr_db"] for p in rd["quarter_pel"] if p["q"] == 4)
+    bpp_q = next(p["bpp"] for p in rd["quarter_pel"] if p["q"] == 4)
+
+    def bpp_at(curve, psnr):
+        pts = sorted(curve, key=lambda p: p["psnr_db"])
+        for a, b in zip(pts, pts[1:]):
+            if a["psnr_db"] <= psnr <= b["psnr_db"]:
+                t = (psnr - a["psnr_db"]) / (b["psnr_db"] - a["psnr_db"])
+                return math.exp(math.log(a["bpp"]) + t * (math.log(b["bpp"]) - math.log(a["bpp"])))
+        return None
+
+    ratios = {k: (bpp_at(v, target) / bpp_q if bpp_at(v, target) else None) for k, v in rd.items()}
+
+    def ref_store(tr, tp):
+        """Resident reference SRVs: block-sparse tiles (B*B int16 per
+        significant block + a 4-byte tile index per block) against CSR of
+        the same dequantised coefficients (2-byte value + 2-byte column per
+        non-zero, 4-byte row pointers) per reference node-channel."""
+        st = H.Stream(H.encode_device(d_lf, c.levels, c.block, c.search, 4, t_ref=tr, t_pred=tp))
+        info = st.info
+        coeff, _ = st.dequant()
+        ref_nc = []
+        base = 0
+        for l in range(c.levels - 1, -1, -1):
+            gu, gv = (c.nu + (1 << l) - 1) >> l, (c.nv + (1 << l) - 1) >> l
+            ref_nc += [base + (a * gv + b) * 3 + ch for a in range(0, gu, 2) for b in range(0, gv, 2) for ch in range(3)]
+            base += 3 * gu * gv
+        rc = coeff[torch.tensor(ref_nc, device=coeff.device)]
+        nnz = int(torch.count_nonzero(rc))
+        nb = info["n_blocks"]
+        tiles = info["n_ref_tiles"] * c.block * c.block * 2 + len(ref_nc) * nb * 4
+        csr = nnz * 4 + len(ref_nc) * (c.height + 1) * 4
+        del coeff, rc
+        return {"T": [tr, tp], "ref_node_channels": len(ref_nc), "significant_tiles": info["n_ref_tiles"],
+                "nonzero_coefficients": nnz, "block_sparse_bytes": tiles, "csr_bytes": csr,
+                "dense_bytes": len(ref_nc) * c.width * c.height * 2}
+
+    sweeps = {
+        "block": [point(1, 4, B=b) for b in (8, 16, 32)],
+        "window": [point(1, 4, Ws=w) for w in (1, 2, 4, 8)],
+        "levels": [point(1, 4, L=l) for l in (2, 3, 4, 5)],
+        "thresholds": [point(1, 4, tr=tr, tp=tp) for tr, tp in ((0, 0), (400, 800), (1600, 3200))],
+    }
+    print(json.dumps({
+        "metric": "bitrate of hierarchical coding without motion compensation over quarter-pel HMLFC at equal PSNR",
+        "value": ratios["no_mc"], "unit": "x", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": f"{c.name}: {c.nu}x{c.nv} grid of {c.width}x{c.height} RGB8 views, {c.n_planes} planes "
+                               f"0-{c.disp_max:g} px disparity; q in 2..16, T=0 unless stated"},
+        "psnr_target_db": target, "bpp_ratio_at_target": ratios, "rd": rd, "sweeps": sweeps,
+        "reference_store": [ref_store(0, 0), ref_store(400, 800)],
+        "gpu_launches": None, "cpu_baseline": None,
+    }), flush=True)
+
+
 def run_encode(args):
     """Device encoder (hmlfc_encode_device) on the paper-scale light field:
     one step encodes the whole 17x17x512^2 field, from the device-resident
@@ -566,6 +658,9 @@ def main():
         return
     if args.form == "lod":
         run_lod(args)
+        return
+    if args.form == "study":
+        run_study(args)
         return
     if args.form == "serve":
         run_serve(args)
