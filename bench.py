@@ -76,6 +76,25 @@ def workload_config(c, qstep, tr, tp, size, n_views) -> dict:
     }
 
 
+def job_time_ms(local_ms: float, world: int, device) -> float:
+    """Whole-job time of the timed region: the maximum over ranks (all-reduce
+    MAX, then a barrier); the local time when there is one rank."""
+    if world <= 1:
+        return float(local_ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_value(units_per_step: float, steps: int, world: int, total_ms: float) -> float:
+    """Whole-job throughput: every rank processes units_per_step per step
+    (replicas, weak scaling), divided by the slowest rank's time."""
+    return units_per_step * steps * world / (total_ms / 1000.0)
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -161,10 +180,11 @@ def cpu_baseline(data: bytes, arr, size: int, seconds: float):
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the oracle, as it stands, on the host cores."""
-    c, lf, arr, size, tr, tp, _ = make_workload(args)
+    """Reference arm: the oracle, as it stands, on the host cores (rank 0
+    only; other ranks exit without work)."""
     if rank != 0:
         return
+    c, lf, arr, size, tr, tp, _ = make_workload(args)
     import oracle
     data = oracle.encode(lf, c.levels, c.block, c.search, args.qstep, t_ref=tr, t_pred=tp).stream
     oracle.set_threads(os.cpu_count() or 1)
@@ -742,11 +762,7 @@ def main():
     phase_ms = None
     if args.path == 0:
         phase_ms = [float(sum(p[q].elapsed_time(p[q + 1]) for p in phases)) / args.steps for q in range(3)]
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
+    total_ms = job_time_ms(total_ms, world, "cuda")
 
     # end to end through the public API: views from host memory, the rendered
     # views copied back to pinned host memory inside the timed region
@@ -766,7 +782,7 @@ def main():
         return
 
     views_per_step = len(arr)
-    value = views_per_step * args.steps * world / (total_ms / 1000.0)
+    value = job_value(views_per_step, args.steps, world, total_ms)
     # compulsory bytes of one step: the cached path reads every distinct item
     # once per call; the per-ray and per-tile paths once per view
     out_bytes = float(n_out * 4)
