@@ -337,7 +337,7 @@ int render_cached(const hmlfc_stream *s, const std::vector<LaunchViews> &chunks,
     ds.lod = lod;
     const int64_t n_keys = (int64_t)g.nu * g.nv * g.nblocks;
     const size_t blk_bytes = (size_t)g.B * g.B * 4;
-    const uint32_t capacity = (uint32_t)std::min<int64_t>(n_keys, (int64_t)(g_cache_bytes / blk_bytes));
+    const uint32_t capacity = (uint32_t)std::min<int64_t>({n_keys, (int64_t)(g_cache_bytes / blk_bytes), kMaxSlots});
     if (capacity == 0) return 1;
     const int64_t n_ck = (int64_t)g.gu[1] * g.gv[1] * g.nblocks;
     const size_t o_flags = 0, o_slot = up256(o_flags + (size_t)n_keys), o_items = up256(o_slot + (size_t)n_keys * 4),
@@ -608,7 +608,8 @@ int hmlfc_render_views_noalloc(const hmlfc_stream *const *streams, int n_streams
                         "stream %d needs %zu bytes of block index in the fixed scratch, which holds %zu; "
                         "use hmlfc_render_views",
                         lf, o_cache + blk_bytes, kFixedScratchBytes);
-        const uint32_t capacity = (uint32_t)std::min<size_t>(n_keys, (kFixedScratchBytes - o_cache) / blk_bytes);
+        const uint32_t capacity =
+            (uint32_t)std::min<size_t>({(size_t)n_keys, (kFixedScratchBytes - o_cache) / blk_bytes, (size_t)kMaxSlots});
         uint8_t *flags = base;
         uint32_t *slotmap = reinterpret_cast<uint32_t *>(base + o_slot);
         uint4 *items = reinterpret_cast<uint4 *>(base + o_items);
@@ -693,7 +694,7 @@ int hmlfc_render_batch(const hmlfc_stream *const *streams, int n_streams, const 
     std::memcpy(img.data() + offs[3], tile_start.data(), sizeof(int) * tile_start.size());
     const int B = streams[0]->g.B;
     const size_t blk_bytes = (size_t)B * B * 4;
-    const uint32_t capacity = (uint32_t)std::min<int64_t>(n_keys, (int64_t)(g_batch.cache_bytes / blk_bytes));
+    const uint32_t capacity = (uint32_t)std::min<int64_t>({n_keys, (int64_t)(g_batch.cache_bytes / blk_bytes), kMaxSlots});
     const size_t o_flags = up256(img_bytes), o_slot = up256(o_flags + (size_t)n_keys),
                  o_items = up256(o_slot + (size_t)n_keys * 4), o_count = up256(o_items + (size_t)n_ck * 16),
                  o_cache = up256(o_count + 16), total = up256(o_cache + (size_t)capacity * blk_bytes);
@@ -727,7 +728,7 @@ int hmlfc_server_create(const hmlfc_stream *s, size_t cache_bytes, void *cuda_st
     const int64_t n_keys = (int64_t)g.nu * g.nv * g.nblocks;
     const int64_t n_ck = (int64_t)g.gu[1] * g.gv[1] * g.nblocks;
     const size_t blk = (size_t)g.B * g.B * 4;
-    const uint32_t capacity = (uint32_t)std::min<int64_t>(n_keys, (int64_t)(cache_bytes / blk));
+    const uint32_t capacity = (uint32_t)std::min<int64_t>({n_keys, (int64_t)(cache_bytes / blk), kMaxSlots});
     if (capacity == 0) return fail(HMLFC_E_INVALID_ARG, "cache of %zu bytes holds no block", cache_bytes);
     auto *sv = new (std::nothrow) hmlfc_server();
     if (!sv) return fail(HMLFC_E_OOM, "host allocation");

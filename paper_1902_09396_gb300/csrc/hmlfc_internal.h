@@ -18,6 +18,7 @@ constexpr uint32_t kMagic = 0x464C4D48u;
 constexpr uint32_t kVersion = 1u;
 constexpr int kHeaderWords = 32;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr int64_t kMaxSlots = 0x7FFFFFFF;   // cache slots stay below 2^31, so kNone is the only value with bit 31 set
 
 // Everything a kernel needs to decode samples of one stream.  Passed by value
 // as a kernel parameter (it lives in the constant bank while the kernel runs).

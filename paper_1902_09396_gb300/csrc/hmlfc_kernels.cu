@@ -1329,17 +1329,17 @@ __global__ void __launch_bounds__(TW *TH, 6) k_render_cached(const __grid_consta
                              (uint32_t)((r.y1 - by[1] * B) * B + (r.x1 - bx[1] * B))};
     (void)nbx;
     uint32_t slot[16];
-    bool all = true;
 #pragma unroll
-    for (int q = 0; q < 16; q++) {
-        slot[q] = __ldg(slotmap + cam[q >> 2] * nbl + blk[q & 3]);
-        all &= slot[q] != kNone;
-    }
+    for (int q = 0; q < 16; q++) slot[q] = __ldg(slotmap + (cam[q >> 2] * nbl + blk[q & 3]));
+    // slots are below 2^31 and kNone has the top bit set: one OR tree tells whether any sample missed the cache
+    uint32_t any_none = 0;
+#pragma unroll
+    for (int q = 0; q < 16; q++) any_none |= slot[q];
     float o[3];
-    if (all) {
+    if (!(any_none >> 31)) {
         uint32_t val[16];
 #pragma unroll
-        for (int q = 0; q < 16; q++) val[q] = __ldg(cache + slot[q] * (uint32_t)(B * B) + off[q & 3]);
+        for (int q = 0; q < 16; q++) val[q] = __ldg(cache + (slot[q] * (uint32_t)(B * B) + off[q & 3]));
         // sample order of blend16: q = a*8 + b*4 + xs*2 + ys  ->  cam a*2+b, corner xs*2+ys
         blend16(r, [&](int a, int b, int xs, int ys, int, int, int, int) { return val[a * 8 + b * 4 + xs * 2 + ys]; }, o);
     } else {
