@@ -182,6 +182,21 @@ int hmlfc_render_views(const hmlfc_stream *const *streams, int n_streams, const 
                        float *d_out, void *cuda_stream);
 
 /*
+ * Render into host memory: as hmlfc_render_views, with the output in h_out
+ * (host memory, the same packed layout; page-locked for full speed).  The
+ * library stages the output in device memory allocated from cuda_stream's
+ * pool; the decode runs once for all views, then the blend runs in groups
+ * of 8 views, each group's views copied to the host on a library-owned copy
+ * stream while the next group blends.  Asynchronous: h_out holds the views
+ * once cuda_stream has synchronised (cuda_stream waits for the copies).
+ * Calls on different CUDA streams overlap: one call's decode runs while an
+ * earlier call's copies drain (all copies run in order on one copy stream
+ * per device).  Errors: as hmlfc_render_views; HMLFC_E_OOM for the staging.
+ */
+int hmlfc_render_views_host(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views, int n_views,
+                            float *h_out, void *cuda_stream);
+
+/*
  * Level-of-detail render: as hmlfc_render_views with every sample decoded
  * progressively to `level` (see hmlfc_decode_pixels_lod): the 16 samples of
  * a ray come from the level-`level` reconstructions of its cameras' nodes,

@@ -79,6 +79,7 @@ def lib() -> C.CDLL:
     L.hmlfc_decode_pixels.argtypes = [P, P, I64, P, P]
     L.hmlfc_decode_pixels_lod.argtypes = [P, P, I64, I, P, P]
     L.hmlfc_render_views_lod.argtypes = [P, I, P, I, I, P, P]
+    L.hmlfc_render_views_host.argtypes = [P, I, P, I, P, P]
     L.hmlfc_touched_bytes_union_lod.argtypes = [P, I, P, I, I, P, P]
     L.hmlfc_check_status.argtypes = [P, P]
     L.hmlfc_render_views.argtypes = [P, I, P, I, P, P]
@@ -218,6 +219,22 @@ def render_views(streams, views, out=None, cuda_stream=None, level: int = 0):
     else:
         _check(lib().hmlfc_render_views(_streams_array(streams), len(streams), va, len(va), _ptr(out),
                                         _stream_handle(cuda_stream)))
+    return out
+
+
+def render_views_host(streams, views, out=None, cuda_stream=None):
+    """render_views into host memory (a page-locked float32 CPU tensor of
+    out_size(views) floats): decode once, blend in groups of views, each group
+    copied back while the next blends.  Asynchronous: out holds the views once
+    the stream has synchronised."""
+    import torch
+    va = _views_array(views)
+    if out is None:
+        out = torch.empty(out_size(views), dtype=torch.float32, pin_memory=True)
+    if out.is_cuda or out.dtype != torch.float32 or not out.is_contiguous() or out.numel() < out_size(views):
+        raise ValueError("out must be a contiguous float32 host tensor of out_size(views) floats")
+    _check(lib().hmlfc_render_views_host(_streams_array(streams), len(streams), va, len(va), _ptr(out),
+                                         _stream_handle(cuda_stream)))
     return out
 
 

@@ -247,19 +247,19 @@ uint32_t tile_div_magic(const hmlfc_view &V) {
 
 // The views of stream `lf`, in launch chunks that fit the by-value view table.
 int view_chunks(const hmlfc_view *views, int n_views, int lf, std::vector<LaunchViews> &chunks,
-                std::vector<int> &tiles) {
+                std::vector<int> &tiles, int per_chunk = kMaxViewsPerLaunch) {
     chunks.clear();
     tiles.clear();
     std::vector<int> idx;
     for (int v = 0; v < n_views; v++)
         if (views[v].lf == lf && views[v].width > 0 && views[v].height > 0) idx.push_back(v);
-    for (size_t s = 0; s < idx.size(); s += kMaxViewsPerLaunch) {
+    for (size_t s = 0; s < idx.size(); s += (size_t)per_chunk) {
         chunks.emplace_back();
         LaunchViews &lv = chunks.back();
         std::memset(&lv, 0, sizeof lv);
         lv.tile_w = 16;
         lv.tile_h = 16;
-        const size_t e = std::min(idx.size(), s + kMaxViewsPerLaunch);
+        const size_t e = std::min(idx.size(), s + (size_t)per_chunk);
         int64_t t = 0;
         for (size_t k = s; k < e; k++) {
             const hmlfc_view &V = views[idx[k]];
@@ -330,8 +330,30 @@ int sm_count(int device) {
 // the tiles reach, give each a slot of a stream-ordered scratch cache, decode
 // those blocks once, then blend every ray from the cache.  Returns 1 (and
 // launches nothing) when the scratch cannot be had, so the caller falls back.
+// Device-to-host copies that follow each blend chunk of a render into host
+// memory: after chunk c's blend, `copy` waits for it and copies that chunk's
+// views from d_out to h_out, so the copies overlap the later chunks.
+struct HostSink {
+    float *h_out = nullptr;
+    cudaStream_t copy = nullptr;
+    cudaEvent_t ev = nullptr;
+};
+
+cudaError_t sink_chunk(const HostSink *sink, const LaunchViews &lv, const float *d_out, cudaStream_t st) {
+    if (!sink) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(sink->ev, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sink->copy, sink->ev, 0);
+    for (int v = 0; v < lv.n_views && e == cudaSuccess; v++) {
+        const hmlfc_view &V = lv.views[v];
+        const size_t n = (size_t)V.width * V.height * 3;
+        e = cudaMemcpyAsync(sink->h_out + V.out_offset, d_out + V.out_offset, n * sizeof(float), cudaMemcpyDeviceToHost,
+                            sink->copy);
+    }
+    return e;
+}
+
 int render_cached(const hmlfc_stream *s, const std::vector<LaunchViews> &chunks, const std::vector<int> &tiles,
-                  float *d_out, cudaStream_t st, int lod = 0) {
+                  float *d_out, cudaStream_t st, int lod = 0, const HostSink *sink = nullptr) {
     const Geometry &g = s->g;
     DevStream ds = s->ds;
     ds.lod = lod;
@@ -362,8 +384,10 @@ int render_cached(const hmlfc_stream *s, const std::vector<LaunchViews> &chunks,
     phase_mark(1, st);
     if (e == cudaSuccess) e = launch_decode_blocks(ds, items, counters, cache, sm_count(s->device) * 32, st);
     phase_mark(2, st);
-    for (size_t c = 0; c < chunks.size() && e == cudaSuccess; c++)
+    for (size_t c = 0; c < chunks.size() && e == cudaSuccess; c++) {
         e = launch_render_cached(ds, chunks[c], tiles[c], slotmap, cache, d_out, st);
+        if (e == cudaSuccess) e = sink_chunk(sink, chunks[c], d_out, st);
+    }
     phase_mark(3, st);
     const cudaError_t ef = cudaFreeAsync(base, st);
     if (e == cudaSuccess) e = ef;
@@ -574,6 +598,76 @@ int hmlfc_render_views_lod(const hmlfc_stream *const *streams, int n_streams, co
         }
     }
     return HMLFC_OK;
+}
+
+// Render into host memory: the output is staged in device memory from the
+// call's stream-ordered pool; the decode runs once for all views, then the
+// blend runs in groups of kHostChunkViews views and each group is copied to
+// the host on a per-device copy stream while the next group blends.
+constexpr int kHostChunkViews = 8;
+
+cudaStream_t copy_stream(int device) {
+    static std::mutex mu;
+    static std::vector<cudaStream_t> per_dev;
+    std::lock_guard<std::mutex> lock(mu);
+    if ((int)per_dev.size() <= device) per_dev.resize(device + 1, nullptr);
+    if (!per_dev[device] && cudaStreamCreateWithFlags(&per_dev[device], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        per_dev[device] = nullptr;
+    }
+    return per_dev[device];
+}
+
+int hmlfc_render_views_host(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views, int n_views,
+                            float *h_out, void *cuda_stream) {
+    int rc = check_views(streams, n_streams, h_views, n_views);
+    if (rc != HMLFC_OK) return rc;
+    if (n_views > 0 && !h_out) return fail(HMLFC_E_INVALID_ARG, "h_out is NULL");
+    if (n_views == 0) return HMLFC_OK;
+    DeviceGuard guard(streams[0]->device);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    size_t n_out = 0;
+    for (int v = 0; v < n_views; v++)
+        n_out = std::max(n_out, (size_t)h_views[v].out_offset + (size_t)h_views[v].width * h_views[v].height * 3);
+    HostSink sink;
+    sink.h_out = h_out;
+    sink.copy = copy_stream(streams[0]->device);
+    if (!sink.copy) return fail(HMLFC_E_CUDA, "copy stream");
+    void *dbuf = nullptr;
+    cudaError_t e = cudaMallocAsync(&dbuf, std::max<size_t>(n_out, 1) * sizeof(float), st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HMLFC_E_OOM, "device staging of %zu output floats", n_out);
+    }
+    float *d_out = static_cast<float *>(dbuf);
+    cudaEvent_t done = nullptr;
+    e = cudaEventCreateWithFlags(&sink.ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+    std::vector<LaunchViews> chunks;
+    std::vector<int> tiles;
+    for (int lf = 0; lf < n_streams && e == cudaSuccess && rc == HMLFC_OK; lf++) {
+        rc = view_chunks(h_views, n_views, lf, chunks, tiles, kHostChunkViews);
+        if (rc != HMLFC_OK || chunks.empty()) continue;
+        if (g_render_path == 0) {
+            rc = render_cached(streams[lf], chunks, tiles, d_out, st, 0, &sink);
+            if (rc == HMLFC_OK) continue;
+            if (rc != 1) break;
+            rc = HMLFC_OK;   // no scratch: per-tile staging needs none
+        }
+        for (size_t c = 0; c < chunks.size() && e == cudaSuccess; c++) {
+            e = launch_render(streams[lf]->ds, chunks[c], tiles[c], d_out, g_render_path == 1 ? 1 : 0, st);
+            if (e == cudaSuccess) e = sink_chunk(&sink, chunks[c], d_out, st);
+        }
+    }
+    // the caller's stream waits for the last copy; the staging is freed behind it
+    if (e == cudaSuccess) e = cudaEventRecord(done, sink.copy);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, done, 0);
+    const cudaError_t ef = cudaFreeAsync(dbuf, st);
+    if (sink.ev) cudaEventDestroy(sink.ev);
+    if (done) cudaEventDestroy(done);
+    if (rc != HMLFC_OK) return rc;
+    if (e == cudaSuccess) e = ef;
+    return e == cudaSuccess ? HMLFC_OK : cuda_fail(e, "render to host");
 }
 
 // Allocation-free variant of the cached render: the decoded-block cache, its

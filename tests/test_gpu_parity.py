@@ -301,3 +301,50 @@ def test_render_batch_graph_replay(H, torch_cuda, tiny_streams, tiny_cfg):
         g.replay()
         torch.cuda.synchronize()
         assert np.array_equal(out.cpu().numpy().astype(np.float64), want)
+
+
+@pytest.mark.parametrize("path", [0, 1, 2])
+def test_render_views_host_equals_device_render(torch_cuda, tiny_streams, tiny_cfg, path):
+    """The host-output render gives the device render's bits for every path,
+    with gaps between views left untouched, also when the decoded-block cache
+    overflows or is absent (per-tile fallback)."""
+    torch = torch_cuda
+    import paper_1902_09396_gb300 as H
+    c = tiny_cfg
+    st = H.Stream(tiny_streams[c.qstep].stream)
+    geo = S.lf_geometry(c.nu, c.nv, c.width, c.height)
+    views = S.views_to_array(S.random_views(51, geo, 19, [(64, 64), (33, 17), (48, 80)]))
+    gap = 7
+    off = 0
+    for v in range(len(views)):                     # leave 7 floats between views
+        views[v]["out_offset"] = off
+        off += int(views[v]["width"]) * int(views[v]["height"]) * 3 + gap
+    H.set_render_path(path)
+    try:
+        for cache in (256 << 20, 3 * st.info["block"] ** 2 * 4, 0):
+            H.set_block_cache_bytes(cache)
+            dev = torch.full((off,), -5.0, dtype=torch.float32, device="cuda")
+            H.render_views([st], views, dev)
+            host = torch.full((off,), -5.0, dtype=torch.float32).pin_memory()
+            H.render_views_host([st], views, host)
+            torch.cuda.synchronize()
+            assert torch.equal(dev.cpu(), host), (path, cache)
+    finally:
+        H.set_block_cache_bytes(256 << 20)
+        H.set_render_path(0)
+
+
+def test_render_views_host_two_streams_and_back_to_back(torch_cuda, tiny_streams, tiny_cfg, ragged_lf):
+    torch = torch_cuda
+    import paper_1902_09396_gb300 as H
+    c = tiny_cfg
+    a = H.Stream(tiny_streams[c.qstep].stream)
+    b = H.Stream(O.encode(ragged_lf, 2, 8, 4, 4).stream)
+    va = S.random_views(61, S.lf_geometry(c.nu, c.nv, c.width, c.height), 5, [(40, 40)])
+    vb = S.random_views(62, S.lf_geometry(5, 3, 37, 29), 6, [(30, 20)], lf=1)
+    views = S.views_to_array(va + vb)
+    dev = H.render_views([a, b], views)
+    outs = [H.render_views_host([a, b], views) for _ in range(3)]   # three calls in flight on one stream
+    torch.cuda.synchronize()
+    for o in outs:
+        assert torch.equal(dev.cpu(), o)
