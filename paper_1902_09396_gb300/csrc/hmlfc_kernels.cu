@@ -503,10 +503,22 @@ __device__ __forceinline__ void srv_desc2(const DevStream &S, const Blk<BS> &bk,
     const int c2 = inb ? clampi(x0 + 2, 0, S.W - 1) : c1;
     const int ya = clampi(y0, 0, S.H - 1), yb = clampi(y0 + 1, 0, S.H - 1);
     const int cx = (int)(D.d0.w & 0xFFFFu), cy = (int)(D.d0.w >> 16);
-    const int a0 = tap(S, bk, D.d1, cx, cy, c0, ya), a1 = tap(S, bk, D.d1, cx, cy, c1, ya);
-    const int a2 = tap(S, bk, D.d1, cx, cy, c2, ya);
-    const int b0 = tap(S, bk, D.d1, cx, cy, c0, yb), b1 = tap(S, bk, D.d1, cx, cy, c1, yb);
-    const int b2 = tap(S, bk, D.d1, cx, cy, c2, yb);
+    // the six taps are 2 rows x 3 columns: tile row / column and in-tile offsets once each
+    const int tya = bk.div(ya), tyb = bk.div(yb);
+    const int tx0 = bk.div(c0), tx1 = bk.div(c1), tx2 = bk.div(c2);
+    const uint32_t la = tya == cy ? D.d1.x : D.d1.z, ra = tya == cy ? D.d1.y : D.d1.w;   // row a: left / right tile
+    const uint32_t lb = tyb == cy ? D.d1.x : D.d1.z, rb = tyb == cy ? D.d1.y : D.d1.w;
+    const int oya = (ya - tya * B) * B, oyb = (yb - tyb * B) * B;
+    const int ox0 = c0 - tx0 * B, ox1 = c1 - tx1 * B, ox2 = c2 - tx2 * B;
+    const bool l0 = tx0 == cx, l1 = tx1 == cx, l2 = tx2 == cx;
+    const int16_t *T = S.tiles;
+    const size_t B2s = (size_t)B * B;
+    const int a0 = __ldg(T + (l0 ? la : ra) * B2s + (oya + ox0));
+    const int a1 = __ldg(T + (l1 ? la : ra) * B2s + (oya + ox1));
+    const int a2 = __ldg(T + (l2 ? la : ra) * B2s + (oya + ox2));
+    const int b0 = __ldg(T + (l0 ? lb : rb) * B2s + (oyb + ox0));
+    const int b1 = __ldg(T + (l1 ? lb : rb) * B2s + (oyb + ox1));
+    const int b2 = __ldg(T + (l2 ? lb : rb) * B2s + (oyb + ox2));
     const int w00 = (4 - fx) * (4 - fy), w10 = fx * (4 - fy), w01 = (4 - fx) * fy, w11 = fx * fy;
     const int p0 = (w00 * a0 + w10 * a1 + w01 * b0 + w11 * b1 + 8) >> 4;
     const int p1 = (w00 * a1 + w10 * a2 + w01 * b1 + w11 * b2 + 8) >> 4;
