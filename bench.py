@@ -816,6 +816,29 @@ def main():
         dom_bytes = bytes_per_step
         dom_s = avg_step_s
     achieved = dom_bytes / dom_s / 1e9
+    # the same kernel against the issue-limited integer rate: every distinct
+    # (level-l node, block) pair the step reaches is evaluated once per pixel
+    # and channel by the super-item decode; ~30 integer operations per
+    # predictive evaluation and ~8 per reference one (tile read)
+    alu = None
+    if args.path == 0:
+        evals_pred = evals_ref = 0.0
+        for l in range(c.levels):
+            _, d_l = H.touched_bytes_union([st], arr, with_blocks=True, level=l)
+            gu, gv = (c.nu + (1 << l) - 1) >> l, (c.nv + (1 << l) - 1) >> l
+            ref_frac = ((gu + 1) // 2) * ((gv + 1) // 2) / (gu * gv)
+            evals_ref += d_l * ref_frac * c.block * c.block * 3
+            evals_pred += d_l * (1.0 - ref_frac) * c.block * c.block * 3
+        ops = 30.0 * evals_pred + 8.0 * evals_ref
+        sm_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+        alu_peak = 152 * 4 * 32 * sm_mhz * 1e6 / 1e9
+        alu = {"bound": "alu", "kernel": dom, "achieved": ops / dom_s / 1e9, "peak": alu_peak, "unit": "Gop/s",
+               "frac": ops / dom_s / 1e9 / alu_peak, "algorithmic_ops_per_launch": ops,
+               "evaluations": {"predictive": evals_pred, "reference": evals_ref},
+               "note": "peak = issue-limited lane operations (152 SMs x 4 schedulers x 32 lanes x max SM clock); "
+                       "ops = 30 per predictive and 8 per reference (sample, channel, level) evaluation, each "
+                       "distinct (node, block) pair of a level evaluated once per pixel; reference share per level "
+                       "taken as the share of reference nodes in the level's grid"}
     res = {
         "metric": f"{size}x{size} novel views/s (fused random-access decode + render)",
         "value": value,
@@ -842,6 +865,7 @@ def main():
                              f"compressed records, tiles and root pixels ({(bytes_per_step - out_bytes) / 1e6:.1f} MB) "
                              f"+ the decoded-block cache it writes ({cache_bytes / 1e6:.1f} MB); the kernel is "
                              f"bound by instruction issue (see profiles/), not by DRAM"},
+        "roofline_alu": alu,
         "step_compulsory_bytes": bytes_per_step,
         "phases_ms": None if phase_ms is None else {"mark+assign": phase_ms[0], "decode": phase_ms[1],
                                                     "blend": phase_ms[2]},
