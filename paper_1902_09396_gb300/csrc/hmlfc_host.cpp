@@ -343,11 +343,18 @@ cudaError_t sink_chunk(const HostSink *sink, const LaunchViews &lv, const float 
     if (!sink) return cudaSuccess;
     cudaError_t e = cudaEventRecord(sink->ev, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(sink->copy, sink->ev, 0);
-    for (int v = 0; v < lv.n_views && e == cudaSuccess; v++) {
-        const hmlfc_view &V = lv.views[v];
-        const size_t n = (size_t)V.width * V.height * 3;
-        e = cudaMemcpyAsync(sink->h_out + V.out_offset, d_out + V.out_offset, n * sizeof(float), cudaMemcpyDeviceToHost,
+    // one copy per run of views whose output ranges follow each other
+    for (int v = 0; v < lv.n_views && e == cudaSuccess;) {
+        const size_t first = (size_t)lv.views[v].out_offset;
+        size_t end = first + (size_t)lv.views[v].width * lv.views[v].height * 3;
+        int w = v + 1;
+        while (w < lv.n_views && (size_t)lv.views[w].out_offset == end) {
+            end += (size_t)lv.views[w].width * lv.views[w].height * 3;
+            w++;
+        }
+        e = cudaMemcpyAsync(sink->h_out + first, d_out + first, (end - first) * sizeof(float), cudaMemcpyDeviceToHost,
                             sink->copy);
+        v = w;
     }
     return e;
 }
