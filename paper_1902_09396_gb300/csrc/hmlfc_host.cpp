@@ -30,6 +30,36 @@ struct BatchTuning {
     size_t cache_bytes = (size_t)2 << 30; // decoded-block cache of one batched call
 } g_batch;
 
+// Stream-ordered scratch of the render calls comes from one library pool per
+// device that keeps the memory it has mapped (release threshold: never), so
+// that back-to-back calls reuse it instead of mapping it again after each
+// synchronisation.  Falls back to the device's default pool.
+cudaError_t lib_malloc_async(void **p, size_t n, int device, cudaStream_t st) {
+    static std::mutex mu;
+    static std::vector<cudaMemPool_t> pools;
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if ((int)pools.size() <= device) pools.resize(device + 1, nullptr);
+        if (!pools[device]) {
+            cudaMemPoolProps props;
+            std::memset(&props, 0, sizeof props);
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = device;
+            if (cudaMemPoolCreate(&pools[device], &props) == cudaSuccess) {
+                uint64_t keep = UINT64_MAX;
+                cudaMemPoolSetAttribute(pools[device], cudaMemPoolAttrReleaseThreshold, &keep);
+            } else {
+                cudaGetLastError();
+                pools[device] = nullptr;
+            }
+        }
+        pool = pools[device];
+    }
+    return pool ? cudaMallocFromPoolAsync(p, n, pool, st) : cudaMallocAsync(p, n, st);
+}
+
 void phase_mark(int k, cudaStream_t st) {
     if (g_phase_ev[k]) cudaEventRecord(g_phase_ev[k], st);
 }
@@ -373,7 +403,7 @@ int render_cached(const hmlfc_stream *s, const std::vector<LaunchViews> &chunks,
                  o_count = up256(o_items + (size_t)n_ck * 16), o_cache = up256(o_count + 8),
                  total = up256(o_cache + (size_t)capacity * blk_bytes);
     void *base = nullptr;
-    if (cudaMallocAsync(&base, total, st) != cudaSuccess) {
+    if (lib_malloc_async(&base, total, s->device, st) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
@@ -641,7 +671,7 @@ int hmlfc_render_views_host(const hmlfc_stream *const *streams, int n_streams, c
     sink.copy = copy_stream(streams[0]->device);
     if (!sink.copy) return fail(HMLFC_E_CUDA, "copy stream");
     void *dbuf = nullptr;
-    cudaError_t e = cudaMallocAsync(&dbuf, std::max<size_t>(n_out, 1) * sizeof(float), st);
+    cudaError_t e = lib_malloc_async(&dbuf, std::max<size_t>(n_out, 1) * sizeof(float), streams[0]->device, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(HMLFC_E_OOM, "device staging of %zu output floats", n_out);
