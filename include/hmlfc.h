@@ -13,8 +13,13 @@
  *   pointers owned by the caller.  The library never frees caller memory.
  * - Calls that take a `cuda_stream` (a cudaStream_t passed as void*; NULL =
  *   the legacy default stream) enqueue their work on it and return without
- *   synchronising, except hmlfc_load_stream, hmlfc_encode,
- *   hmlfc_check_status and hmlfc_touched_bytes, which are synchronous.
+ *   synchronising, except hmlfc_load_stream, hmlfc_encode_device and
+ *   hmlfc_check_status, which synchronise it.  hmlfc_encode,
+ *   hmlfc_requantize and the hmlfc_touched_bytes* counters are host-only.
+ * - Render scratch (decoded-block cache, its index, the host-output staging)
+ *   is allocated stream-ordered from a library-owned pool per device that
+ *   keeps the memory it has mapped for later calls.
+ * - The hmlfc_set_* switches are process-wide and not thread-safe.
  * - A stream object may be used from several CUDA streams at once for
  *   reading (render, decode, backward); it must not be freed while work
  *   that uses it is in flight.
