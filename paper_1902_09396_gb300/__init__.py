@@ -20,7 +20,7 @@ from .build import LIB, build  # noqa: F401
 # Identifies the render kernel's code; profile figures recorded for another
 # version are not reused.
 KERNEL_VERSION = "render-cached-v9"
-ENCODER_VERSION = "encode-planes-v3"
+ENCODER_VERSION = "encode-planes-v4"
 
 OK, E_INVALID_ARG, E_CORRUPT, E_OOM, E_CUDA, E_TIMEOUT, E_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 MC_OFF, MC_QPEL, MC_ZERO, MC_INTEGER = 0, 1, 2, 3

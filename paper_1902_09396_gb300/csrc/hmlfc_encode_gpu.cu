@@ -25,7 +25,7 @@ using namespace hmlfc;
 
 namespace {
 
-constexpr int kEncThreads = 256;
+constexpr int kEncThreads = 128;
 constexpr int kMaxEncSearch = 32;           // window (2 Ws + 1)^2 candidates kept in shared memory
 constexpr int kMaxPlaneBlock = 32;          // largest block whose refinement phase planes fit in shared memory
 
@@ -145,7 +145,7 @@ __global__ void k_enc_rkv(const int16_t *__restrict__ lo, int16_t *__restrict__ 
 // (prediction from the reference member's dequantised SRV), else reference
 // member.  ZMV: predictive with motion forced to (0, 0), sign +.
 template <bool PRED, int SEARCH, bool ZMV>
-__global__ void __launch_bounds__(kEncThreads, 6) k_enc_block(
+__global__ void __launch_bounds__(kEncThreads, 12) k_enc_block(
     const EncGeo G, const EncItem *__restrict__ items, const int16_t *__restrict__ child_lev,
     const int16_t *__restrict__ par_recon, const int16_t *__restrict__ rhat_in, int16_t *__restrict__ recon_out,
     int16_t *__restrict__ rhat_out, int16_t *__restrict__ lvbuf, uint32_t *__restrict__ hdr,
