@@ -80,3 +80,27 @@ def test_path_views_sampled_pixels(paper, how):
     want = O.Stream(data).render_pixels(views, pix)
     idx = (views["out_offset"][pix[:, 0]] + (pix[:, 2] * 512 + pix[:, 1]) * 3)[:, None] + np.arange(3)[None, :]
     assert np.max(np.abs(out[idx] - want)) <= 1e-3
+
+
+@pytest.mark.parametrize("level", [1, 2])
+def test_progressive_decode_at_full_size(paper, level):
+    """Progressive decode at the benchmark's configuration: 200,000 random
+    samples bit-exact at the level, and 10,000 sampled pixels of the 64
+    cached-path views within 1e-3 of the oracle's FP64 render at the level."""
+    import paper_1902_09396_gb300 as H
+    torch, c, _, data, views = paper
+    st, ost = H.Stream(data), O.Stream(data)
+    rng = np.random.default_rng(80 + level)
+    n = 200_000
+    coords = np.stack([rng.integers(0, c.nu, n), rng.integers(0, c.nv, n), rng.integers(0, c.width, n),
+                       rng.integers(0, c.height, n)], -1).astype(np.int32)
+    got = st.decode_pixels(torch.from_numpy(coords).cuda(), level=level)
+    assert np.array_equal(got.cpu().numpy(), ost.decode_samples(coords, level=level))
+    out = H.render_views([st], views, level=level)
+    torch.cuda.synchronize()
+    out = out.cpu().numpy().astype(np.float64)
+    m = 10_000
+    pix = np.stack([rng.integers(0, 64, m), rng.integers(0, 512, m), rng.integers(0, 512, m)], -1).astype(np.int32)
+    want = ost.render_pixels(views, pix, level=level)
+    idx = (views["out_offset"][pix[:, 0]] + (pix[:, 2] * 512 + pix[:, 1]) * 3)[:, None] + np.arange(3)[None, :]
+    assert np.max(np.abs(out[idx] - want)) <= 1e-3
