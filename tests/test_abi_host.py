@@ -37,6 +37,20 @@ def test_encoder_matches_oracle_bytes(tiny_lf, tiny_cfg, ragged_lf, mc):
         assert a == b
 
 
+@pytest.mark.parametrize("search", [0, 1, 7, 16])
+def test_encoder_matches_oracle_search_windows(ragged_lf, search):
+    for mc in (O.MC_QPEL, O.MC_INTEGER):
+        assert H.encode(ragged_lf, 2, 8, search, 3, mc=mc, threads=4) == O.encode(ragged_lf, 2, 8, search, 3, mc=mc).stream
+
+
+@pytest.mark.parametrize("block", [4, 5, 32, 64])
+def test_encoder_matches_oracle_block_sizes(block):
+    lf = S.make_lf(23, 3, 4, 70, 45, 3, 5.0, "pink")
+    for q, tr, tp in [(1, 0, 0), (6, 100, 300)]:
+        a = O.encode(lf, 2, block, 3, q, t_ref=tr, t_pred=tp).stream
+        assert H.encode(lf, 2, block, 3, q, t_ref=tr, t_pred=tp, threads=4) == a
+
+
 def test_encoder_thread_count_does_not_change_output(ragged_lf):
     a = H.encode(ragged_lf, 2, 8, 4, 4, threads=1)
     b = H.encode(ragged_lf, 2, 8, 4, 4, threads=7)
