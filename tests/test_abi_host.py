@@ -135,3 +135,20 @@ def test_touched_bytes_union(tiny_streams, tiny_cfg):
     assert abs(H.touched_bytes_union([st], twice) - (want + 48 * 40 * 12)) < 1e-6
     three = S.views_to_array(vs)
     assert H.touched_bytes_union([st], three) <= float(np.sum(H.touched_bytes([st], three))) + 1e-6
+
+
+@pytest.mark.gpu
+def test_touched_bytes_significant_blocks_match_oracle():
+    """On the hand-derived field with significant predictive records and
+    reference tiles reached directly and through motion-compensation taps,
+    the product's counter equals the oracle's (whose values are pinned by
+    closed forms), per view and over the union."""
+    from tests.test_oracle_pins import _sig_field
+    data = O.encode(_sig_field(), 1, 8, 4, 1, mc=O.MC_ZERO).stream
+    views = S.views_to_array([S.grid_view(1.0, 1.0, 4.5, 2.5, 2, 2), S.grid_view(1.0, 1.0, 5.5, 2.5, 2, 2),
+                              S.grid_view(0.0, 0.0, 5.5, 2.5, 2, 2)])
+    want = O.Stream(data).touched_bytes(views)
+    st = H.Stream(data)
+    assert np.allclose(H.touched_bytes([st], views), want, rtol=0, atol=1e-6)
+    for v in range(len(views)):
+        assert abs(H.touched_bytes_union([st], views[v:v + 1]) - want[v]) < 1e-6

@@ -39,6 +39,15 @@ MUTANTS = {
     "touched_root_bytes": ("if (!root_seen[rp]) { root_seen[rp] = 1; acc += 6.0; }",
                            "if (!root_seen[rp]) { root_seen[rp] = 1; acc += 3.0; }",
                            ["touched"]),
+    "touched_record_header_dropped": ("acc += 2.0 + 4.0 * (1 + (orc_bise_bits(md, bb, (uint64_t)bw * bh) + 31) / 32);",
+                                      "acc += 2.0 + 4.0 * ((orc_bise_bits(md, bb, (uint64_t)bw * bh) + 31) / 32);",
+                                      ["touched_sig"]),
+    "touched_tap_tile_double_counted": ("if (!blk_seen[rk]) {\n                                                    blk_seen[rk] = 1;",
+                                        "if (1) {\n                                                    blk_seen[rk] = 1;",
+                                        ["touched_sig", "touched_direct_and_taps"]),
+    "touched_tap_tile_bytes": ("if (find_record(s, rnc, kk)) acc += g->B * g->B * 2.0 + 4.0;",
+                               "if (find_record(s, rnc, kk)) acc += g->B * g->B * 2.0;",
+                               ["touched_sig"]),
     "progressive_one_level_too_deep": ("for (int l = lod; l < L; l++)", "for (int l = lod > 0 ? lod - 1 : 0; l < L; l++)",
                                        ["progressive"]),
 }
@@ -73,6 +82,10 @@ def _run(name, tiny_lf, tiny_cfg, ragged_lf):
         pins.test_adjoint_dot_product((st, views))
     elif name == "touched":
         pins.test_touched_bytes_closed_form(tiny_cfg)
+    elif name == "touched_sig":
+        pins.test_touched_bytes_significant_blocks_closed_form()
+    elif name == "touched_direct_and_taps":
+        pins.test_touched_bytes_reference_reached_directly_and_by_taps()
     elif name == "progressive":
         pins.test_progressive_lossless_equals_level_images(tiny_lf, tiny_cfg, ragged_lf, O.MC_QPEL)
     else:

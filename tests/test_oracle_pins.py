@@ -604,6 +604,74 @@ def test_touched_bytes_closed_form(tiny_cfg):
     assert abs(st.touched_bytes(v)[0] - want) < 1e-6
 
 
+
+def _sig_field(seed=5):
+    """A 2x2 grid of 16x16 views (L = 1, B = 8) whose significant blocks are
+    known by hand.  Cameras (0,0), (0,1), (1,0) show one texture; camera (1,1)
+    adds d(x, y) = (x mod 8) + 8y to all three of R, G, B in the top block row
+    (y < 8).  Adding d to R, G and B moves only Y of YCoCg-R (Co = R - B and
+    Cg = G - t cancel it), so in the YCoCg-R domain, with q = 1, T = 0 and
+    zero motion (mv = 0, sign +):
+    - the root (rounded mean of 4) is Y + floor((d + 2) / 4), Co, Cg;
+    - reference (0,0)'s SRV is -floor((d + 2) / 4) in Y: Y blocks 0 and 1
+      significant (resident tiles), every other block zero;
+    - predictive (0,1), (1,0) equal the reference's SRV: zero residual;
+    - predictive (1,1)'s residual is d: Y blocks 0 and 1 significant with
+      levels 0..63, i.e. BISE alphabet 2^6, 6 bits a value, 64 * 6 / 32 = 12
+      payload words behind the one header word."""
+    rng = np.random.default_rng(seed)
+    base = rng.integers(0, 150, size=(16, 16, 3))
+    lf = np.broadcast_to(base, (2, 2, 16, 16, 3)).copy()
+    yy, xx = np.mgrid[0:8, 0:16]
+    lf[1, 1, 0:8, :, :] += ((xx % 8) + 8 * yy)[..., None]
+    return lf.astype(np.uint8)
+
+
+def test_touched_bytes_significant_blocks_closed_form():
+    """Algorithmic bytes with significant predictive records and reference
+    tiles (Sec. 4.6 records, Sec. 4.8.2 resident references): a view at
+    camera (1,1) only, reaching pixels x in {x0..x0+2}, y in {2, 3, 4} of its
+    block 0.  Bytes = 12 per output pixel + 6 per root pixel + per touched
+    predictive block (16 B group entry + MV bits / 8) + the significant Y
+    record of block 0 (2 B offset + 4 B header + 12 x 4 B payload = 54 B)
+    + every significant reference tile its zero-motion taps reach, once
+    (8 * 8 * 2 + 4 = 132 B).  Taps of (x, y) read (x + 1, y + 1) too, so
+    x0 = 5 reaches reference block 1 through its taps alone; x0 = 4 does not."""
+    lf = _sig_field()
+    st = O.Stream(O.encode(lf, 1, 8, 4, 1, mc=O.MC_ZERO).stream)
+    # the hand derivation of which blocks are significant
+    nc = {(a, b, c): (a * 2 + b) * 3 + c for a in range(2) for b in range(2) for c in range(3)}
+    for (a, b, c), n in nc.items():
+        for k in range(4):
+            sig = st.block_info(n, k)[0]
+            want = c == 0 and k < 2 and (a, b) in ((0, 0), (1, 1))
+            assert bool(sig) == want, (a, b, c, k)
+    mode, b = O.bise_choose(2 * (8 * 4 + 1) ** 2)
+    mv_bits = O.bise_bits(mode, b, 15) / 15.0
+    record, tile = 2 + 4 * (1 + 64 * 6 // 32), 8 * 8 * 2 + 4
+    fixed = 2 * 2 * 12 + 9 * 6 + 3 * (16 + mv_bits / 8.0) + record
+    got = st.touched_bytes(S.views_to_array([S.grid_view(1.0, 1.0, 4.5, 2.5, 2, 2),
+                                             S.grid_view(1.0, 1.0, 5.5, 2.5, 2, 2)]))
+    assert abs(got[0] - (fixed + tile)) < 1e-6
+    assert abs(got[1] - (fixed + 2 * tile)) < 1e-6
+
+
+def test_touched_bytes_reference_reached_directly_and_by_taps():
+    """The field of the test above seen from (u, v) = (0, 0): the ray's
+    neighbours are all four cameras (u = 0 gives cameras 0 and 1 with
+    weights 1 and 0).  Reference (0,0)'s Y tiles 0 and 1 are reached directly
+    and through the taps of three predictive nodes, and count once each; the
+    three predictive nodes add 3 channels x (group entry + MV bits) each, and
+    only (1,1)'s Y block 0 has a record."""
+    lf = _sig_field()
+    st = O.Stream(O.encode(lf, 1, 8, 4, 1, mc=O.MC_ZERO).stream)
+    mode, b = O.bise_choose(2 * (8 * 4 + 1) ** 2)
+    mv_bits = O.bise_bits(mode, b, 15) / 15.0
+    record, tile = 2 + 4 * (1 + 64 * 6 // 32), 8 * 8 * 2 + 4
+    want = 2 * 2 * 12 + 9 * 6 + 3 * 3 * (16 + mv_bits / 8.0) + record + 2 * tile
+    got = st.touched_bytes(S.views_to_array([S.grid_view(0.0, 0.0, 5.5, 2.5, 2, 2)]))
+    assert abs(got[0] - want) < 1e-6
+
 # --------------------------------------------------------------------------
 # progressive decoding (Sec. 1, Sec. 4: the upper levels of the tree carry
 # what the views share, the lower levels their detail)
