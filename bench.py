@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU baseline sample")
     ap.add_argument("--traffic-json", default=os.path.join(ROOT, "profiles", "decode_traffic.json"))
     ap.add_argument("--path", type=int, default=0, help="render path: 0 cached blocks, 1 direct, 2 per-tile")
+    ap.add_argument("--no-points", action="store_true", help="skip the extra operating points (q sweep, T=0)")
     ap.add_argument("--form", default="plain", choices=["plain", "diff", "batched", "serve", "encode", "lod", "study"],
                     help="plain: the paper-scale render step (default); diff: 200 Adam steps of the "
                          "differentiable form")
@@ -67,12 +68,14 @@ def make_workload(args):
 
 
 def workload_config(c, qstep, tr, tp, size, n_views) -> dict:
-    """The `config` of both arms: the workload by what it is, with its sizes."""
+    """The `config` of both arms: the workload by what it is, with its sizes,
+    and how the GPU arm keeps L2 from carrying data between timed steps."""
     return {
         "workload": f"{c.name}: {c.nu}x{c.nv} grid of {c.width}x{c.height} RGB8 views, {c.n_planes} planes "
                     f"0-{c.disp_max:g} px disparity, L={c.levels} B={c.block} quarter-pel MC Ws={c.search} "
                     f"q={qstep} T=({tr},{tp}); step = {n_views}-pose circular path of {size}x{size} views",
         "views_per_step": n_views,
+        "l2": "GPU arm: flushed (256 MB write) before every timed step",
     }
 
 
@@ -203,14 +206,19 @@ def run_reference(args, rank, world):
             times.append(dt)
     rate = per_step * len(times) / sum(times) / (size * size)
     unit = f"{size}x{size} views/s"
+    full_rays = size * size * len(arr)
+    sample = (f"each step is a bounded sample: {per_step} random rays of the {full_rays} rays of the "
+              f"{len(arr)} views (1/{full_rays // per_step} of a full step); value = sampled rays per second / "
+              f"rays per view, i.e. a rate extrapolated from the sample")
     print(json.dumps({
         "impl": "reference", "metric": f"{size}x{size} novel views/s (fused random-access decode + render)",
         "value": rate, "unit": unit, "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000.0 * len(arr) / rate, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1000.0 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32 decode, f64 blend", "data": "synthetic",
         "config": workload_config(c, args.qstep, tr, tp, size, len(arr)),
-        "cpu_baseline": {"value": rate, "unit": unit, "cores": os.cpu_count(), "kind": "oracle",
-                         "sample": f"{per_step} random rays per step of the {len(arr)} views"},
+        "render_path": "oracle: FP64 render, random-access decode of each ray's 16 samples",
+        "rays_per_step": per_step, "rays_per_full_step": full_rays, "value_is_extrapolated": True,
+        "cpu_baseline": {"value": rate, "unit": unit, "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
         "e2e": {"value": rate, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -671,6 +679,78 @@ def run_encode(args):
     }), flush=True)
 
 
+def time_steps(H, st, arr, out, flush, stream, steps, warmup, path, world=1):
+    """W untimed steps, then K steps each timed with CUDA events on the
+    launching stream, L2 flushed by a 256 MB write before every step; with
+    the cached path, the four phase events of the render (before mark,
+    decode, blend, end) of each step too.  Returns (per-step ms, mean phase
+    ms [mark+assign, decode, blend] or None)."""
+    import torch
+    for _ in range(warmup):
+        flush.zero_()
+        H.render_views([st], arr, out)
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    phases = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    for evs in phases:
+        for e in evs:
+            e.record(stream)
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.zero_()
+        H.set_phase_events(phases[k] if path == 0 else None)
+        starts[k].record(stream)
+        H.render_views([st], arr, out)
+        ends[k].record(stream)
+    H.set_phase_events(None)
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    phase_ms = None
+    if path == 0:
+        phase_ms = [float(sum(p[q].elapsed_time(p[q + 1]) for p in phases)) / steps for q in range(3)]
+    return step_ms, phase_ms
+
+
+def rooflines(H, st, arr, n_out, ms_per_step, phase_ms, path, peak, peak_kind):
+    """The gather roofline of the dominant kernel and of the whole step.
+
+    Algorithmic bytes of a step (the touched-set count): the FP32 output
+    plus every distinct compressed item the step's rays reach -- root
+    pixels, predictive block records with their index entries and motion
+    vector bits, significant reference tiles.  The dominant kernel (the
+    block decode of the cached path) must read the compressed items once;
+    the decoded-block cache it writes and the blend reads back is this
+    design's intermediate, reported beside the roofline, not in it."""
+    out_bytes = float(n_out * 4)
+    if path == 0:
+        step_bytes, cam_blocks = H.touched_bytes_union([st], arr, with_blocks=True)
+    else:
+        step_bytes, cam_blocks = float(np.sum(H.touched_bytes([st], arr))), 0.0
+    B = st.info["block"]
+    cache_bytes = cam_blocks * B * B * 4
+    if path == 0:
+        dom, dom_bytes, dom_s = "k_decode_blocks", step_bytes - out_bytes, phase_ms[1] / 1000.0
+    else:
+        dom, dom_bytes, dom_s = "k_render", step_bytes, ms_per_step / 1000.0
+    kern = {"bound": "hbm", "kernel": dom, "achieved": dom_bytes / dom_s / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": dom_bytes / dom_s / 1e9 / peak, "algorithmic_bytes_per_launch": dom_bytes,
+            "launch_ms": dom_s * 1e3,
+            "intermediate_bytes": {"decoded_block_cache_written": cache_bytes,
+                                   "decoded_block_cache_read_by_blend": cache_bytes},
+            "note": f"peak = {peak_kind} HBM copy bandwidth; algorithmic bytes per launch = the step's distinct "
+                    f"compressed items (root pixels, predictive records with index entries and MV bits, significant "
+                    f"reference tiles), counted by the touched-set counter; the decoded-block cache the kernel "
+                    f"writes ({cache_bytes / 1e6:.1f} MB) is an intermediate of this design, not counted"}
+    step = {"bound": "hbm", "achieved": step_bytes / (ms_per_step / 1000.0) / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": step_bytes / (ms_per_step / 1000.0) / 1e9 / peak, "algorithmic_bytes_per_step": step_bytes,
+            "note": "FP32 output + distinct compressed items of the step, over the step's CUDA-event time"}
+    return kern, step, step_bytes, cam_blocks
+
+
 def main():
     args = parse()
     if args.form == "encode":
@@ -733,35 +813,10 @@ def main():
         psnr = 10 * math.log10(255.0 ** 2 / (se / cnt)) if se > 0 else float("inf")
     bpp = len(data) * 8.0 / (c.nu * c.nv * c.width * c.height)
 
-    for _ in range(args.warmup):
-        flush.zero_()
-        H.render_views([st], arr, out)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
     sampler = ClockSampler(local)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    # phase markers of the cached render (before mark, decode, blend, end)
-    phases = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
-    for evs in phases:
-        for e in evs:
-            e.record(stream)
-    torch.cuda.synchronize()
-    for k in range(args.steps):
-        flush.zero_()
-        H.set_phase_events(phases[k] if args.path == 0 else None)
-        starts[k].record(stream)
-        H.render_views([st], arr, out)
-        ends[k].record(stream)
-    H.set_phase_events(None)
-    torch.cuda.synchronize()
+    step_ms, phase_ms = time_steps(H, st, arr, out, flush, stream, args.steps, args.warmup, args.path, world)
     clocks = sampler.stop()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = float(sum(step_ms))
-    phase_ms = None
-    if args.path == 0:
-        phase_ms = [float(sum(p[q].elapsed_time(p[q + 1]) for p in phases)) / args.steps for q in range(3)]
     total_ms = job_time_ms(total_ms, world, "cuda")
 
     # end to end through the public API: view records from host memory, every
@@ -787,35 +842,20 @@ def main():
 
     views_per_step = len(arr)
     value = job_value(views_per_step, args.steps, world, total_ms)
-    # compulsory bytes of one step: the cached path reads every distinct item
-    # once per call; the per-ray and per-tile paths once per view
-    out_bytes = float(n_out * 4)
-    if args.path == 0:
-        bytes_per_step, cam_blocks = H.touched_bytes_union([st], arr, with_blocks=True)
-    else:
-        bytes_per_step, cam_blocks = float(np.sum(H.touched_bytes([st], arr))), 0.0
-    avg_step_s = total_ms / 1000.0 / args.steps
+    ms_per_step = total_ms / args.steps
     peak, peak_kind = peaks()
-    traffic = None
+    roof, roof_step, bytes_per_step, cam_blocks = rooflines(H, st, arr, n_out, ms_per_step, phase_ms, args.path,
+                                                            peak, peak_kind)
+    roof["traffic"] = None
     try:
         with open(args.traffic_json) as f:
             tj = json.load(f)
         if tj.get("kernel_version") == H.KERNEL_VERSION:
-            traffic = float(tj["dram_bytes_per_launch"])
+            roof["traffic"] = float(tj["dram_bytes_per_launch"])
+            roof["traffic_source"] = tj.get("source")
     except Exception:
         pass
-    cache_bytes = cam_blocks * c.block * c.block * 4
-    if args.path == 0:
-        # dominant kernel: the block decode; it must read the step's distinct
-        # compressed data and write one RGB8 cache entry per reached block
-        dom = "k_decode_blocks"
-        dom_bytes = (bytes_per_step - out_bytes) + cache_bytes
-        dom_s = phase_ms[1] / 1000.0
-    else:
-        dom = "k_render"
-        dom_bytes = bytes_per_step
-        dom_s = avg_step_s
-    achieved = dom_bytes / dom_s / 1e9
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     # the same kernel against the issue-limited integer rate: every distinct
     # (level-l node, block) pair the step reaches is evaluated once per pixel
     # and channel by the super-item decode; ~30 integer operations per
@@ -831,14 +871,34 @@ def main():
             evals_pred += d_l * (1.0 - ref_frac) * c.block * c.block * 3
         ops = 30.0 * evals_pred + 8.0 * evals_ref
         sm_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
-        alu_peak = 152 * 4 * 32 * sm_mhz * 1e6 / 1e9
-        alu = {"bound": "alu", "kernel": dom, "achieved": ops / dom_s / 1e9, "peak": alu_peak, "unit": "Gop/s",
-               "frac": ops / dom_s / 1e9 / alu_peak, "algorithmic_ops_per_launch": ops,
+        alu_peak = n_sm * 4 * 32 * sm_mhz * 1e6 / 1e9
+        dom_s = phase_ms[1] / 1000.0
+        alu = {"bound": "alu", "kernel": roof["kernel"], "achieved": ops / dom_s / 1e9, "peak": alu_peak,
+               "unit": "Gop/s", "frac": ops / dom_s / 1e9 / alu_peak, "algorithmic_ops_per_launch": ops,
                "evaluations": {"predictive": evals_pred, "reference": evals_ref},
-               "note": "peak = issue-limited lane operations (152 SMs x 4 schedulers x 32 lanes x max SM clock); "
-                       "ops = 30 per predictive and 8 per reference (sample, channel, level) evaluation, each "
-                       "distinct (node, block) pair of a level evaluated once per pixel; reference share per level "
-                       "taken as the share of reference nodes in the level's grid"}
+               "note": f"peak = issue-limited lane operations ({n_sm} SMs x 4 schedulers x 32 lanes x max SM clock; "
+                       f"derived, not measured); ops = 30 per predictive and 8 per reference (sample, channel, "
+                       f"level) evaluation, each distinct (node, block) pair of a level evaluated once per pixel; "
+                       f"reference share per level taken as the share of reference nodes in the level's grid"}
+    # other operating points of the same workload and poses: the quantiser
+    # steps of the compression sweep and the untruncated stream (T = 0)
+    points = {}
+    if args.path == 0 and not args.no_points:
+        k_steps = max(3, min(args.steps, 100))
+        for q, pr, pp in ((2, tr, tp), (8, tr, tp), (args.qstep, 0, 0)):
+            d2 = H.encode(lf, c.levels, c.block, c.search, q, t_ref=pr, t_pred=pp)
+            s2 = H.Stream(d2, device=local)
+            ms2, ph2 = time_steps(H, s2, arr, out, flush, stream, k_steps, 3, 0)
+            ms2 = float(np.mean(ms2))
+            r2, rs2, b2, cb2 = rooflines(H, s2, arr, n_out, ms2, ph2, 0, peak, peak_kind)
+            points[f"q={q} T=({pr},{pp})"] = {
+                "views_per_s": views_per_step / (ms2 / 1000.0), "ms_per_step": ms2, "steps": k_steps,
+                "phases_ms": {"mark+assign": ph2[0], "decode": ph2[1], "blend": ph2[2]},
+                "bpp": len(d2) * 8.0 / (c.nu * c.nv * c.width * c.height),
+                "decoded_camera_blocks": cb2,
+                "roofline_frac": r2["frac"], "roofline_step_frac": rs2["frac"],
+                "algorithmic_bytes_per_step": b2}
+            del s2
     res = {
         "metric": f"{size}x{size} novel views/s (fused random-access decode + render)",
         "value": value,
@@ -846,34 +906,27 @@ def main():
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": total_ms / args.steps,
+        "ms_per_step": ms_per_step,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "int32 decode, fp32 blend",
         "data": "synthetic",
-        "config": {
-            **workload_config(c, args.qstep, tr, tp, size, views_per_step),
-            "l2": "flushed (256 MB write) before every timed step",
-            "render_path": ["cached blocks", "direct per ray", "per-tile staging"][args.path],
-        },
+        "config": workload_config(c, args.qstep, tr, tp, size, views_per_step),
+        "render_path": ["cached blocks", "direct per ray", "per-tile staging"][args.path],
         "mrays_per_s": value * size * size / 1e6,
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "algorithmic_bytes_per_launch": dom_bytes,
-                     "note": f"peak {peak_kind} HBM copy bandwidth; algorithmic bytes = the step's distinct "
-                             f"compressed records, tiles and root pixels ({(bytes_per_step - out_bytes) / 1e6:.1f} MB) "
-                             f"+ the decoded-block cache it writes ({cache_bytes / 1e6:.1f} MB); the kernel is "
-                             f"bound by instruction issue (see profiles/), not by DRAM"},
+        "roofline": roof,
+        "roofline_step": roof_step,
         "roofline_alu": alu,
-        "step_compulsory_bytes": bytes_per_step,
         "phases_ms": None if phase_ms is None else {"mark+assign": phase_ms[0], "decode": phase_ms[1],
                                                     "blend": phase_ms[2]},
+        "decoded_camera_blocks": cam_blocks,
         "e2e": {"value": views_per_step * e2e_steps / e2e_s, "unit": f"{size}x{size} views/s",
                 "h2d_bytes_per_step": int(views_per_step * 96), "d2h_bytes_per_step": int(n_out * 4)},
-        "gpu_launches": args.steps * (4 if args.path == 0 else 1),
+        "gpu_launches": args.steps * (H.launches_per_render(arr) if args.path == 0 else 1),
         "stream": {"bytes": len(data), "bpp": bpp, "psnr_db": psnr, "encode_s": t_enc, "load_s": t_load,
                    "lf_gen_s": t_gen},
+        "operating_points": points,
     }
     if clocks:
         res["clocks"] = clocks

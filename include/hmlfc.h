@@ -219,10 +219,10 @@ int hmlfc_render_views_lod(const hmlfc_stream *const *streams, int n_streams, co
  *
  * Some callers cannot allocate device memory at the time they render: a
  * frame loop with a hard deadline that must not stall on the allocator or
- * fail on fragmentation midway, a host function or stream callback (where
- * CUDA API calls that allocate are not allowed), code running under a
- * caching allocator that has to account for every byte, or code capturing
- * work into a CUDA graph in a capture mode that forbids cudaMalloc.  This
+ * fail on fragmentation midway, code running under a caching allocator that
+ * has to account for every byte, or code capturing work into a CUDA graph
+ * in a capture mode that forbids cudaMalloc.  (It makes CUDA calls, so it
+ * cannot run inside a host function enqueued on a stream.)  This
  * entry point gives them the cached render of hmlfc_render_views, with the
  * same results, using only memory the library reserved when it was loaded:
  * a fixed device array of 32 MiB (HMLFC_FIXED_SCRATCH_BYTES), which every GPU

@@ -206,6 +206,22 @@ def out_size(views) -> int:
     return max((v.out_offset + v.width * v.height * 3 for v in views), default=0)
 
 
+MAX_VIEWS_PER_LAUNCH = 128       # views of one launch of the render kernels
+
+
+def launches_per_render(views) -> int:
+    """Kernels one hmlfc_render_views call launches on the cached path: per
+    stream, the footprint marking and the blend once per launch chunk of its
+    views, the slot assignment and the block decode once."""
+    lfs = np.asarray(views["lf"])
+    sizes = np.asarray(views["width"]).astype(np.int64) * np.asarray(views["height"])
+    n = 0
+    for lf in np.unique(lfs[sizes > 0]):
+        chunks = -(-int(np.sum((lfs == lf) & (sizes > 0))) // MAX_VIEWS_PER_LAUNCH)
+        n += 2 * chunks + 2
+    return n
+
+
 def render_views(streams, views, out=None, cuda_stream=None, level: int = 0):
     """Fused decode + render of novel views (float32 [sum H*W*3] CUDA tensor);
     level > 0 renders from the progressive decode at that level."""

@@ -419,7 +419,7 @@ int render_cached(const hmlfc_stream *s, const std::vector<LaunchViews> &chunks,
     for (size_t c = 0; c < chunks.size() && e == cudaSuccess; c++) e = launch_mark(ds, chunks[c], tiles[c], flags, st);
     if (e == cudaSuccess) e = launch_assign(ds, flags, slotmap, items, counters, capacity, st);
     phase_mark(1, st);
-    if (e == cudaSuccess) e = launch_decode_blocks(ds, items, counters, cache, sm_count(s->device) * 32, st);
+    if (e == cudaSuccess) e = launch_decode_blocks(ds, items, counters, cache, sm_count(s->device) * kDecodeCtasPerSm, st);
     phase_mark(2, st);
     for (size_t c = 0; c < chunks.size() && e == cudaSuccess; c++) {
         e = launch_render_cached(ds, chunks[c], tiles[c], slotmap, cache, d_out, st);
@@ -755,7 +755,7 @@ int hmlfc_render_views_noalloc(const hmlfc_stream *const *streams, int n_streams
             e = launch_mark(s->ds, lv, tiles, flags, st);
         }
         if (e == cudaSuccess) e = launch_assign(s->ds, flags, slotmap, items, counters, capacity, st);
-        if (e == cudaSuccess) e = launch_decode_blocks(s->ds, items, counters, cache, sm_count(dev) * 8, st);
+        if (e == cudaSuccess) e = launch_decode_blocks(s->ds, items, counters, cache, sm_count(dev) * kDecodeCtasPerSm, st);
         pos = 0;
         while (e == cudaSuccess && (k = next_chunk(h_views, n_views, lf, &pos, lv, tiles)) != 0) {
             if (k < 0) return fail(HMLFC_E_INVALID_ARG, "too many tiles in one launch");

@@ -74,3 +74,99 @@ def test_autotune_signature_is_order_free_and_size_aware():
     c[0]["width"] = 300
     assert signature(st, a) != signature(st, c)
     assert signature([_FakeStream((9, 9, 512, 512, 4, 16))], a) != signature(st, a)
+
+
+class _V:
+    def __init__(self, w, h):
+        self.width, self.height = w, h
+
+
+class _Req:
+    def __init__(self, rid, w, h, arrival=0.0):
+        self.rid, self.arrival, self.left, self.right = rid, arrival, _V(w, h), _V(w, h)
+
+
+def _drain(b, until_idle=200):
+    """Alternate admission and completion (a device that finishes the oldest
+    batch each round) until the batcher is idle; returns the batches."""
+    batches = []
+    for _ in range(until_idle):
+        if b.idle():
+            return batches
+        got = b.next_batch()
+        if got:
+            batches.append(got)
+        else:
+            b.complete()
+    raise AssertionError("batcher did not drain")
+
+
+def test_batcher_rejects_requests_larger_than_the_pool():
+    """Memory-based admission: a request whose output exceeds the whole pool
+    is rejected with a reason at once (it could never be admitted), and the
+    other requests are all served."""
+    from paper_1902_09396_gb300.serve import Batcher
+    pool = 3 * 2 * 64 * 64 * 3
+    b = Batcher(pool, max_batch_views=8, max_inflight=2)
+    reqs = [_Req(0, 64, 64), _Req(1, 512, 512), _Req(2, 32, 48), _Req(3, 64, 64)]
+    for r in reqs:
+        b.submit(r)
+    assert b.served[1].status == "rejected" and "exceeds the output pool" in b.served[1].reason
+    batches = _drain(b)
+    assert sorted(r.rid for bt in batches for r, _ in bt) == [0, 2, 3]
+    assert all(b.served[k].status == "done" for k in (0, 2, 3))
+    assert b.pool.free == [(0, pool)]
+
+
+def test_batcher_admits_by_free_memory_without_overlap():
+    """Ranges of requests in flight at the same time never overlap, and a
+    request waits (in order) until a completed batch frees enough memory."""
+    from paper_1902_09396_gb300.serve import Batcher, _pair_floats
+    rng = np.random.default_rng(3)
+    pool = 4 * 2 * 96 * 96 * 3
+    b = Batcher(pool, max_batch_views=6, max_inflight=3)
+    reqs = [_Req(k, int(rng.integers(8, 97)), int(rng.integers(8, 97))) for k in range(60)]
+    for r in reqs:
+        b.submit(r)
+    live = {}
+    order = []
+    for _ in range(1000):
+        if b.idle():
+            break
+        got = b.next_batch()
+        if got:
+            for r, o in got:
+                n = _pair_floats(r)
+                assert 0 <= o and o + n <= pool
+                for o2, n2 in live.values():
+                    assert o + n <= o2 or o2 + n2 <= o
+                live[r.rid] = (o, n)
+                order.append(r.rid)
+        else:
+            for r in b.complete():
+                live.pop(r.rid)
+    assert b.idle() and order == list(range(60))
+
+
+def test_batcher_cancellation_queued_and_in_flight():
+    """A queued request that is cancelled is never admitted; one cancelled
+    while its batch is on the device keeps its range until the batch
+    completes, is not reported done, and its batch's other requests are."""
+    from paper_1902_09396_gb300.serve import Batcher
+    pool = 2 * 2 * 64 * 64 * 3
+    b = Batcher(pool, max_batch_views=4, max_inflight=1)
+    for k in range(6):
+        b.submit(_Req(k, 64, 64))
+    first = b.next_batch()
+    assert [r.rid for r, _ in first] == [0, 1]
+    assert b.cancel(1) and b.served[1].status == "cancelled"
+    assert b.cancel(4) and b.served[4].status == "cancelled"
+    assert not b.cancel(4) and not b.cancel(99)
+    assert b.next_batch() == []                  # max_inflight reached
+    done = b.complete()
+    assert [r.rid for r in done] == [0]
+    rest = _drain(b)
+    assert sorted(r.rid for bt in rest for r, _ in bt) == [2, 3, 5]
+    assert [b.served[k].status for k in range(6)] == ["done", "cancelled", "done", "done", "cancelled", "done"]
+    assert not b.cancel(0)
+    assert b.pool.free == [(0, pool)]
