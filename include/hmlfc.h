@@ -16,9 +16,9 @@
  *   synchronising, except hmlfc_load_stream, hmlfc_encode_device and
  *   hmlfc_check_status, which synchronise it.  hmlfc_encode,
  *   hmlfc_requantize and the hmlfc_touched_bytes* counters are host-only.
- * - Render scratch (decoded-block cache, its index, the host-output staging)
- *   is allocated stream-ordered from a library-owned pool per device that
- *   keeps the memory it has mapped for later calls.
+ * - Render scratch (decoded camera images, their index, the host-output
+ *   staging) is allocated stream-ordered from a library-owned pool per
+ *   device that keeps the memory it has mapped for later calls.
  * - The hmlfc_set_* switches are process-wide and not thread-safe.
  * - A stream object may be used from several CUDA streams at once for
  *   reading (render, decode, backward); it must not be freed while work
@@ -232,12 +232,12 @@ int hmlfc_render_views_lod(const hmlfc_stream *const *streams, int n_streams, co
  * - Set-up: the first call on a device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call
  *   before any stream capture.
- * - Limit: the block index of a stream (5 bytes per (camera, block) pair plus
- *   16 bytes per (level-1 node, block) pair, plus one decoded block) must fit
- *   the array; a larger stream is rejected with HMLFC_E_UNSUPPORTED and a
- *   message, and hmlfc_render_views should be used instead.  Blocks beyond
- *   the space left for the decoded-block cache are decoded per ray (same
- *   results, slower).
+ * - Limit: the block index of a stream (1 byte per (camera, block) pair, 16
+ *   bytes per (level-2 node, block) pair, 4 bytes per camera) must fit the
+ *   array; a larger stream is rejected with HMLFC_E_UNSUPPORTED and a
+ *   message, and hmlfc_render_views should be used instead.  The rest of the
+ *   array holds decoded camera images (W * H * 4 bytes each); the rays of
+ *   cameras beyond it decode their samples directly (same results, slower).
  * - Sharing: every call uses the same array and leaves its contents behind;
  *   each call clears what must start at zero.  Calls whose GPU work overlaps
  *   (on different CUDA streams, or from several host threads without
@@ -403,18 +403,20 @@ int hmlfc_touched_bytes_union_lod(const hmlfc_stream *const *streams, int n_stre
 
 /*
  * Render strategy (process-wide).  0 (default): decode every (camera, block)
- * pair the call's views reach once, into a decoded-block cache held in
- * stream-ordered scratch memory (cudaMallocAsync on the call's stream, freed
- * on it when the call's work ends), then blend each ray from the cache;
- * blocks beyond the cache capacity, or all of them if the scratch cannot be
- * allocated, are decoded per tile instead.  1: every ray decodes its own 16
- * samples.  2: each 16 x 16 tile stages its footprint in shared memory.
- * All give bit-identical output.
+ * pair the call's views reach once, into per-camera RGB8 images held in
+ * stream-ordered scratch memory (allocated on the call's stream from the
+ * library pool, released on it when the call's work ends), then blend each
+ * ray from the images; the rays of cameras beyond the scratch capacity decode
+ * their samples directly, and if not even one image fits or the scratch
+ * cannot be allocated, each tile stages its own footprint instead.  1: every
+ * ray decodes its own 16 samples.  2: each 16 x 16 tile stages its footprint
+ * in shared memory.  All give bit-identical output.
  */
 int hmlfc_set_render_path(int path);
 
-/* Capacity of the decoded-block cache of one render call, in bytes
- * (default 256 MiB; B * B * 4 bytes per block; 0 disables the cache). */
+/* Scratch budget of one cached render call, in bytes: the block index plus
+ * the decoded camera images (W * H * 4 bytes each).  Default 1 GiB; 0
+ * disables the cache. */
 int hmlfc_set_block_cache_bytes(size_t bytes);
 
 /*

@@ -20,7 +20,7 @@ namespace {
 
 thread_local std::string g_err;
 int g_render_path = 0;                      // 0 cached blocks, 1 direct per ray, 2 per-tile staging
-size_t g_cache_bytes = (size_t)256 << 20;   // decoded-block cache of one render call
+size_t g_cache_bytes = (size_t)1 << 30;     // scratch of one cached render call: index and camera images
 cudaEvent_t g_phase_ev[4] = {nullptr, nullptr, nullptr, nullptr};   // optional phase markers of the cached render
 
 struct BatchTuning {
@@ -389,46 +389,94 @@ cudaError_t sink_chunk(const HostSink *sink, const LaunchViews &lv, const float 
     return e;
 }
 
+// Scratch of one cached render call: flags (one per (camera, block) pair,
+// grouped by super key), the camera slots, the decode items, two counters,
+// then the camera images (W x H RGB8 u32 each).
+struct CachedLayout {
+    size_t o_flags = 0, o_slot = 0, o_items = 0, o_count = 0, index_bytes = 0;
+    int64_t n_keys = 0, n_cam = 0;
+    size_t image_bytes = 0;
+};
+
+CachedLayout cached_layout(const hmlfc_stream *s) {
+    const Geometry &g = s->g;
+    CachedLayout c;
+    c.n_cam = (int64_t)g.nu * g.nv;
+    const int K = g.L < 2 ? g.L : 2;
+    const int64_t n_sk = (int64_t)g.gu[K] * g.gv[K] * g.nblocks;
+    c.n_keys = n_sk << (2 * K);            // flags grouped by super key, (2^K)^2 cameras each (zero-padded at edges)
+    c.o_flags = 0;
+    c.o_slot = up256((size_t)c.n_keys);
+    c.o_items = up256(c.o_slot + (size_t)c.n_cam * 4);
+    c.o_count = up256(c.o_items + (size_t)n_sk * 16);
+    c.index_bytes = up256(c.o_count + 16);
+    c.image_bytes = (size_t)g.W * g.H * 4;
+    return c;
+}
+
+// The cached render's launches on scratch `b` laid out by `c`, with room for
+// `capacity` camera images after the index.  each_chunk(f) calls f(launch
+// views, tiles) for every launch chunk of the stream's views, in order, and
+// returns the first error (or cudaSuccess); after each blend chunk, `sink`
+// (if any) copies it.
+template <class EachChunk>
+int cached_launches(const hmlfc_stream *s, const DevStream &ds, const CachedLayout &c, uint8_t *b, uint32_t capacity,
+                    EachChunk each_chunk, float *d_out, cudaStream_t st, const HostSink *sink, bool phases) {
+    uint8_t *flags = b + c.o_flags;
+    uint32_t *camslot = reinterpret_cast<uint32_t *>(b + c.o_slot);
+    uint4 *items = reinterpret_cast<uint4 *>(b + c.o_items);
+    unsigned long long *counters = reinterpret_cast<unsigned long long *>(b + c.o_count);
+    uint32_t *cache = reinterpret_cast<uint32_t *>(b + c.index_bytes);
+    if (phases) phase_mark(0, st);
+    // the scratch keeps an earlier call's contents: clear what must start at zero
+    cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)c.n_keys, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 16, st);
+    if (e == cudaSuccess)
+        e = each_chunk([&](const LaunchViews &lv, int t) { return launch_mark(ds, lv, t, flags, true, st); });
+    if (e == cudaSuccess) e = launch_assign(ds, flags, camslot, items, counters, capacity, st);
+    if (phases) phase_mark(1, st);
+    if (e == cudaSuccess)
+        e = launch_decode_blocks(ds, items, counters, camslot, cache, sm_count(s->device) * kDecodeCtasPerSm, st);
+    if (phases) phase_mark(2, st);
+    if (e == cudaSuccess)
+        e = each_chunk([&](const LaunchViews &lv, int t) {
+            cudaError_t r = launch_render_cached(ds, lv, t, camslot, cache, capacity >= c.n_cam, d_out, st);
+            if (r == cudaSuccess) r = sink_chunk(sink, lv, d_out, st);
+            return r;
+        });
+    if (phases) phase_mark(3, st);
+    return e == cudaSuccess ? HMLFC_OK : cuda_fail(e, "cached render");
+}
+
+// Camera images that fit `budget` bytes of scratch after the index (0 when
+// not even one fits).
+uint32_t cached_capacity(const CachedLayout &c, size_t budget) {
+    if (budget <= c.index_bytes) return 0;
+    return (uint32_t)std::min<int64_t>({c.n_cam, (int64_t)((budget - c.index_bytes) / c.image_bytes), kMaxSlots});
+}
+
 int render_cached(const hmlfc_stream *s, const std::vector<LaunchViews> &chunks, const std::vector<int> &tiles,
                   float *d_out, cudaStream_t st, int lod = 0, const HostSink *sink = nullptr) {
-    const Geometry &g = s->g;
     DevStream ds = s->ds;
     ds.lod = lod;
-    const int64_t n_keys = (int64_t)g.nu * g.nv * g.nblocks;
-    const size_t blk_bytes = (size_t)g.B * g.B * 4;
-    const uint32_t capacity = (uint32_t)std::min<int64_t>({n_keys, (int64_t)(g_cache_bytes / blk_bytes), kMaxSlots});
+    const CachedLayout c = cached_layout(s);
+    const uint32_t capacity = cached_capacity(c, g_cache_bytes);
     if (capacity == 0) return 1;
-    const int64_t n_ck = (int64_t)g.gu[1] * g.gv[1] * g.nblocks;
-    const size_t o_flags = 0, o_slot = up256(o_flags + (size_t)n_keys), o_items = up256(o_slot + (size_t)n_keys * 4),
-                 o_count = up256(o_items + (size_t)n_ck * 16), o_cache = up256(o_count + 8),
-                 total = up256(o_cache + (size_t)capacity * blk_bytes);
+    const size_t total = up256(c.index_bytes + (size_t)capacity * c.image_bytes);
     void *base = nullptr;
     if (lib_malloc_async(&base, total, s->device, st) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
-    uint8_t *b = static_cast<uint8_t *>(base);
-    uint8_t *flags = b + o_flags;
-    uint32_t *slotmap = reinterpret_cast<uint32_t *>(b + o_slot);
-    uint4 *items = reinterpret_cast<uint4 *>(b + o_items);
-    unsigned long long *counters = reinterpret_cast<unsigned long long *>(b + o_count);
-    uint32_t *cache = reinterpret_cast<uint32_t *>(b + o_cache);
-    phase_mark(0, st);
-    cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)n_keys, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 8, st);
-    for (size_t c = 0; c < chunks.size() && e == cudaSuccess; c++) e = launch_mark(ds, chunks[c], tiles[c], flags, st);
-    if (e == cudaSuccess) e = launch_assign(ds, flags, slotmap, items, counters, capacity, st);
-    phase_mark(1, st);
-    if (e == cudaSuccess) e = launch_decode_blocks(ds, items, counters, cache, sm_count(s->device) * kDecodeCtasPerSm, st);
-    phase_mark(2, st);
-    for (size_t c = 0; c < chunks.size() && e == cudaSuccess; c++) {
-        e = launch_render_cached(ds, chunks[c], tiles[c], slotmap, cache, d_out, st);
-        if (e == cudaSuccess) e = sink_chunk(sink, chunks[c], d_out, st);
-    }
-    phase_mark(3, st);
+    auto each_chunk = [&](auto f) {
+        cudaError_t e = cudaSuccess;
+        for (size_t k = 0; k < chunks.size() && e == cudaSuccess; k++) e = f(chunks[k], tiles[k]);
+        return e;
+    };
+    int rc = cached_launches(s, ds, c, static_cast<uint8_t *>(base), capacity, each_chunk, d_out, st, sink, true);
     const cudaError_t ef = cudaFreeAsync(base, st);
-    if (e == cudaSuccess) e = ef;
-    return e == cudaSuccess ? HMLFC_OK : cuda_fail(e, "cached render");
+    if (rc == HMLFC_OK && ef != cudaSuccess) rc = cuda_fail(ef, "cached render scratch");
+    return rc;
 }
 
 }  // namespace
@@ -487,10 +535,11 @@ int hmlfc_load_stream(const void *h_bytes, size_t nbytes, int device, void *cuda
     const size_t sz_tab = ref_tab.size() * 4 + 4;
     const size_t sz_tiles = (size_t)(s->n_tiles + 1) * B2 * 2;
     const size_t sz_src = tile_src.size() * 4 + 16;
+    const size_t sz_planes = (size_t)g.n_ref_nc * plane * 2 + 256;   // padded: a pixel pair may read one past
     size_t o_roots = 0, o_groups = up256(o_roots + sz_roots), o_offs = up256(o_groups + sz_groups),
            o_recs = up256(o_offs + sz_offs), o_mvs = up256(o_recs + sz_recs), o_tab = up256(o_mvs + sz_mvs),
            o_tiles = up256(o_tab + sz_tab), o_src = up256(o_tiles + sz_tiles), o_status = up256(o_src + sz_src),
-           total = up256(o_status + 256);
+           o_planes = up256(o_status + 256), total = up256(o_planes + sz_planes);
     cudaError_t e = cudaMalloc(&s->d_mem, total);
     if (e != cudaSuccess) {
         delete s;
@@ -528,6 +577,7 @@ int hmlfc_load_stream(const void *h_bytes, size_t nbytes, int device, void *cuda
     ds.ref_tab = reinterpret_cast<const uint32_t *>(base + o_tab);
     ds.tiles = reinterpret_cast<const int16_t *>(base + o_tiles);
     ds.status = reinterpret_cast<uint32_t *>(base + o_status);
+    ds.planes = reinterpret_cast<const int16_t *>(base + o_planes);
     e = cudaMemcpyAsync(base, img.data(), img.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !tile_src.empty())
         e = cudaMemcpyAsync(base + o_src, tile_src.data(), tile_src.size() * 4, cudaMemcpyHostToDevice, st);
@@ -536,6 +586,8 @@ int hmlfc_load_stream(const void *h_bytes, size_t nbytes, int device, void *cuda
     if (e == cudaSuccess)
         e = launch_decode_tiles(ds, reinterpret_cast<const uint32_t *>(base + o_src), (int)s->n_tiles,
                                 reinterpret_cast<int16_t *>(base + o_tiles), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_planes + sz_planes - 256, 0, 256, st);
+    if (e == cudaSuccess) e = launch_build_planes(ds, g.n_ref_nc, reinterpret_cast<int16_t *>(base + o_planes), st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         hmlfc_free_stream(s);
@@ -707,8 +759,8 @@ int hmlfc_render_views_host(const hmlfc_stream *const *streams, int n_streams, c
     return e == cudaSuccess ? HMLFC_OK : cuda_fail(e, "render to host");
 }
 
-// Allocation-free variant of the cached render: the decoded-block cache, its
-// slot map, flags and work list live in the fixed device array set up by
+// Allocation-free variant of the cached render: the flags, camera slots,
+// decode items and camera images live in the fixed device array set up by
 // fixed_scratch() (hmlfc_kernels.cu).  Nothing is allocated, on the device
 // or on the host.
 int hmlfc_render_views_noalloc(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views,
@@ -720,48 +772,40 @@ int hmlfc_render_views_noalloc(const hmlfc_stream *const *streams, int n_streams
     const int dev = streams[0]->device;
     DeviceGuard guard(dev);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    void *scratch = nullptr;
-    cudaError_t e = fixed_scratch(dev, &scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "fixed scratch set-up");
-    uint8_t *base = static_cast<uint8_t *>(scratch);
-    LaunchViews lv;
-    int tiles = 0;
     for (int lf = 0; lf < n_streams; lf++) {
-        const hmlfc_stream *s = streams[lf];
-        const Geometry &g = s->g;
-        const size_t n_keys = (size_t)g.nu * g.nv * g.nblocks;
-        const size_t n_ck = (size_t)g.gu[1] * g.gv[1] * g.nblocks;
-        const size_t blk_bytes = (size_t)g.B * g.B * 4;
-        const size_t o_slot = up256(n_keys), o_items = up256(o_slot + n_keys * 4), o_count = up256(o_items + n_ck * 16),
-                     o_cache = up256(o_count + 8);
-        if (o_cache + blk_bytes > kFixedScratchBytes)
+        const CachedLayout c = cached_layout(streams[lf]);
+        if (c.index_bytes > kFixedScratchBytes)
             return fail(HMLFC_E_UNSUPPORTED,
                         "stream %d needs %zu bytes of block index in the fixed scratch, which holds %zu; "
                         "use hmlfc_render_views",
-                        lf, o_cache + blk_bytes, kFixedScratchBytes);
-        const uint32_t capacity =
-            (uint32_t)std::min<size_t>({(size_t)n_keys, (kFixedScratchBytes - o_cache) / blk_bytes, (size_t)kMaxSlots});
-        uint8_t *flags = base;
-        uint32_t *slotmap = reinterpret_cast<uint32_t *>(base + o_slot);
-        uint4 *items = reinterpret_cast<uint4 *>(base + o_items);
-        unsigned long long *counters = reinterpret_cast<unsigned long long *>(base + o_count);
-        uint32_t *cache = reinterpret_cast<uint32_t *>(base + o_cache);
-        // the array keeps the previous call's contents: clear what must start at zero
-        e = cudaMemsetAsync(flags, 0, n_keys, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 8, st);
-        int pos = 0, k;
-        while (e == cudaSuccess && (k = next_chunk(h_views, n_views, lf, &pos, lv, tiles)) != 0) {
-            if (k < 0) return fail(HMLFC_E_INVALID_ARG, "too many tiles in one launch");
-            e = launch_mark(s->ds, lv, tiles, flags, st);
-        }
-        if (e == cudaSuccess) e = launch_assign(s->ds, flags, slotmap, items, counters, capacity, st);
-        if (e == cudaSuccess) e = launch_decode_blocks(s->ds, items, counters, cache, sm_count(dev) * kDecodeCtasPerSm, st);
-        pos = 0;
-        while (e == cudaSuccess && (k = next_chunk(h_views, n_views, lf, &pos, lv, tiles)) != 0) {
-            if (k < 0) return fail(HMLFC_E_INVALID_ARG, "too many tiles in one launch");
-            e = launch_render_cached(s->ds, lv, tiles, slotmap, cache, d_out, st);
-        }
-        if (e != cudaSuccess) return cuda_fail(e, "allocation-free render");
+                        lf, c.index_bytes, kFixedScratchBytes);
+    }
+    void *scratch = nullptr;
+    cudaError_t e = fixed_scratch(dev, &scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "fixed scratch set-up");
+    for (int lf = 0; lf < n_streams; lf++) {
+        const hmlfc_stream *s = streams[lf];
+        const CachedLayout c = cached_layout(s);
+        const uint32_t capacity = cached_capacity(c, kFixedScratchBytes);
+        // launch chunks built one at a time on the stack: no host allocation either
+        bool too_many = false;
+        auto each_chunk = [&](auto f) {
+            LaunchViews lv;
+            int pos = 0, k = 0, t = 0;
+            cudaError_t r = cudaSuccess;
+            while (r == cudaSuccess && (k = next_chunk(h_views, n_views, lf, &pos, lv, t)) != 0) {
+                if (k < 0) {
+                    too_many = true;
+                    return cudaErrorInvalidValue;
+                }
+                r = f(lv, t);
+            }
+            return r;
+        };
+        rc = cached_launches(s, s->ds, c, static_cast<uint8_t *>(scratch), capacity, each_chunk, d_out, st, nullptr,
+                             false);
+        if (too_many) return fail(HMLFC_E_INVALID_ARG, "too many tiles in one launch");
+        if (rc != HMLFC_OK) return rc;
     }
     return HMLFC_OK;
 }
@@ -927,14 +971,15 @@ int hmlfc_server_render(hmlfc_server *sv, const hmlfc_view *h_views, int n_views
     phase_mark(0, st);
     cudaError_t e = cudaMemsetAsync(sv->flags, 0, (size_t)sv->n_keys, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(sv->counters, 0, 8, st);
-    for (size_t c = 0; c < chunks.size() && e == cudaSuccess; c++) e = launch_mark(s->ds, chunks[c], tiles[c], sv->flags, st);
+    for (size_t c = 0; c < chunks.size() && e == cudaSuccess; c++)
+        e = launch_mark(s->ds, chunks[c], tiles[c], sv->flags, false, st);
     phase_mark(1, st);
     if (e == cudaSuccess)
         e = launch_resident(s->ds, sv->flags, sv->n_keys, sv->slotmap, sv->owner, sv->epoch, sv->clock, sv->capacity, cur,
                             sv->items, sv->counters, sv->cache, sm_count(s->device) * 8, st);
     phase_mark(2, st);
     for (size_t c = 0; c < chunks.size() && e == cudaSuccess; c++)
-        e = launch_render_cached(s->ds, chunks[c], tiles[c], sv->slotmap, sv->cache, d_out, st);
+        e = launch_render_slots(s->ds, chunks[c], tiles[c], sv->slotmap, sv->cache, d_out, st);
     phase_mark(3, st);
     if (e == cudaSuccess) e = launch_accumulate(sv->counters, sv->totals, st);
     return e == cudaSuccess ? HMLFC_OK : cuda_fail(e, "server render");

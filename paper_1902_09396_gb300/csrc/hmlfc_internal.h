@@ -38,6 +38,7 @@ struct DevStream {
     const uint32_t *mvs;            // [n_mv_words + 2]
     const uint32_t *ref_tab;        // [n_ref_nc][nblocks] tile index, 0 = the zero tile
     const int16_t *tiles;           // [n_tiles + 1][B * B]
+    const int16_t *planes;          // [n_ref_nc][H][W] the same reference SRVs as dense planes (+ padding)
     uint32_t *status;               // bit 0: an out-of-range coordinate was seen
     int lod;                        // progressive decode: levels below lod are left out (0 = full decode)
 };
@@ -65,17 +66,28 @@ cudaError_t fixed_scratch(int device, void **ptr);
 // Launchers implemented in hmlfc_kernels.cu.
 cudaError_t launch_decode_tiles(const DevStream &ds, const uint32_t *d_src, int n_tiles, int16_t *d_tiles,
                                 cudaStream_t st);
+cudaError_t launch_build_planes(const DevStream &ds, int64_t n_ref, int16_t *d_planes, cudaStream_t st);
 cudaError_t launch_decode_pixels(const DevStream &ds, const int32_t *d_coords, int64_t n, uint8_t *d_rgb,
                                  cudaStream_t st);
 cudaError_t launch_render(const DevStream &ds, const LaunchViews &lv, int total_tiles, float *d_out, int mode,
                           cudaStream_t st);
-cudaError_t launch_mark(const DevStream &ds, const LaunchViews &lv, int total_tiles, uint8_t *flags, cudaStream_t st);
-cudaError_t launch_assign(const DevStream &ds, const uint8_t *flags, uint32_t *slotmap, uint4 *items,
+// Flags of the (camera, block) pairs the views reach: super_layout groups the
+// cameras of each (level-min(2, L) node, block) pair (the cached render),
+// otherwise camera-major (the serving form's keys).
+cudaError_t launch_mark(const DevStream &ds, const LaunchViews &lv, int total_tiles, uint8_t *flags, bool super_layout,
+                        cudaStream_t st);
+// Camera slots (counters[1]) and decode items (counters[0] >> 32).
+cudaError_t launch_assign(const DevStream &ds, const uint8_t *flags, uint32_t *camslot, uint4 *items,
                           unsigned long long *counters, uint32_t capacity, cudaStream_t st);
 cudaError_t launch_decode_blocks(const DevStream &ds, const uint4 *items, const unsigned long long *counters,
-                                 uint32_t *cache, int grid, cudaStream_t st);
-cudaError_t launch_render_cached(const DevStream &ds, const LaunchViews &lv, int total_tiles, const uint32_t *slotmap,
-                                 const uint32_t *cache, float *d_out, cudaStream_t st);
+                                 const uint32_t *camslot, uint32_t *cache, int grid, cudaStream_t st);
+// all_cameras: the cache holds an image for every camera of the light field,
+// so no ray needs the direct-decode fallback.
+cudaError_t launch_render_cached(const DevStream &ds, const LaunchViews &lv, int total_tiles, const uint32_t *camslot,
+                                 const uint32_t *cache, bool all_cameras, float *d_out, cudaStream_t st);
+// Blend from a cache with one B x B slot per (camera, block) pair (slotmap).
+cudaError_t launch_render_slots(const DevStream &ds, const LaunchViews &lv, int total_tiles, const uint32_t *slotmap,
+                                const uint32_t *cache, float *d_out, cudaStream_t st);
 // Serving form: resident decoded-block cache (hits, misses with eviction, decode).
 cudaError_t launch_resident(const DevStream &ds, const uint8_t *flags, int64_t n_keys, uint32_t *slotmap,
                             uint32_t *owner, uint32_t *epoch, uint32_t *clock, uint32_t capacity, uint32_t cur,

@@ -259,6 +259,25 @@ __global__ void k_decode_tiles(const DevStream S, const uint4 *__restrict__ src,
     }
 }
 
+// Dense copy of the resident reference SRVs for the block decode: plane r
+// (reference node-channel rank r, [H][W] int16) holds every block's tile, the
+// zero tile where the block is insignificant.  One CTA per (block, plane).
+__global__ void __launch_bounds__(256) k_build_planes(const DevStream S, int n_ref, int16_t *__restrict__ planes) {
+    const int k = blockIdx.x;
+    const int B = S.B;
+    const int bx = k % S.nbx, by = k / S.nbx;
+    const int bw = min(B, S.W - bx * B), bh = min(B, S.H - by * B);
+    for (int r = blockIdx.y; r < n_ref; r += gridDim.y) {
+        const uint32_t tile = __ldg(S.ref_tab + (size_t)r * S.nblocks + k);
+        const int16_t *src = S.tiles + (size_t)tile * B * B;
+        int16_t *dst = planes + (size_t)r * S.W * S.H + (size_t)by * B * S.W + (size_t)bx * B;
+        for (int e = threadIdx.x; e < bw * bh; e += blockDim.x) {
+            const int yy = e / bw, xx = e - yy * bw;
+            dst[(size_t)yy * S.W + xx] = src[yy * B + xx];
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // K2: random-access decoding of a list of samples
 // ---------------------------------------------------------------------------
@@ -920,12 +939,15 @@ __global__ void __launch_bounds__(256) k_dequant(const __grid_constant__ DevStre
 //
 // mark:   each 16 x 16 ray tile flags the (camera, block) pairs of its
 //         footprint's bounding box (idempotent byte stores);
-// assign: flagged keys get consecutive slots of the call's decoded-block
-//         cache (keys past the capacity keep kNone and are decoded per ray);
-// decode: a persistent kernel decodes each slot's block -- root + every level
-//         of the tree path with motion re-compensation -- to RGB8, with the
-//         block's per-(level, channel) descriptors staged once;
-// render: each ray gathers its 16 RGB8 samples from the cache and blends.
+// assign: every camera with a flagged block gets a slot of the call's cache
+//         (a whole W x H RGB8 image; cameras past the capacity keep kNone and
+//         their rays decode directly), and every (level-2 node, block) with
+//         a flagged camera becomes a decode item;
+// decode: a persistent kernel decodes each item's flagged blocks -- root +
+//         every level of the tree path with motion re-compensation, the
+//         levels the item's cameras share evaluated once -- to RGB8 in the
+//         camera images;
+// render: each ray gathers its 16 RGB8 samples from the images and blends.
 
 // Descriptor of block (bx, by) of node (a, b) at level l, channel c.
 template <int BS>
@@ -967,20 +989,35 @@ __device__ Desc make_desc(const DevStream &S, const LevelTabs &T, const Blk<BS> 
     return D;
 }
 
-// Mark the (camera, block) pairs of one tile's footprint.  Under a
-// projective map with w > 0 over the tile, each coordinate's extremes over
-// the tile's pixel centres are at its corner pixels, so the 4 corner rays
-// bound the footprint; the box is widened by a small margin against fp32
-// rounding of interior rays (a pair missed all the same only sends its rays
-// to the direct decode).  A tile whose w is not positive at all corners is
-// marked ray by ray.
-template <int BS, int TW, int TH>
-__global__ void __launch_bounds__(128) k_mark(const __grid_constant__ DevStream S,
+// Index of the flag of (camera (i, j), block k).  kSuper: grouped by super
+// key -- the (2^K)^2 cameras of a (level-K node, block) pair, K = min(2, L),
+// are consecutive bytes (a zero-padded group at the grid's edge); otherwise
+// camera-major, i * nv * nblocks + j * nblocks + k.
+template <bool kSuper>
+__device__ __forceinline__ size_t flag_index(const DevStream &S, int i, int j, int k) {
+    if (!kSuper) return ((size_t)i * S.nv + j) * S.nblocks + k;
+    const int K = S.L < 2 ? S.L : 2, cpa = 1 << K;
+    const size_t node = (size_t)(i >> K) * S.gv[K] + (j >> K);
+    return ((node * S.nblocks + k) << (2 * K)) + (size_t)(((i & (cpa - 1)) << K) | (j & (cpa - 1)));
+}
+
+// Mark the (camera, block) pairs of one tile's footprint; one warp per tile.
+// Under a projective map with w > 0 over the tile, each coordinate's extremes
+// over the tile's pixel centres are at its corner pixels, so the 4 corner
+// rays bound the footprint; the box is widened by a small margin against
+// fp32 rounding of interior rays (a pair missed all the same only sends its
+// rays to the direct decode).  A tile whose w is not positive at all corners
+// is marked ray by ray.  The lanes share the box's (camera, block) pairs.
+template <int BS, int TW, int TH, bool kSuper>
+__global__ void __launch_bounds__(256) k_mark(const __grid_constant__ DevStream S,
                                              const __grid_constant__ LaunchViews LV, int total_tiles,
                                              uint8_t *__restrict__ flags) {
-    const int tile = blockIdx.x * blockDim.x + threadIdx.x;
-    if (tile >= total_tiles) return;
-    const int vi = find_view(LV, tile);
+    const int lane = threadIdx.x & 31;
+    const int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (tile >= total_tiles) return;                       // uniform over the warp
+    int vi = 0;
+    if (lane == 0) vi = find_view(LV, tile);
+    vi = __shfl_sync(0xFFFFFFFFu, vi, 0);
     const hmlfc_view &V = LV.views[vi];
     const int tiles_x = (V.width + TW - 1) / TW;
     const int local = tile - LV.tile_start[vi];
@@ -988,21 +1025,38 @@ __global__ void __launch_bounds__(128) k_mark(const __grid_constant__ DevStream 
     const int x1 = min(x0 + TW, V.width) - 1, y1 = min(y0 + TH, V.height) - 1;
     const Blk<BS> bk(S.B);
     const float eps_uv = 1e-3f, eps_st = 1e-2f;
-    float lo[4] = {1e30f, 1e30f, 1e30f, 1e30f}, hi[4] = {-1e30f, -1e30f, -1e30f, -1e30f};
-    bool ok = true;
+    // every group of 4 lanes evaluates the 4 corner rays, then a butterfly gives all lanes the extremes
+    const int q = lane & 3;
+    const float X = (float)((q & 1) ? x1 : x0) + 0.5f, Y = (float)((q & 2) ? y1 : y0) + 0.5f;
+    const float *h = V.H_uv, *g = V.H_st;
+    const float wu = h[6] * X + h[7] * Y + h[8], ws = g[6] * X + g[7] * Y + g[8];
+    float lo[4] = {__fdividef(h[0] * X + h[1] * Y + h[2], wu), __fdividef(h[3] * X + h[4] * Y + h[5], wu),
+                   __fdividef(g[0] * X + g[1] * Y + g[2], ws), __fdividef(g[3] * X + g[4] * Y + g[5], ws)};
+    float hi[4] = {lo[0], lo[1], lo[2], lo[3]};
+    bool ok = wu > 0.f && ws > 0.f;
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-        const float X = (float)((q & 1) ? x1 : x0) + 0.5f, Y = (float)((q & 2) ? y1 : y0) + 0.5f;
-        const float *h = V.H_uv, *g = V.H_st;
-        const float wu = h[6] * X + h[7] * Y + h[8], ws = g[6] * X + g[7] * Y + g[8];
-        ok &= wu > 0.f && ws > 0.f;
-        const float c[4] = {__fdividef(h[0] * X + h[1] * Y + h[2], wu), __fdividef(h[3] * X + h[4] * Y + h[5], wu),
-                            __fdividef(g[0] * X + g[1] * Y + g[2], ws), __fdividef(g[3] * X + g[4] * Y + g[5], ws)};
+    for (int k = 0; k < 4; k++) ok = ok && lo[k] == lo[k];   // NaN
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1)
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            lo[k] = fminf(lo[k], c[k]);
-            hi[k] = fmaxf(hi[k], c[k]);
+            lo[k] = fminf(lo[k], __shfl_xor_sync(0xFFFFFFFFu, lo[k], o));
+            hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xFFFFFFFFu, hi[k], o));
         }
+    ok = __all_sync(0xFFFFFFFFu, ok);
+    if (!ok) {                                             // ray by ray
+        const int tw = x1 - x0 + 1, n = tw * (y1 - y0 + 1);
+        for (int e = lane; e < n; e += 32) {
+            const int py = y0 + e / tw, px = x0 + e % tw;
+            Ray r;
+            ray_setup(V, S.nu, S.nv, S.W, S.H, px, py, r);
+            const int ci[2] = {(r.i0 >> S.lod) << S.lod, (r.i1 >> S.lod) << S.lod};
+            const int cj[2] = {(r.j0 >> S.lod) << S.lod, (r.j1 >> S.lod) << S.lod};
+            const int kb[4] = {bk.div(r.y0) * S.nbx + bk.div(r.x0), bk.div(r.y0) * S.nbx + bk.div(r.x1),
+                               bk.div(r.y1) * S.nbx + bk.div(r.x0), bk.div(r.y1) * S.nbx + bk.div(r.x1)};
+            for (int k = 0; k < 16; k++) flags[flag_index<kSuper>(S, ci[k >> 3], cj[(k >> 2) & 1], kb[k & 3])] = 1;
+        }
+        return;
     }
     const int n[4] = {S.nu, S.nv, S.W, S.H};
     int bl[4], bh[4];
@@ -1014,123 +1068,309 @@ __global__ void __launch_bounds__(128) k_mark(const __grid_constant__ DevStream 
         axis_nb(hi[k] + e, n[k], b0, b1);
         bl[k] = a0;
         bh[k] = b1;
-        if (!(lo[k] == lo[k]) || !(hi[k] == hi[k])) ok = false;   // NaN
     }
-    if (!ok) {                              // ray by ray
-        for (int py = y0; py <= y1; py++)
-            for (int px = x0; px <= x1; px++) {
-                Ray r;
-                ray_setup(V, S.nu, S.nv, S.W, S.H, px, py, r);
-                const int ci[2] = {(r.i0 >> S.lod) << S.lod, (r.i1 >> S.lod) << S.lod};
-                const int cj[2] = {(r.j0 >> S.lod) << S.lod, (r.j1 >> S.lod) << S.lod};
-                const int kb[4] = {bk.div(r.y0) * S.nbx + bk.div(r.x0), bk.div(r.y0) * S.nbx + bk.div(r.x1),
-                                   bk.div(r.y1) * S.nbx + bk.div(r.x0), bk.div(r.y1) * S.nbx + bk.div(r.x1)};
-                for (int q = 0; q < 16; q++)
-                    flags[((size_t)ci[q >> 3] * S.nv + cj[(q >> 2) & 1]) * S.nblocks + kb[q & 3]] = 1;
-            }
-        return;
+    const int bx0 = bk.div(bl[2]), by0 = bk.div(bl[3]);
+    const int nbx = bk.div(bh[2]) - bx0 + 1, nby = bk.div(bh[3]) - by0 + 1;
+    const int sh = S.lod;                                  // progressive decode: one representative camera per node
+    const int i0 = (bl[0] >> sh) << sh, j0 = (bl[1] >> sh) << sh;
+    const int ni = ((bh[0] - i0) >> sh) + 1, nj = ((bh[1] - j0) >> sh) + 1;
+    // lanes over the box's (camera, block row) pairs; each stores its row's blocks, whose flags lie a fixed
+    // stride apart (one block further in either layout)
+    const int n_rows = ni * nj * nby;
+    const size_t stride = kSuper ? (size_t)1 << (2 * (S.L < 2 ? S.L : 2)) : 1;
+    for (int e = lane; e < n_rows; e += 32) {
+        const int cam = e / nby, by = by0 + (e - cam * nby);
+        const int ci = cam / nj;
+        const int i = i0 + (ci << sh), j = j0 + ((cam - ci * nj) << sh);
+        uint8_t *f = flags + flag_index<kSuper>(S, i, j, by * S.nbx + bx0);
+        for (int bx = 0; bx < nbx; bx++) f[bx * stride] = 1;
     }
-    const int bx0 = bk.div(bl[2]), bx1 = bk.div(bh[2]), by0 = bk.div(bl[3]), by1 = bk.div(bh[3]);
-    const int step = 1 << S.lod;            // progressive decode: one representative camera per level-lod node
-    for (int i = (bl[0] >> S.lod) << S.lod; i <= bh[0]; i += step)
-        for (int j = (bl[1] >> S.lod) << S.lod; j <= bh[1]; j += step) {
-            uint8_t *f = flags + ((size_t)i * S.nv + j) * S.nblocks;
-            for (int by = by0; by <= by1; by++)
-                for (int bx = bx0; bx <= bx1; bx++) f[by * S.nbx + bx] = 1;
-        }
 }
 
-// Compact the flags into cache slots, super-item by super-item: a super key
-// is a (level-K node, block) pair, K = min(2, L); its up to (2^K)^2 cameras
-// get consecutive slots in camera order, and every super key with a flagged
-// camera becomes one decode item {super key, camera mask, first slot, 0}.
-// Keys beyond the capacity get no slot (kNone): their rays decode directly.
+// Per-camera decoded images: a call gives every camera its views reach (a
+// camera with a flagged block) one slot of W x H RGB8 pixels (u32 each) in its
+// scratch, in the order the cameras are found; cameras beyond the capacity
+// keep kNone and their rays decode directly.  Only the flagged blocks of a
+// slot are written.
+//
+// Decode items: a super key is a (level-K node, block) pair, K = min(2, L);
+// every super key with a flagged camera among its (2^K)^2 cameras becomes one
+// item {super key, camera mask, 0, 0}.  One launch does both: the first
+// blocks of the grid the items, the rest the camera slots.
 __global__ void __launch_bounds__(256) k_assign(const __grid_constant__ DevStream S, const uint8_t *__restrict__ flags,
-                                                uint32_t *__restrict__ slotmap, uint4 *__restrict__ items,
-                                                unsigned long long *__restrict__ counters, uint32_t capacity) {
-    __shared__ uint32_t s_warp[8][2];
-    __shared__ uint32_t s_base[2];
-    const int K = S.L < 2 ? S.L : 2, cpa = 1 << K;
+                                                uint32_t *__restrict__ camslot, uint4 *__restrict__ items,
+                                                unsigned long long *__restrict__ counters, uint32_t capacity,
+                                                int item_blocks) {
+    const int K = S.L < 2 ? S.L : 2, cpa = 1 << K, ncg = cpa * cpa;
+    if ((int)blockIdx.x >= item_blocks) {           // camera slots: one warp per camera
+        const int cam = ((int)blockIdx.x - item_blocks) * 8 + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
+        if (cam >= S.nu * S.nv) return;
+        const int i = cam / S.nv, j = cam - (cam / S.nv) * S.nv;
+        const uint8_t *f = flags + flag_index<true>(S, i, j, 0);   // block k of this camera at f[k * ncg]
+        uint32_t any = 0;
+        for (int k = lane; k < S.nblocks; k += 32) any |= __ldg(f + (size_t)k * ncg);
+        any = __any_sync(0xFFFFFFFFu, any != 0);
+        if (lane == 0) {
+            uint32_t slot = kNone;
+            if (any) {
+                const uint32_t s = (uint32_t)atomicAdd(counters + 1, 1ull);
+                if (s < capacity) slot = s;
+            }
+            camslot[cam] = slot;
+        }
+        return;
+    }
+    __shared__ uint32_t s_warp[8];
+    __shared__ uint32_t s_base;
     const int64_t n_sk = (int64_t)S.gu[K] * S.gv[K] * S.nblocks;
     const int64_t sk = (int64_t)blockIdx.x * 256 + threadIdx.x;
     uint32_t mask = 0;
-    int node = 0, k = 0;
     if (sk < n_sk) {
-        node = (int)(sk / S.nblocks);
-        k = (int)(sk - (int64_t)node * S.nblocks);
-        const int aK = node / S.gv[K], bK = node - (node / S.gv[K]) * S.gv[K];
-        for (int q = 0; q < cpa * cpa; q++) {
-            const int i = aK * cpa + q / cpa, j = bK * cpa + q % cpa;
-            if (i < S.nu && j < S.nv && flags[((int64_t)i * S.nv + j) * S.nblocks + k]) mask |= 1u << q;
+        const uint8_t *f = flags + ((size_t)sk << (2 * K));       // the super key's camera flags, consecutive
+        if (K == 2) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(f));
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int q = 0; q < 16; q++) mask |= ((w[q >> 2] >> (8 * (q & 3))) & 0xFFu) ? 1u << q : 0u;
+        } else {
+            for (int q = 0; q < ncg; q++) mask |= f[q] ? 1u << q : 0u;
         }
     }
-    const uint32_t nslot = __popc(mask), nitem = mask ? 1u : 0u;
+    const uint32_t nitem = mask ? 1u : 0u;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t is = nslot, ii = nitem;
+    uint32_t ii = nitem;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t vs = __shfl_up_sync(0xFFFFFFFFu, is, o), vi = __shfl_up_sync(0xFFFFFFFFu, ii, o);
-        if (lane >= o) {
-            is += vs;
-            ii += vi;
-        }
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, ii, o);
+        if (lane >= o) ii += v;
     }
-    if (lane == 31) {
-        s_warp[warp][0] = is;
-        s_warp[warp][1] = ii;
-    }
+    if (lane == 31) s_warp[warp] = ii;
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint32_t as = 0, ai = 0;
+        uint32_t a = 0;
         for (int w = 0; w < 8; w++) {
-            const uint32_t vs = s_warp[w][0], vi = s_warp[w][1];
-            s_warp[w][0] = as;
-            s_warp[w][1] = ai;
-            as += vs;
-            ai += vi;
+            const uint32_t v = s_warp[w];
+            s_warp[w] = a;
+            a += v;
         }
-        const unsigned long long old = atomicAdd(counters, ((unsigned long long)ai << 32) | as);
-        s_base[0] = (uint32_t)(old & 0xFFFFFFFFull);
-        s_base[1] = (uint32_t)(old >> 32);
+        s_base = (uint32_t)(atomicAdd(counters, (unsigned long long)a << 32) >> 32);
     }
     __syncthreads();
-    if (sk >= n_sk) return;
-    const uint32_t slot0 = s_base[0] + s_warp[warp][0] + is - nslot;
-    const uint32_t item = s_base[1] + s_warp[warp][1] + ii - nitem;
-    const bool fits = slot0 + nslot <= capacity;
-    const int aK = node / S.gv[K], bK = node - (node / S.gv[K]) * S.gv[K];
-    uint32_t slot = slot0;
-    for (int q = 0; q < cpa * cpa; q++) {
-        const int i = aK * cpa + q / cpa, j = bK * cpa + q % cpa;
-        if (i >= S.nu || j >= S.nv) continue;
-        const int64_t key = ((int64_t)i * S.nv + j) * S.nblocks + k;
-        if ((mask >> q) & 1u) {
-            slotmap[key] = fits ? slot : kNone;
-            slot++;
-        } else {
-            slotmap[key] = kNone;
-        }
-    }
-    if (mask) items[item] = make_uint4((uint32_t)sk, fits ? mask : 0u, slot0, 0u);
+    if (mask) items[s_base + s_warp[warp] + ii - nitem] = make_uint4((uint32_t)sk, mask, 0u, 0u);
 }
 
-// Decode the cached blocks, one super item ((level-K node, block), K =
-// min(2, L)) at a time: per pixel, the node's reconstruction (root + SRV
-// levels L-1 .. K) is evaluated once, level 1 once per active child node
-// (K = 2), and level 0 once per marked camera.  Persistent CTAs; several
-// items per pass so that one descriptor phase serves more pixel work.
+// Descriptor of one (level, node, channel) of a decode item, for the block
+// decode (32 B, shared memory).  The resident reference SRVs are read as
+// dense planes: `base` points at the value under the block's first pixel --
+// the node's own plane for a reference node, the reference's plane shifted
+// by the integer part of the motion vector for a predictive one -- so every
+// tap of every pixel is base + (pixel offset in the block) + a constant.
+// Blocks whose taps would leave the image take the clamped path instead,
+// with base at the plane origin and the tap origin in (ox, oy).
+constexpr uint32_t kDRef = 1u, kDNeg = 2u, kDClamp = 4u, kDInt = 8u, kDNoMC = 16u;
+
+struct NDesc {
+    const int16_t *base;
+    uint32_t rec;          // residual record word, kNone when insignificant (r^ = 0)
+    uint32_t hdr;          // record header (min level, BISE mode and bits)
+    uint32_t w;            // bilinear weights w00 | w10 << 8 | w01 << 16 | w11 << 24 (sum 16)
+    uint32_t flags;        // kD*
+    int32_t ox, oy;        // clamped path: block origin + integer part of the motion vector
+};
+static_assert(sizeof(NDesc) == 32, "descriptor size");
+
+template <int BS>
+__device__ NDesc make_ndesc(const DevStream &S, const LevelTabs &T, const Blk<BS> &bk, int l, int a, int b, int c,
+                            int bx, int by) {
+    const int B = bk.size();
+    const int k = by * S.nbx + bx;
+    const int x0 = bx * B, y0 = by * B;
+    const size_t plane = (size_t)S.W * S.H;
+    NDesc D;
+    D.rec = kNone;
+    D.hdr = 0u;
+    D.w = 16u;
+    D.ox = x0;
+    D.oy = y0;
+    if (is_ref(a, b)) {
+        D.base = S.planes + (size_t)ref_rank(T, l, a, b, c) * plane + (size_t)y0 * S.W + x0;
+        D.flags = kDRef;
+        return D;
+    }
+    const int nc = nc_index(T, l, a, b, c);
+    const uint4 g = __ldg(S.groups + (size_t)nc * S.ngroups + (k >> 5));
+    const uint32_t bit = (uint32_t)k & 31u;
+    if ((g.x >> bit) & 1u) {
+        D.rec = g.y + __ldg(S.offs + g.z + __popc(g.x & ((1u << bit) - 1u)));
+        D.hdr = __ldg(S.recs + D.rec);
+    }
+    D.base = S.planes;
+    if (!S.mc) {
+        D.flags = kDNoMC;
+        return D;
+    }
+    const uint32_t sym = bise_get_long(S.mvs, S.mv_mode, S.mv_b, (uint64_t)pred_rank(T, l, a, b, c) * S.nblocks + k);
+    int mvx, mvy, sign;
+    decode_mv(S, sym, mvx, mvy, sign);
+    const int fx = mvx & 3, fy = mvy & 3;     // X = 4x + mvx: floor(X / 4) = x + (mvx >> 2), X & 3 = mvx & 3
+    D.w = (uint32_t)((4 - fx) * (4 - fy)) | ((uint32_t)(fx * (4 - fy)) << 8) | ((uint32_t)((4 - fx) * fy) << 16) |
+          ((uint32_t)(fx * fy) << 24);
+    D.ox = x0 + (mvx >> 2);
+    D.oy = y0 + (mvy >> 2);
+    const int16_t *rp = S.planes + (size_t)ref_rank(T, l, a & ~1, b & ~1, c) * plane;
+    D.flags = sign < 0 ? kDNeg : 0u;
+    // unclamped: every tap (x .. x + 2 of a pixel pair, y .. y + 1) of every pixel of the block lies in the image
+    if (D.ox >= 0 && D.oy >= 0 && D.ox + B + 1 <= S.W - 1 && D.oy + B <= S.H - 1) {
+        D.base = rp + (size_t)D.oy * S.W + D.ox;
+        if (fx == 0 && fy == 0) D.flags |= kDInt;
+    } else {
+        D.base = rp;
+        D.flags |= kDClamp;
+    }
+    return D;
+}
+
+// Values idx0 and idx1 of a block's BISE payload (Sec. 4.6).  The mode is
+// the same for every lane of a warp (one block per warp), so the power-of-two
+// alphabet reads both values from one three-word window.
+__device__ __forceinline__ void bise_pair(const uint32_t *__restrict__ w, uint32_t mode, uint32_t b, uint32_t idx0,
+                                          uint32_t idx1, uint32_t &v0, uint32_t &v1) {
+    if (mode == 0) {
+        const uint32_t pos0 = idx0 * b, pos1 = idx1 * b, k = pos0 >> 5;
+        const uint32_t lo = __ldg(w + k), mid = __ldg(w + k + 1), hi = __ldg(w + k + 2);
+        const uint32_t mask = (1u << b) - 1u;
+        v0 = __funnelshift_r(lo, mid, pos0 & 31u) & mask;
+        const bool nxt = (pos1 >> 5) != k;
+        v1 = __funnelshift_r(nxt ? mid : lo, nxt ? hi : mid, pos1 & 31u) & mask;
+    } else {
+        v0 = bise_get_small(w, mode, b, idx0);
+        v1 = bise_get_small(w, mode, b, idx1);
+    }
+}
+
+// SRV of one node-channel at a horizontally adjacent pixel pair of a block
+// (Sec. 4.4, Sec. 4.8.1): p = in-block offset y * W + x of the first pixel,
+// (xi, yi) its in-block position, idx0 / idx1 the payload indices of the
+// two pixels.  A reference node gives its resident R^; a predictive node
+// sign * P + r^, P the quarter-pel bilinear of the reference's R^ with
+// weights summing to 16, + 8, >> 4.
+template <int BS>
+__device__ __forceinline__ void eval_pair(const DevStream &S, const NDesc &D, int p, int xi, int yi, uint32_t idx0,
+                                          uint32_t idx1, int &o0, int &o1) {
+    const uint32_t f = D.flags;
+    if (f & kDRef) {
+        o0 = __ldg(D.base + p);
+        o1 = __ldg(D.base + p + 1);
+        return;
+    }
+    int r0 = 0, r1 = 0;
+    if (D.rec != kNone) {
+        const int m = (int)(int16_t)(D.hdr & 0xFFFFu);
+        uint32_t v0, v1;
+        bise_pair(S.recs + D.rec + 1, (D.hdr >> 21) & 3u, (D.hdr >> 16) & 31u, idx0, idx1, v0, v1);
+        r0 = S.q * (m + (int)v0);
+        r1 = S.q * (m + (int)v1);
+    }
+    if (f & kDNoMC) {
+        o0 = r0;
+        o1 = r1;
+        return;
+    }
+    int p0, p1;
+    if (f & kDInt) {
+        p0 = __ldg(D.base + p);
+        p1 = __ldg(D.base + p + 1);
+    } else {
+        int a0, a1, a2, b0, b1, b2;
+        if (!(f & kDClamp)) {
+            const int16_t *t = D.base + p;
+            a0 = __ldg(t);
+            a1 = __ldg(t + 1);
+            a2 = __ldg(t + 2);
+            t += S.W;
+            b0 = __ldg(t);
+            b1 = __ldg(t + 1);
+            b2 = __ldg(t + 2);
+        } else {
+            const int X = D.ox + xi, Y = D.oy + yi;
+            const int c0 = clampi(X, 0, S.W - 1), c1 = clampi(X + 1, 0, S.W - 1), c2 = clampi(X + 2, 0, S.W - 1);
+            const int16_t *ra = D.base + (size_t)clampi(Y, 0, S.H - 1) * S.W;
+            const int16_t *rb = D.base + (size_t)clampi(Y + 1, 0, S.H - 1) * S.W;
+            a0 = __ldg(ra + c0);
+            a1 = __ldg(ra + c1);
+            a2 = __ldg(ra + c2);
+            b0 = __ldg(rb + c0);
+            b1 = __ldg(rb + c1);
+            b2 = __ldg(rb + c2);
+        }
+        const int w00 = (int)(D.w & 0xFFu), w10 = (int)((D.w >> 8) & 0xFFu), w01 = (int)((D.w >> 16) & 0xFFu),
+                  w11 = (int)(D.w >> 24);
+        p0 = (w00 * a0 + w10 * a1 + w01 * b0 + w11 * b1 + 8) >> 4;
+        p1 = (w00 * a1 + w10 * a2 + w01 * b1 + w11 * b2 + 8) >> 4;
+    }
+    o0 = (f & kDNeg) ? r0 - p0 : r0 + p0;
+    o1 = (f & kDNeg) ? r1 - p1 : r1 + p1;
+}
+
+// Entry e of a decode item's descriptor list ((level-K node, block) pair,
+// K = min(2, L), camera mask it.y): the shared levels L-1 .. K first, then
+// level 1 of the 4 child nodes (K = 2), then level 0 of the (2^K)^2 cameras,
+// channels innermost.  Returns false for the entry of a child node or camera
+// that the item does not decode.
+template <int BS>
+__device__ __forceinline__ bool item_desc(const DevStream &S, const LevelTabs &T, const Blk<BS> &bk, const uint4 &it,
+                                          int e, NDesc &D) {
+    const int L = S.L, K = L < 2 ? L : 2, cpa = 1 << K;
+    const int n_sh = (L - K) * 3, n_mid = K == 2 ? 12 : 0;
+    const int node = (int)(it.x / (uint32_t)S.nblocks), k = (int)(it.x - (uint32_t)node * S.nblocks);
+    const int aK = node / T.gv[K], bK = node - (node / T.gv[K]) * T.gv[K];
+    int l, a, b, c;
+    if (e < n_sh) {
+        l = K + e / 3;
+        c = e - 3 * (l - K);
+        a = aK >> (l - K);
+        b = bK >> (l - K);
+    } else if (e < n_sh + n_mid) {
+        const int m = (e - n_sh) / 3;                           // child node m of level 1
+        c = (e - n_sh) - 3 * m;
+        l = 1;
+        a = 2 * aK + (m >> 1);
+        b = 2 * bK + (m & 1);
+        const uint32_t under = 0x33u << (8 * (m >> 1) + 2 * (m & 1));   // its 2x2 cameras in the 4x4 mask
+        if (!(it.y & under)) return false;
+    } else {
+        const int q = (e - n_sh - n_mid) / 3;
+        c = (e - n_sh - n_mid) - 3 * q;
+        l = 0;
+        a = aK * cpa + q / cpa;
+        b = bK * cpa + q % cpa;
+        if (!((it.y >> q) & 1u)) return false;
+    }
+    D = make_ndesc(S, T, bk, l, a, b, c, k % S.nbx, k / S.nbx);
+    return true;
+}
+
+// Decode the flagged blocks into the camera images, one item ((level-K node,
+// block), K = min(2, L)) at a time: per pixel, the node's reconstruction
+// (root + SRV levels L-1 .. K) is evaluated once, level 1 once per active
+// child node (K = 2), and level 0 once per flagged camera with a slot.
+// Persistent CTAs; several items per pass so that one descriptor phase
+// serves more pixel work.  Each thread decodes two horizontally adjacent
+// pixels, which share the descriptor reads and four of their six taps.
 template <int BS>
 __global__ void __launch_bounds__(256, 4) k_decode_blocks(const __grid_constant__ DevStream S,
                                                       const uint4 *__restrict__ items,
                                                       const unsigned long long *__restrict__ counters,
+                                                      const uint32_t *__restrict__ camslot,
                                                       uint32_t *__restrict__ cache) {
     constexpr int kGroup = 2;                                   // items per pass
     constexpr int kDescPer = (kMaxLevels - 2) * 3 + 4 * 3 + 16 * 3;
     __shared__ LevelTabs T;
-    __shared__ Desc s_desc[kGroup * kDescPer];
+    __shared__ __align__(16) NDesc s_desc[kGroup * kDescPer];
+    __shared__ uint32_t s_slot[kGroup][16];
     load_tabs(S, T);
     const Blk<BS> bk(S.B);
-    const int B = bk.size(), B2 = B * B;
+    const int B = bk.size();
     const int L = S.L, K = L < 2 ? L : 2, cpa = 1 << K;
     const int n_sh = (L - K) * 3;                               // shared levels L-1 .. K
     const int n_mid = K == 2 ? 12 : 0;                          // level 1 of the 4 child nodes
@@ -1139,36 +1379,20 @@ __global__ void __launch_bounds__(256, 4) k_decode_blocks(const __grid_constant_
     const size_t plane = (size_t)S.W * S.H;
     __syncthreads();
     for (uint32_t first = blockIdx.x * kGroup; first < n; first += gridDim.x * kGroup) {
-        for (int d = threadIdx.x; d < kGroup * nd; d += blockDim.x) {
-            const int gi = d / nd, e = d - gi * nd;
+        for (int d = threadIdx.x; d < kGroup * (nd + 16); d += blockDim.x) {
+            const int gi = d / (nd + 16), e = d - gi * (nd + 16);
             if (first + gi >= n) continue;
             const uint4 it = __ldg(items + first + gi);
-            if (!it.y) continue;
-            const int node = (int)(it.x / (uint32_t)S.nblocks), k = (int)(it.x - (uint32_t)node * S.nblocks);
-            const int aK = node / T.gv[K], bK = node - (node / T.gv[K]) * T.gv[K];
-            int l, a, b, c;
-            if (e < n_sh) {
-                l = K + e / 3;
-                c = e - 3 * (l - K);
-                a = aK >> (l - K);
-                b = bK >> (l - K);
-            } else if (e < n_sh + n_mid) {
-                const int m = (e - n_sh) / 3;                   // child node m of level 1
-                c = (e - n_sh) - 3 * m;
-                l = 1;
-                a = 2 * aK + (m >> 1);
-                b = 2 * bK + (m & 1);
-                const uint32_t under = 0x33u << (8 * (m >> 1) + 2 * (m & 1));   // its 2x2 cameras in the 4x4 mask
-                if (!(it.y & under)) continue;
-            } else {
-                const int q = (e - n_sh - n_mid) / 3;
-                c = (e - n_sh - n_mid) - 3 * q;
-                l = 0;
-                a = aK * cpa + q / cpa;
-                b = bK * cpa + q % cpa;
-                if (!((it.y >> q) & 1u)) continue;
+            if (e >= nd) {                                      // slots of the item's cameras
+                const int q = e - nd;
+                const int node = (int)(it.x / (uint32_t)S.nblocks);
+                const int aK = node / T.gv[K], bK = node - (node / T.gv[K]) * T.gv[K];
+                const int i = aK * cpa + q / cpa, j = bK * cpa + q % cpa;
+                s_slot[gi][q] = (q < cpa * cpa && ((it.y >> q) & 1u)) ? __ldg(camslot + i * S.nv + j) : kNone;
+                continue;
             }
-            s_desc[d] = make_desc(S, T, bk, l, a, b, c, k % S.nbx, k / S.nbx);
+            NDesc D;
+            if (item_desc(S, T, bk, it, e, D)) s_desc[gi * kDescPer + e] = D;
         }
         __syncthreads();
         // two horizontally adjacent pixels per thread: (xx, yy) and (xx + 1, yy)
@@ -1177,49 +1401,41 @@ __global__ void __launch_bounds__(256, 4) k_decode_blocks(const __grid_constant_
             const int gi = e / npair, pp = e - gi * npair;
             if (first + gi >= n) continue;
             const uint4 it = __ldg(items + first + gi);
-            if (!it.y) continue;
             const int node = (int)(it.x / (uint32_t)S.nblocks), k = (int)(it.x - (uint32_t)node * S.nblocks);
             const int aK = node / T.gv[K], bK = node - (node / T.gv[K]) * T.gv[K];
             const int bx = k % S.nbx, by = k / S.nbx;
             const int yy = pp / hp, xx = 2 * (pp - yy * hp);
             const int bw = min(B, S.W - bx * B), bh = min(B, S.H - by * B);
             const bool in0 = xx < bw && yy < bh, in1 = xx + 1 < bw && yy < bh;
-            const bool tile1 = xx + 1 < B;                      // second pixel inside the B x B tile
-            PixGeom g;
-            g.x = bx * B + min(xx, bw - 1);
-            g.y = by * B + min(yy, bh - 1);
-            g.blk = 0;
-            g.idx = (g.y - by * B) * bw + (g.x - bx * B);
-            g.toff = (g.y - by * B) * B + (g.x - bx * B);
-            const bool inb = in1;                               // second pixel's taps inside the tap window
-            const int idx1 = in1 ? g.idx + 1 : g.idx, toff1 = in1 ? g.toff + 1 : g.toff;
-            const int x1 = in1 ? g.x + 1 : g.x;
-            const size_t rb = ((size_t)(aK >> (L - K)) * T.gv[L] + (bK >> (L - K))) * 3 * plane + (size_t)g.y * S.W;
+            const int xi = min(xx, bw - 1), yi = min(yy, bh - 1);   // pixels outside the image compute a copy
+            const int p = yi * S.W + xi;
+            const uint32_t idx0 = (uint32_t)(yi * bw + xi), idx1 = in1 ? idx0 + 1u : idx0;
+            const int gx = bx * B + xi, gy = by * B + yi;
+            const size_t rb = ((size_t)(aK >> (L - K)) * T.gv[L] + (bK >> (L - K))) * 3 * plane + (size_t)gy * S.W + gx;
             int v0[3], v1[3];
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                v0[c] = __ldg(S.roots + rb + c * plane + g.x);
-                v1[c] = __ldg(S.roots + rb + c * plane + x1);
+                v0[c] = __ldg(S.roots + rb + c * plane);
+                v1[c] = __ldg(S.roots + rb + c * plane + 1);
             }
-            const Desc *dd = s_desc + gi * nd;
+            const NDesc *dd = s_desc + gi * kDescPer;
+            const uint32_t *slots = s_slot[gi];
             const int lod = S.lod;                              // progressive decode: stop at level lod
             const uint32_t mask = it.y;
             const int nm = K == 2 ? 4 : 1;
-            const size_t o0 = (size_t)yy * B + xx;
+            const size_t o0 = (size_t)gy * S.W + gx;
             // One evaluation site for every (node, 3 channels) step, so that the loop body stays small:
             // phase 0 the shared levels L-1 .. max(K, lod) into v; phase 1 the next child node m with a
-            // marked camera, its level 1 into w = v + SRV (K = 2, lod <= 1); phase 2 its marked cameras,
-            // level 0 into z = w + SRV (lod = 0), each stored to its slot.
+            // flagged camera, its level 1 into w = v + SRV (K = 2, lod <= 1); phase 2 its flagged cameras
+            // with a slot, level 0 into z = w + SRV (lod = 0), each stored to its camera image.
             int w0[3] = {0, 0, 0}, w1[3] = {0, 0, 0};
             int l = L - 1, m = -1, phase = 0, q = 0;
             uint32_t cams = 0;
             for (;;) {
-                const Desc *d = nullptr;
-                bool ref = false;
+                const NDesc *d = nullptr;
                 if (phase == 0) {
                     if (l >= max(K, lod)) {
                         d = dd + (l - K) * 3;
-                        ref = is_ref(aK >> (l - K), bK >> (l - K));
                         l--;
                     } else {
                         phase = 1;
@@ -1237,7 +1453,6 @@ __global__ void __launch_bounds__(256, 4) k_decode_blocks(const __grid_constant_
                     phase = 2;
                     if (K == 2 && lod <= 1) {
                         d = dd + n_sh + m * 3;
-                        ref = is_ref(2 * aK + (m >> 1), 2 * bK + (m & 1));
                     } else {
                         continue;
                     }
@@ -1248,19 +1463,19 @@ __global__ void __launch_bounds__(256, 4) k_decode_blocks(const __grid_constant_
                     }
                     q = __ffs(cams) - 1;
                     cams &= cams - 1;
+                    if (slots[q] == kNone) continue;
                     if (lod == 0) {
                         d = dd + n_sh + n_mid + q * 3;
-                        ref = is_ref(aK * cpa + q / cpa, bK * cpa + q % cpa);
                     } else {
-                        uint32_t *dst = cache + (size_t)(it.z + __popc(mask & ((1u << q) - 1u))) * B2 + o0;
-                        dst[0] = in0 ? ycocg_to_rgb8(w0[0], w0[1], w0[2]) : 0u;
-                        if (tile1) dst[1] = in1 ? ycocg_to_rgb8(w1[0], w1[1], w1[2]) : 0u;
+                        uint32_t *dst = cache + (size_t)slots[q] * plane + o0;
+                        if (in0) dst[0] = ycocg_to_rgb8(w0[0], w0[1], w0[2]);
+                        if (in1) dst[1] = ycocg_to_rgb8(w1[0], w1[1], w1[2]);
                         continue;
                     }
                 }
                 int s0[3], s1[3];
 #pragma unroll
-                for (int c = 0; c < 3; c++) srv_desc2(S, bk, d[c], ref, g, idx1, toff1, inb, s0[c], s1[c]);
+                for (int c = 0; c < 3; c++) eval_pair<BS>(S, d[c], p, xi, yi, idx0, idx1, s0[c], s1[c]);
                 if (phase == 0) {
 #pragma unroll
                     for (int c = 0; c < 3; c++) {
@@ -1274,9 +1489,9 @@ __global__ void __launch_bounds__(256, 4) k_decode_blocks(const __grid_constant_
                         w1[c] += s1[c];
                     }
                 } else {                                            // a camera's level 0
-                    uint32_t *dst = cache + (size_t)(it.z + __popc(mask & ((1u << q) - 1u))) * B2 + o0;
-                    dst[0] = in0 ? ycocg_to_rgb8(w0[0] + s0[0], w0[1] + s0[1], w0[2] + s0[2]) : 0u;
-                    if (tile1) dst[1] = in1 ? ycocg_to_rgb8(w1[0] + s1[0], w1[1] + s1[1], w1[2] + s1[2]) : 0u;
+                    uint32_t *dst = cache + (size_t)slots[q] * plane + o0;
+                    if (in0) dst[0] = ycocg_to_rgb8(w0[0] + s0[0], w0[1] + s0[1], w0[2] + s0[2]);
+                    if (in1) dst[1] = ycocg_to_rgb8(w1[0] + s1[0], w1[1] + s1[1], w1[2] + s1[2]);
                 }
             }
         }
@@ -1307,8 +1522,75 @@ __device__ __noinline__ float3 blend_direct(const DevStream &S, const hmlfc_view
     return make_float3(o[0], o[1], o[2]);
 }
 
+// Blend of the cached render: each ray gathers its 16 RGB8 samples from the
+// decoded camera images (4 camera slots, then 4 pixels per camera at offsets
+// shared by all cameras) and blends them quadrilinearly.  Each thread blends
+// two rays of its tile, (px, py) and (px, py + TH / 2), which share the view
+// lookup and the tile arithmetic.  kFallback: some camera may have no image
+// (the call's cache could not hold every camera of the light field); a ray
+// with such a camera decodes its samples directly.
+template <int BS, bool kFallback>
+__device__ __forceinline__ void blend_cached_ray(const DevStream &S, const hmlfc_view &V, int px, int py,
+                                                 const uint32_t *__restrict__ camslot,
+                                                 const uint32_t *__restrict__ cache, float *__restrict__ out) {
+    Ray r;
+    ray_setup(V, S.nu, S.nv, S.W, S.H, px, py, r);
+    const int sh = S.lod;                          // progressive decode: representative camera of the level-lod node
+    const int i0 = (r.i0 >> sh) << sh, i1 = (r.i1 >> sh) << sh;
+    const int j0 = (r.j0 >> sh) << sh, j1 = (r.j1 >> sh) << sh;
+    const uint32_t s00 = __ldg(camslot + i0 * S.nv + j0), s01 = __ldg(camslot + i0 * S.nv + j1);
+    const uint32_t s10 = __ldg(camslot + i1 * S.nv + j0), s11 = __ldg(camslot + i1 * S.nv + j1);
+    float o[3];
+    // slots are below 2^31 and kNone has the top bit set: one OR tells whether a camera has no image
+    if (!kFallback || !((s00 | s01 | s10 | s11) >> 31)) {
+        const uint32_t plane = (uint32_t)(S.W * S.H);
+        const uint32_t p00 = (uint32_t)(r.y0 * S.W + r.x0);
+        const uint32_t dx = (uint32_t)(r.x1 - r.x0), dy = (uint32_t)((r.y1 - r.y0) * S.W);
+        const uint32_t *c0 = cache + (size_t)s00 * plane + p00, *c1 = cache + (size_t)s01 * plane + p00;
+        const uint32_t *c2 = cache + (size_t)s10 * plane + p00, *c3 = cache + (size_t)s11 * plane + p00;
+        uint32_t val[16];
+        // sample order of blend16: q = a*8 + b*4 + xs*2 + ys  ->  camera a*2+b, corner xs*2+ys
+        val[0] = __ldg(c0); val[1] = __ldg(c0 + dy); val[2] = __ldg(c0 + dx); val[3] = __ldg(c0 + dx + dy);
+        val[4] = __ldg(c1); val[5] = __ldg(c1 + dy); val[6] = __ldg(c1 + dx); val[7] = __ldg(c1 + dx + dy);
+        val[8] = __ldg(c2); val[9] = __ldg(c2 + dy); val[10] = __ldg(c2 + dx); val[11] = __ldg(c2 + dx + dy);
+        val[12] = __ldg(c3); val[13] = __ldg(c3 + dy); val[14] = __ldg(c3 + dx); val[15] = __ldg(c3 + dx + dy);
+        blend16(r, [&](int a, int b, int xs, int ys, int, int, int, int) { return val[a * 8 + b * 4 + xs * 2 + ys]; }, o);
+    } else {
+        const float3 d = blend_direct<BS>(S, V, px, py);   // a camera beyond the cache capacity: decode this ray directly
+        o[0] = d.x;
+        o[1] = d.y;
+        o[2] = d.z;
+    }
+    float *dst = out + V.out_offset + ((size_t)py * V.width + px) * 3;
+    __stcs(dst, o[0]);
+    __stcs(dst + 1, o[1]);
+    __stcs(dst + 2, o[2]);
+}
+
+template <int BS, int TW, int TH, bool kFallback>
+__global__ void __launch_bounds__(TW *TH / 2, 12) k_render_cached(const __grid_constant__ DevStream S,
+                                                             const __grid_constant__ LaunchViews LV,
+                                                             const uint32_t *__restrict__ camslot,
+                                                             const uint32_t *__restrict__ cache, float *__restrict__ out) {
+    int vi = 0;                                     // uniform over the CTA: one search per warp
+    if ((threadIdx.x & 31) == 0) vi = find_view(LV, blockIdx.x);
+    vi = __shfl_sync(0xFFFFFFFFu, vi, 0);
+    const hmlfc_view &V = LV.views[vi];
+    const int local = blockIdx.x - LV.tile_start[vi];
+    const uint32_t mag = LV.tiles_x_magic[vi];
+    const int ty = mag == 1u ? local / ((V.width + TW - 1) / TW) : qdiv(local, mag);
+    const int px = (local - ty * ((V.width + TW - 1) / TW)) * TW + (int)threadIdx.x % TW;
+    const int py = ty * TH + (int)threadIdx.x / TW;
+    if (px >= V.width) return;
+    if (py < V.height) blend_cached_ray<BS, kFallback>(S, V, px, py, camslot, cache, out);
+    if (py + TH / 2 < V.height) blend_cached_ray<BS, kFallback>(S, V, px, py + TH / 2, camslot, cache, out);
+}
+
+// Blend from a decoded-block cache with one slot per (camera, block) pair
+// (the serving form's resident cache): 16 slot lookups, then 16 cached RGB8
+// samples.  A sample beyond the cache decodes its ray directly.
 template <int BS, int TW, int TH>
-__global__ void __launch_bounds__(TW *TH, 6) k_render_cached(const __grid_constant__ DevStream S,
+__global__ void __launch_bounds__(TW *TH, 6) k_render_slots(const __grid_constant__ DevStream S,
                                                          const __grid_constant__ LaunchViews LV,
                                                          const uint32_t *__restrict__ slotmap,
                                                          const uint32_t *__restrict__ cache, float *__restrict__ out) {
@@ -1932,6 +2214,13 @@ cudaError_t launch_decode_tiles(const DevStream &ds, const uint32_t *d_src, int 
     return cudaGetLastError();
 }
 
+cudaError_t launch_build_planes(const DevStream &ds, int64_t n_ref, int16_t *d_planes, cudaStream_t st) {
+    if (n_ref <= 0 || ds.nblocks <= 0) return cudaSuccess;
+    dim3 grid((unsigned)ds.nblocks, (unsigned)(n_ref < 65535 ? n_ref : 65535));
+    k_build_planes<<<grid, 256, 0, st>>>(ds, (int)n_ref, d_planes);
+    return cudaGetLastError();
+}
+
 #define HMLFC_DISPATCH_B(B, CALL) \
     switch (B) {                  \
         case 4: { constexpr int BS = 4; CALL; } break;   \
@@ -1959,32 +2248,51 @@ cudaError_t launch_render(const DevStream &ds, const LaunchViews &lv, int total_
     return e;
 }
 
-cudaError_t launch_mark(const DevStream &ds, const LaunchViews &lv, int total_tiles, uint8_t *flags, cudaStream_t st) {
+cudaError_t launch_mark(const DevStream &ds, const LaunchViews &lv, int total_tiles, uint8_t *flags, bool super_layout,
+                        cudaStream_t st) {
     if (total_tiles <= 0) return cudaSuccess;
-    HMLFC_DISPATCH_B(ds.B, (k_mark<BS, 16, 16><<<(total_tiles + 127) / 128, 128, 0, st>>>(ds, lv, total_tiles, flags)));
+    const unsigned grid = (unsigned)((total_tiles + 7) / 8);
+    if (super_layout) {
+        HMLFC_DISPATCH_B(ds.B, (k_mark<BS, 16, 16, true><<<grid, 256, 0, st>>>(ds, lv, total_tiles, flags)));
+    } else {
+        HMLFC_DISPATCH_B(ds.B, (k_mark<BS, 16, 16, false><<<grid, 256, 0, st>>>(ds, lv, total_tiles, flags)));
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_assign(const DevStream &ds, const uint8_t *flags, uint32_t *slotmap, uint4 *items,
+cudaError_t launch_assign(const DevStream &ds, const uint8_t *flags, uint32_t *camslot, uint4 *items,
                           unsigned long long *counters, uint32_t capacity, cudaStream_t st) {
     const int K = ds.L < 2 ? ds.L : 2;
     const int64_t n_sk = (int64_t)ds.gu[K] * ds.gv[K] * ds.nblocks;
-    const int64_t grid = (n_sk + 255) / 256;
-    if (grid <= 0) return cudaSuccess;
-    k_assign<<<(unsigned)grid, 256, 0, st>>>(ds, flags, slotmap, items, counters, capacity);
+    const int64_t item_blocks = (n_sk + 255) / 256, cam_blocks = ((int64_t)ds.nu * ds.nv + 7) / 8;
+    k_assign<<<(unsigned)(item_blocks + cam_blocks), 256, 0, st>>>(ds, flags, camslot, items, counters, capacity,
+                                                                    (int)item_blocks);
     return cudaGetLastError();
 }
 
 cudaError_t launch_decode_blocks(const DevStream &ds, const uint4 *items, const unsigned long long *counters,
-                                 uint32_t *cache, int grid, cudaStream_t st) {
-    HMLFC_DISPATCH_B(ds.B, (k_decode_blocks<BS><<<grid, 256, 0, st>>>(ds, items, counters, cache)));
+                                 const uint32_t *camslot, uint32_t *cache, int grid, cudaStream_t st) {
+    HMLFC_DISPATCH_B(ds.B, (k_decode_blocks<BS><<<grid, 256, 0, st>>>(ds, items, counters, camslot, cache)));
     return cudaGetLastError();
 }
 
-cudaError_t launch_render_cached(const DevStream &ds, const LaunchViews &lv, int total_tiles, const uint32_t *slotmap,
-                                 const uint32_t *cache, float *d_out, cudaStream_t st) {
+cudaError_t launch_render_cached(const DevStream &ds, const LaunchViews &lv, int total_tiles, const uint32_t *camslot,
+                                 const uint32_t *cache, bool all_cameras, float *d_out, cudaStream_t st) {
     if (total_tiles <= 0) return cudaSuccess;
-    HMLFC_DISPATCH_B(ds.B, (k_render_cached<BS, 16, 16><<<total_tiles, 256, 0, st>>>(ds, lv, slotmap, cache, d_out)));
+    if (all_cameras) {
+        HMLFC_DISPATCH_B(ds.B, (k_render_cached<BS, 16, 16, false><<<total_tiles, 128, 0, st>>>(ds, lv, camslot, cache,
+                                                                                                 d_out)));
+    } else {
+        HMLFC_DISPATCH_B(ds.B, (k_render_cached<BS, 16, 16, true><<<total_tiles, 128, 0, st>>>(ds, lv, camslot, cache,
+                                                                                                d_out)));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render_slots(const DevStream &ds, const LaunchViews &lv, int total_tiles, const uint32_t *slotmap,
+                                const uint32_t *cache, float *d_out, cudaStream_t st) {
+    if (total_tiles <= 0) return cudaSuccess;
+    HMLFC_DISPATCH_B(ds.B, (k_render_slots<BS, 16, 16><<<total_tiles, 256, 0, st>>>(ds, lv, slotmap, cache, d_out)));
     return cudaGetLastError();
 }
 

@@ -131,7 +131,8 @@ def test_render_tiny_within_tolerance(H, torch_cuda, tiny_streams, tiny_cfg, pat
 def test_render_paths_identical(H, torch_cuda, tiny_streams, tiny_cfg, ragged_lf):
     """The cached, direct and per-tile paths decode the same integers and
     blend in the same order: bitwise equal outputs; so does the cached path
-    when its capacity overflows and some blocks fall back to per-ray decode."""
+    when its capacity overflows and the rays of some cameras fall back to
+    per-ray decode."""
     c = tiny_cfg
     cases = [(H.Stream(tiny_streams[c.qstep].stream), _views_mix(c, 32, 8, [(64, 64), (48, 40), (5, 70)]))]
     geo2 = S.lf_geometry(5, 3, 37, 29)
@@ -145,12 +146,13 @@ def test_render_paths_identical(H, torch_cuda, tiny_streams, tiny_cfg, ragged_lf
                 H.set_render_path(path)
                 outs.append(_render_gpu(H, torch_cuda, [st], arr))
             H.set_render_path(0)
-            for cap in (4 * 8 * 8 * 4, 0):        # four blocks, then none
+            # room for a few camera images (the other cameras' rays decode directly), for less than one, none
+            for cap in (5 * st.info["width"] * st.info["height"] * 4, 4 * 8 * 8 * 4, 0):
                 H.set_block_cache_bytes(cap)
                 outs.append(_render_gpu(H, torch_cuda, [st], arr))
         finally:
             H.set_render_path(0)
-            H.set_block_cache_bytes(256 << 20)
+            H.set_block_cache_bytes(H.DEFAULT_CACHE_BYTES)
         for o in outs[1:]:
             assert np.array_equal(outs[0], o)
 
@@ -321,7 +323,7 @@ def test_render_views_host_equals_device_render(torch_cuda, tiny_streams, tiny_c
         off += int(views[v]["width"]) * int(views[v]["height"]) * 3 + gap
     H.set_render_path(path)
     try:
-        for cache in (256 << 20, 3 * st.info["block"] ** 2 * 4, 0):
+        for cache in (H.DEFAULT_CACHE_BYTES, 5 * c.width * c.height * 4, 3 * st.info["block"] ** 2 * 4, 0):
             H.set_block_cache_bytes(cache)
             dev = torch.full((off,), -5.0, dtype=torch.float32, device="cuda")
             H.render_views([st], views, dev)
@@ -330,7 +332,7 @@ def test_render_views_host_equals_device_render(torch_cuda, tiny_streams, tiny_c
             torch.cuda.synchronize()
             assert torch.equal(dev.cpu(), host), (path, cache)
     finally:
-        H.set_block_cache_bytes(256 << 20)
+        H.set_block_cache_bytes(H.DEFAULT_CACHE_BYTES)
         H.set_render_path(0)
 
 

@@ -97,11 +97,12 @@ def test_progressive_paths_bitwise_equal_and_cache_overflow(torch_cuda, tiny_str
                 H.set_render_path(path)
                 outs.append(H.render_views([st], views, level=k))
             H.set_render_path(0)
-            H.set_block_cache_bytes(3 * st.info["block"] ** 2 * 4)
             try:
-                outs.append(H.render_views([st], views, level=k))
+                for cap in (3 * W * Hh * 4, 3 * st.info["block"] ** 2 * 4):   # three camera images; less than one
+                    H.set_block_cache_bytes(cap)
+                    outs.append(H.render_views([st], views, level=k))
             finally:
-                H.set_block_cache_bytes(256 << 20)
+                H.set_block_cache_bytes(H.DEFAULT_CACHE_BYTES)
             for o in outs[1:]:
                 assert torch.equal(outs[0], o), k
 

@@ -67,11 +67,11 @@ def test_noalloc_render_matches_render_views(tiny_streams, tiny_cfg, ragged_lf):
 
 
 def test_noalloc_overflow_into_per_ray_decode():
-    """A 9x9 grid of 512x512 views with 16x16 blocks: 64 circling views reach
-    more (camera, block) pairs than the 32 MiB array holds, so the blocks
-    beyond it are decoded per ray.  Two calls in a row (different views),
-    each the same bits as hmlfc_render_views; sampled pixels within 1e-3 of
-    the oracle."""
+    """A 9x9 grid of 512x512 views with 16x16 blocks: the decoded camera
+    images that 64 circling views reach do not all fit the 32 MiB array
+    (1 MiB per camera), so the rays of the cameras beyond it decode their
+    samples directly.  Two calls in a row (different views), each the same
+    bits as hmlfc_render_views; sampled pixels within 1e-3 of the oracle."""
     torch, H, lib, fn = _setup()
     lf = S.make_lf(91, 9, 9, 512, 512, 6, 12.0, "pink")
     data = O.encode(lf, 3, 16, 4, 4, t_ref=400, t_pred=800).stream
@@ -93,19 +93,20 @@ def test_noalloc_overflow_into_per_ray_decode():
         ref = O.Stream(data).render_pixels(arr, pix)
         idx = (arr["out_offset"][pix[:, 0]] + (pix[:, 2] * 512 + pix[:, 1]) * 3)[:, None] + np.arange(3)[None, :]
         assert np.max(np.abs(got.cpu().numpy().astype(np.float64)[idx] - ref)) <= 1e-3
-    # the array holds at most 32 MiB / (16 * 16 * 4 B) slots: the first call overflowed it
+    # even the blocks alone (16 * 16 * 4 B each) exceed the array: the first call overflowed it
     assert reached[0] * 16 * 16 * 4 > (32 << 20)          # HMLFC_FIXED_SCRATCH_BYTES
 
 
 def test_noalloc_rejects_a_block_index_beyond_the_array():
-    """8x8 cameras of 512x512 with 2x2 blocks: 4.2M (camera, block) pairs, a
-    block index of more than 32 MiB.  The call returns HMLFC_E_UNSUPPORTED
-    with a message and writes nothing; hmlfc_render_views still renders."""
+    """8x8 cameras of 1024x512 with 2x2 blocks and one SRV level: 8.4M
+    (camera, block) pairs and 2.1M (level-1 node, block) decode items, a
+    block index of about 42 MB.  The call returns HMLFC_E_UNSUPPORTED with a
+    message and writes nothing; hmlfc_render_views still renders."""
     torch, H, lib, fn = _setup()
-    lf = S.make_lf(93, 8, 8, 512, 512, 3, 4.0, "noise_gradient")
-    data = O.encode(lf, 2, 2, 1, 8, mc=O.MC_OFF).stream
+    lf = S.make_lf(93, 8, 8, 1024, 512, 3, 4.0, "noise_gradient")
+    data = O.encode(lf, 1, 2, 1, 8, mc=O.MC_OFF).stream
     st = H.Stream(data)
-    geo = S.lf_geometry(8, 8, 512, 512)
+    geo = S.lf_geometry(8, 8, 1024, 512)
     arr = S.views_to_array(S.random_views(94, geo, 2, [(64, 64)]))
     rc, got = _noalloc(torch, H, fn, [st], arr, fill=-7.0)
     assert rc == H.E_UNSUPPORTED
