@@ -14,9 +14,20 @@
 
 #include "hmlfc_host.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 using namespace hmlfc;
 
 namespace {
+
+// A named range on the host timeline (NVTX; free when no profiler listens):
+// the load, render, decode and serve calls of the library.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 thread_local std::string g_err;
 int g_render_path = 0;                      // 0 cached blocks, 1 direct per ray, 2 per-tile staging
@@ -428,6 +439,7 @@ int cached_launches(const hmlfc_stream *s, const DevStream &ds, const CachedLayo
     unsigned long long *counters = reinterpret_cast<unsigned long long *>(b + c.o_count);
     uint32_t *cache = reinterpret_cast<uint32_t *>(b + c.index_bytes);
     if (phases) phase_mark(0, st);
+    NvtxRange range("hmlfc cached render: mark, assign, decode, blend launches");
     // the scratch keeps an earlier call's contents: clear what must start at zero
     cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)c.n_keys, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 16, st);
@@ -502,6 +514,7 @@ int hmlfc_set_block_cache_bytes(size_t bytes) {
 }
 
 int hmlfc_load_stream(const void *h_bytes, size_t nbytes, int device, void *cuda_stream, hmlfc_stream **out) {
+    NvtxRange nvtx_range("hmlfc load_stream");
     if (!out) return fail(HMLFC_E_INVALID_ARG, "out is NULL");
     *out = nullptr;
     const uint8_t *p = static_cast<const uint8_t *>(h_bytes);
@@ -619,6 +632,7 @@ int hmlfc_stream_info(const hmlfc_stream *s, hmlfc_stream_info_t *out) {
 
 int hmlfc_decode_pixels_lod(const hmlfc_stream *s, const int32_t *d_coords, int64_t n, int level, uint8_t *d_rgb,
                             void *cuda_stream) {
+    NvtxRange nvtx_range("hmlfc decode_pixels");
     if (!s) return fail(HMLFC_E_INVALID_ARG, "stream is NULL");
     if (n < 0) return fail(HMLFC_E_INVALID_ARG, "negative count");
     if (level < 0 || level > s->g.L) return fail(HMLFC_E_INVALID_ARG, "level %d outside 0..%d", level, s->g.L);
@@ -656,6 +670,7 @@ int hmlfc_render_views(const hmlfc_stream *const *streams, int n_streams, const 
 
 int hmlfc_render_views_lod(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views, int n_views,
                            int level, float *d_out, void *cuda_stream) {
+    NvtxRange nvtx_range("hmlfc render_views");
     int rc = check_views(streams, n_streams, h_views, n_views);
     if (rc != HMLFC_OK) return rc;
     for (int k = 0; k < n_streams; k++)
@@ -709,6 +724,7 @@ cudaStream_t copy_stream(int device) {
 
 int hmlfc_render_views_host(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views, int n_views,
                             float *h_out, void *cuda_stream) {
+    NvtxRange nvtx_range("hmlfc render_views_host");
     int rc = check_views(streams, n_streams, h_views, n_views);
     if (rc != HMLFC_OK) return rc;
     if (n_views > 0 && !h_out) return fail(HMLFC_E_INVALID_ARG, "h_out is NULL");
@@ -765,6 +781,7 @@ int hmlfc_render_views_host(const hmlfc_stream *const *streams, int n_streams, c
 // or on the host.
 int hmlfc_render_views_noalloc(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views,
                                int n_views, float *d_out, void *cuda_stream) {
+    NvtxRange nvtx_range("hmlfc render_views_noalloc");
     int rc = check_views(streams, n_streams, h_views, n_views);
     if (rc != HMLFC_OK) return rc;
     if (n_views > 0 && !d_out) return fail(HMLFC_E_INVALID_ARG, "d_out is NULL");
@@ -822,6 +839,7 @@ int hmlfc_set_batch_tuning(int tile_shape, int group, int ctas_per_sm, size_t ca
 
 int hmlfc_render_batch(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views, int n_views,
                        float *d_out, void *cuda_stream) {
+    NvtxRange nvtx_range("hmlfc render_batch");
     int rc = check_views(streams, n_streams, h_views, n_views);
     if (rc != HMLFC_OK) return rc;
     if (n_views > 0 && !d_out) return fail(HMLFC_E_INVALID_ARG, "d_out is NULL");
@@ -955,6 +973,7 @@ void hmlfc_server_free(hmlfc_server *sv) {
 }
 
 int hmlfc_server_render(hmlfc_server *sv, const hmlfc_view *h_views, int n_views, float *d_out, void *cuda_stream) {
+    NvtxRange nvtx_range("hmlfc server_render");
     if (!sv) return fail(HMLFC_E_INVALID_ARG, "server is NULL");
     const hmlfc_stream *s = sv->s;
     int rc = check_views(&s, 1, h_views, n_views);
@@ -1002,6 +1021,7 @@ int hmlfc_server_stats(const hmlfc_server *sv, void *cuda_stream, int64_t *out3)
 int hmlfc_render_views_relaxed(const hmlfc_stream *const *streams, int n_streams, const float *const *d_coeff,
                                const float *const *d_root, const hmlfc_view *h_views, int n_views, float *d_out,
                                void *cuda_stream) {
+    NvtxRange nvtx_range("hmlfc render_views_relaxed");
     int rc = check_views(streams, n_streams, h_views, n_views);
     if (rc != HMLFC_OK) return rc;
     if (n_views == 0) return HMLFC_OK;
@@ -1023,6 +1043,7 @@ int hmlfc_render_views_relaxed(const hmlfc_stream *const *streams, int n_streams
 int hmlfc_render_backward(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views, int n_views,
                           const float *d_grad_out, float *const *d_grad_coeff, float *const *d_grad_root,
                           void *cuda_stream) {
+    NvtxRange nvtx_range("hmlfc render_backward");
     int rc = check_views(streams, n_streams, h_views, n_views);
     if (rc != HMLFC_OK) return rc;
     if (n_views == 0) return HMLFC_OK;

@@ -247,17 +247,19 @@ def serve_continuous(cache: ResidentCache, requests, pool_floats: int, max_batch
         while events and events[0].query():
             events.popleft()
             t = time.perf_counter() - t0
-            for r in sched.complete(t):
-                s = sched.served[r.rid]
-                if keep_results:
-                    s.result = pool.buf[s.offset:s.offset + s.n].cpu().numpy()
+            with torch.cuda.nvtx.range("serve: complete batch"):
+                for r in sched.complete(t):
+                    s = sched.served[r.rid]
+                    if keep_results:
+                        s.result = pool.buf[s.offset:s.offset + s.n].cpu().numpy()
         batch = sched.next_batch()
         if batch:
-            arr = np.concatenate([_pair_array(r, o) for r, o in batch])
-            with torch.cuda.stream(cs):
-                cache.render(arr, pool.buf, cuda_stream=cs)
-                ev = torch.cuda.Event()
-                ev.record(cs)
+            with torch.cuda.nvtx.range(f"serve: launch batch of {len(batch)} requests"):
+                arr = np.concatenate([_pair_array(r, o) for r, o in batch])
+                with torch.cuda.stream(cs):
+                    cache.render(arr, pool.buf, cuda_stream=cs)
+                    ev = torch.cuda.Event()
+                    ev.record(cs)
             events.append(ev)
             rep.batches += 1
             rep.views += 2 * len(batch)
