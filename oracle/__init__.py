@@ -217,7 +217,7 @@ def bise_unpack(buf: np.ndarray, mode: int, b: int, n: int) -> np.ndarray:
 
 class _Params(C.Structure):
     _fields_ = [(n, C.c_int32) for n in
-                ("nu", "nv", "W", "H", "L", "B", "Ws", "q", "t_ref", "t_pred", "mc")]
+                ("nu", "nv", "W", "H", "L", "B", "Ws", "q", "t_ref", "t_pred", "mc", "sub")]
 
 
 MC_OFF, MC_QPEL, MC_ZERO, MC_INTEGER = 0, 1, 2, 3
@@ -231,12 +231,13 @@ class EncodeResult:
 
 
 def encode(lf: np.ndarray, levels: int, block: int, search: int, qstep: int,
-           t_ref: int = 0, t_pred: int = 0, mc: int = MC_QPEL, debug: bool = False) -> EncodeResult:
+           t_ref: int = 0, t_pred: int = 0, mc: int = MC_QPEL, debug: bool = False, sub: int = 0) -> EncodeResult:
     """HMLFC encoder (Sec. 4.3-4.7): hierarchy, closed-loop phase-shifted MC,
-    quantiser + two block thresholds, BISE, breadth-first stream."""
+    quantiser + two block thresholds, BISE, breadth-first stream.  sub = 1:
+    chroma sub-sampled 4:2:0 (Sec. 4.5; Co, Cg coded at half resolution)."""
     lf = np.ascontiguousarray(lf, np.uint8)
     nu, nv, H, W, _ = lf.shape
-    prm = _Params(nu, nv, W, H, levels, block, search, qstep, t_ref, t_pred, mc)
+    prm = _Params(nu, nv, W, H, levels, block, search, qstep, t_ref, t_pred, mc, sub)
     out = C.c_void_p()
     n = C.c_size_t()
     S = R = None
@@ -275,11 +276,11 @@ class Stream:
         h = C.c_void_p()
         _check(lib().orc_open(_p(self._buf), len(self._buf), C.byref(h)), "open")
         self._h = h
-        info = np.zeros(16, np.int32)
+        info = np.zeros(17, np.int32)
         lib().orc_stream_info(self._h, _p(info))
         (self.nu, self.nv, self.W, self.H, self.L, self.B, self.Ws, self.q, self.mc,
          self.n_nc, self.nblocks, self.n_sig, self.n_rec_words, self.n_mv, self.n_roots,
-         self.nbytes) = (int(x) for x in info)
+         self.nbytes, self.sub) = (int(x) for x in info)
 
     def close(self):
         if getattr(self, "_h", None):

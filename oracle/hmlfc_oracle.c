@@ -248,18 +248,36 @@ typedef struct {
     int gu[33], gv[33];
     int64_t nc_base[33]; /* BFS index of the first node-channel of level l */
     int64_t n_nc;
+    /* chroma sub-sampling (Sec. 4.5): sub = 1 codes Co and Cg at
+     * ceil(W/2) x ceil(H/2); per channel c its plane size, block grid and
+     * the offset of its plane within one node's planes (npx values) */
+    int sub;
+    int cW[3], cH[3], cnbx[3], cnby[3], cnb[3];
+    size_t coff[3], npx;
 } geom;
 
 static int grid_n(int n, int l) { return (n + (1 << l) - 1) >> l; }
 
-static int make_geom(geom *g, int nu, int nv, int W, int H, int L, int B) {
+static int make_geom(geom *g, int nu, int nv, int W, int H, int L, int B, int sub) {
     if (nu < 1 || nv < 1 || W < 1 || H < 1 || L < 1 || L > 30 || B < 1 || B > 64) return ORC_E_ARG;
+    if (sub != 0 && (sub != 1 || B % 2 != 0)) return ORC_E_ARG;
     memset(g, 0, sizeof(*g));
-    g->nu = nu; g->nv = nv; g->W = W; g->H = H; g->L = L; g->B = B;
+    g->nu = nu; g->nv = nv; g->W = W; g->H = H; g->L = L; g->B = B; g->sub = sub;
     g->nbx = (W + B - 1) / B;
     g->nby = (H + B - 1) / B;
     g->nblocks = g->nbx * g->nby;
     g->ngroups = (g->nblocks + 31) / 32;
+    size_t off = 0;
+    for (int c = 0; c < 3; c++) {
+        g->cW[c] = (sub && c > 0) ? (W + 1) / 2 : W;
+        g->cH[c] = (sub && c > 0) ? (H + 1) / 2 : H;
+        g->cnbx[c] = (g->cW[c] + B - 1) / B;
+        g->cnby[c] = (g->cH[c] + B - 1) / B;
+        g->cnb[c] = g->cnbx[c] * g->cnby[c];
+        g->coff[c] = off;
+        off += (size_t)g->cW[c] * g->cH[c];
+    }
+    g->npx = off;
     for (int l = 0; l <= L; l++) { g->gu[l] = grid_n(nu, l); g->gv[l] = grid_n(nv, l); }
     /* breadth-first from the top: level L-1 first, nodes row-major (u major),
      * channels Y, Co, Cg innermost (Sec. 4.7) */
@@ -275,6 +293,19 @@ static int make_geom(geom *g, int nu, int nv, int W, int H, int L, int B) {
 static int64_t nc_of(const geom *g, int l, int a, int b, int c) {
     return g->nc_base[l] + ((int64_t)a * g->gv[l] + b) * 3 + c;
 }
+
+/* The geometry of channel c's planes: a copy of g with the plane size and
+ * block grid of that channel (the other fields unchanged). */
+static geom chan_geom(const geom *g, int c) {
+    geom gc = *g;
+    gc.W = g->cW[c]; gc.H = g->cH[c];
+    gc.nbx = g->cnbx[c]; gc.nby = g->cnby[c]; gc.nblocks = g->cnb[c];
+    return gc;
+}
+
+/* Channel of a node-channel (the channels are innermost in BFS order, and
+ * every level's first node-channel index is a multiple of 3). */
+static int chan_of(int64_t nc) { return (int)(nc % 3); }
 
 /* Reference member of a sibling cluster: the node with both grid
  * coordinates even (the top-left member of its 2x2 cluster). */
@@ -297,8 +328,9 @@ static uint32_t mv_range(int Ws) { return 2u * (uint32_t)(8 * Ws + 1) * (uint32_
 /* ------------------------------------------------------------------ */
 
 typedef struct {
-    int32_t nu, nv, W, H, L, B, Ws, q, t_ref, t_pred, mc;
+    int32_t nu, nv, W, H, L, B, Ws, q, t_ref, t_pred, mc, sub;
 } orc_params;
+/* sub: 1 = chroma sub-sampled 4:2:0 (Co, Cg at half resolution; B even). */
 /* mc: 0 = no motion compensation (plain hierarchical residual coding),
  *     1 = phase-shifted search, integer then quarter-pel refinement,
  *     2 = zero motion (mv = 0, subtractive sign) for every block,
@@ -418,7 +450,7 @@ static void mc_search(const int32_t *S, const int16_t *R, const geom *g, int k, 
 int orc_mc_search_block(const int32_t *S, const int16_t *R, int W, int H, int B, int k, int Ws, int refine,
                         int64_t *out4) {
     geom g;
-    if (make_geom(&g, 1, 1, W, H, 1, B) != ORC_OK || k < 0 || k >= g.nblocks || Ws < 0) return ORC_E_ARG;
+    if (make_geom(&g, 1, 1, W, H, 1, B, 0) != ORC_OK || k < 0 || k >= g.nblocks || Ws < 0) return ORC_E_ARG;
     int mvx, mvy, sign;
     int64_t cost;
     mc_search(S, R, &g, k, Ws, refine, &mvx, &mvy, &sign, &cost);
@@ -426,44 +458,67 @@ int orc_mc_search_block(const int32_t *S, const int16_t *R, int W, int H, int B,
     return ORC_OK;
 }
 
-/* Level images I_l (int16, [node][3][H][W]); I_0 = YCoCg-R of the views and
- * I_{l+1}(node) = floor((sum of the cluster's members + floor(k/2)) / k),
- * per pixel and channel (Sec. 4.3 reading: uniform pixel-wise filter). */
+/* Level images I_l (int16, [node][npx]: channel c's plane at coff[c]).
+ * I_0 = YCoCg-R of the views (Sec. 4.5); with chroma sub-sampling, Co and Cg
+ * are then reduced to ceil(W/2) x ceil(H/2) by the rounded mean of each 2x2
+ * pixel group (1-4 members at odd edges) -- the reading fixed for "the
+ * chroma channels are sub-sampled".  I_{l+1}(node) = floor((sum of the
+ * cluster's members + floor(k/2)) / k), per pixel and channel (Sec. 4.3
+ * reading: uniform pixel-wise filter). */
 static int16_t *build_levels(const geom *g, const uint8_t *lf, int l_top, int16_t **lev) {
-    size_t plane = (size_t)g->W * g->H;
-    lev[0] = (int16_t *)malloc((size_t)g->nu * g->nv * 3 * plane * sizeof(int16_t));
-    if (!lev[0]) return NULL;
+    size_t plane = (size_t)g->W * g->H, npx = g->npx;
+    lev[0] = (int16_t *)malloc((size_t)g->nu * g->nv * npx * sizeof(int16_t));
+    int16_t *full = (int16_t *)malloc(3 * plane * sizeof(int16_t));
+    if (!lev[0] || !full) { free(full); return NULL; }
     for (int i = 0; i < g->nu; i++)
-        for (int j = 0; j < g->nv; j++)
+        for (int j = 0; j < g->nv; j++) {
             for (size_t p = 0; p < plane; p++) {
                 const uint8_t *px = lf + (((size_t)i * g->nv + j) * plane + p) * 3;
                 int y, co, cg;
                 orc_rgb_to_ycocg(px[0], px[1], px[2], &y, &co, &cg);
-                int16_t *dst = lev[0] + ((size_t)i * g->nv + j) * 3 * plane;
-                dst[p] = (int16_t)y;
-                dst[plane + p] = (int16_t)co;
-                dst[2 * plane + p] = (int16_t)cg;
+                full[p] = (int16_t)y;
+                full[plane + p] = (int16_t)co;
+                full[2 * plane + p] = (int16_t)cg;
             }
+            int16_t *dst = lev[0] + ((size_t)i * g->nv + j) * npx;
+            for (int c = 0; c < 3; c++) {
+                const int16_t *src = full + c * plane;
+                int16_t *d = dst + g->coff[c];
+                if (!(g->sub && c > 0)) { memcpy(d, src, plane * sizeof(int16_t)); continue; }
+                for (int yc = 0; yc < g->cH[c]; yc++)
+                    for (int xc = 0; xc < g->cW[c]; xc++) {
+                        int64_t sum = 0;
+                        int k = 0;
+                        for (int dy = 0; dy < 2; dy++)
+                            for (int dx = 0; dx < 2; dx++) {
+                                int x = 2 * xc + dx, y = 2 * yc + dy;
+                                if (x >= g->W || y >= g->H) continue;
+                                sum += src[(size_t)y * g->W + x];
+                                k++;
+                            }
+                        d[(size_t)yc * g->cW[c] + xc] = (int16_t)fdiv(sum + k / 2, k);
+                    }
+            }
+        }
+    free(full);
     for (int l = 0; l < l_top; l++) {
         int gu = g->gu[l], gv = g->gv[l], pu = g->gu[l + 1], pv = g->gv[l + 1];
-        lev[l + 1] = (int16_t *)malloc((size_t)pu * pv * 3 * plane * sizeof(int16_t));
+        lev[l + 1] = (int16_t *)malloc((size_t)pu * pv * npx * sizeof(int16_t));
         if (!lev[l + 1]) return NULL;
         for (int A = 0; A < pu; A++)
             for (int Bn = 0; Bn < pv; Bn++)
-                for (int c = 0; c < 3; c++)
-                    for (size_t p = 0; p < plane; p++) {
-                        int64_t sum = 0;
-                        int k = 0;
-                        for (int da = 0; da < 2; da++)
-                            for (int db = 0; db < 2; db++) {
-                                int a = 2 * A + da, b = 2 * Bn + db;
-                                if (a >= gu || b >= gv) continue;
-                                sum += lev[l][(((size_t)a * gv + b) * 3 + c) * plane + p];
-                                k++;
-                            }
-                        lev[l + 1][(((size_t)A * pv + Bn) * 3 + c) * plane + p] =
-                            (int16_t)fdiv(sum + k / 2, k);
-                    }
+                for (size_t p = 0; p < npx; p++) {
+                    int64_t sum = 0;
+                    int k = 0;
+                    for (int da = 0; da < 2; da++)
+                        for (int db = 0; db < 2; db++) {
+                            int a = 2 * A + da, b = 2 * Bn + db;
+                            if (a >= gu || b >= gv) continue;
+                            sum += lev[l][((size_t)a * gv + b) * npx + p];
+                            k++;
+                        }
+                    lev[l + 1][((size_t)A * pv + Bn) * npx + p] = (int16_t)fdiv(sum + k / 2, k);
+                }
     }
     return lev[0];
 }
@@ -570,12 +625,12 @@ int orc_encode(const orc_params *P, const uint8_t *lf, uint8_t **out, size_t *ou
                int32_t *dbg_S, int32_t *dbg_R) {
     geom g;
     if (!P || !lf || !out || !out_len) return ORC_E_ARG;
-    if (make_geom(&g, P->nu, P->nv, P->W, P->H, P->L, P->B) != ORC_OK) return ORC_E_ARG;
+    if (make_geom(&g, P->nu, P->nv, P->W, P->H, P->L, P->B, P->sub) != ORC_OK) return ORC_E_ARG;
     if (P->q < 1 || P->Ws < 0 || P->Ws > 64 || P->mc < 0 || P->mc > 3 || P->t_ref < 0 || P->t_pred < 0)
         return ORC_E_ARG;
     g.Ws = P->Ws; g.q = P->q; g.t_ref = P->t_ref; g.t_pred = P->t_pred; g.mc = P->mc;
     const int L = g.L, W = g.W, H = g.H;
-    const size_t plane = (size_t)W * H;
+    const size_t plane = (size_t)W * H, npx = g.npx;
     int rc = ORC_OK;
 
     int16_t *lev[33] = {0};
@@ -586,7 +641,7 @@ int orc_encode(const orc_params *P, const uint8_t *lf, uint8_t **out, size_t *ou
 
     /* roots: the level-L RKVs, stored losslessly (reconstruction = exact) */
     {
-        size_t n = (size_t)g.gu[L] * g.gv[L] * 3 * plane;
+        size_t n = (size_t)g.gu[L] * g.gv[L] * npx;
         rec[L] = (int32_t *)malloc(n * sizeof(int32_t));
         if (!rec[L]) { rc = ORC_E_OOM; goto done; }
         for (size_t i = 0; i < n; i++) rec[L][i] = lev[L][i];
@@ -594,8 +649,8 @@ int orc_encode(const orc_params *P, const uint8_t *lf, uint8_t **out, size_t *ou
 
     for (int l = L - 1; l >= 0 && rc == ORC_OK; l--) {
         const int gu = g.gu[l], gv = g.gv[l], pv = g.gv[l + 1];
-        rec[l] = (int32_t *)malloc((size_t)gu * gv * 3 * plane * sizeof(int32_t));
-        int32_t *Rhat = (int32_t *)calloc((size_t)gu * gv * 3 * plane, sizeof(int32_t));
+        rec[l] = (int32_t *)malloc((size_t)gu * gv * npx * sizeof(int32_t));
+        int32_t *Rhat = (int32_t *)calloc((size_t)gu * gv * npx, sizeof(int32_t));
         if (!rec[l] || !Rhat) { free(Rhat); rc = ORC_E_OOM; break; }
         /* references first: their dequantised SRVs predict the siblings */
         for (int pass = 0; pass < 2 && rc == ORC_OK; pass++) {
@@ -604,39 +659,47 @@ int orc_encode(const orc_params *P, const uint8_t *lf, uint8_t **out, size_t *ou
                     int ref = is_ref(a, b);
                     if ((pass == 0) != ref) continue;
                     for (int c = 0; c < 3 && rc == ORC_OK; c++) {
+                        /* every plane of channel c has that channel's size and block grid */
+                        const geom gc = chan_geom(&g, c);
+                        const size_t cpl = (size_t)gc.W * gc.H;
                         int64_t nc = nc_of(&g, l, a, b, c);
                         nc_out *o = &ncs[nc];
-                        o->sig = (uint8_t *)calloc((size_t)g.nblocks, 1);
-                        o->roff = (uint32_t *)calloc((size_t)g.nblocks, sizeof(uint32_t));
-                        if (!ref && g.mc != 0) o->mvsym = (uint32_t *)calloc((size_t)g.nblocks, sizeof(uint32_t));
-                        int32_t *S = (int32_t *)malloc(plane * sizeof(int32_t));
-                        int32_t *res = (int32_t *)malloc(plane * sizeof(int32_t));
-                        int32_t *deq = (int32_t *)malloc(plane * sizeof(int32_t));
-                        int16_t *R16 = (int16_t *)malloc(plane * sizeof(int16_t));
+                        o->sig = (uint8_t *)calloc((size_t)gc.nblocks, 1);
+                        o->roff = (uint32_t *)calloc((size_t)gc.nblocks, sizeof(uint32_t));
+                        if (!ref && g.mc != 0) o->mvsym = (uint32_t *)calloc((size_t)gc.nblocks, sizeof(uint32_t));
+                        int32_t *S = (int32_t *)malloc(cpl * sizeof(int32_t));
+                        int32_t *res = (int32_t *)malloc(cpl * sizeof(int32_t));
+                        int32_t *deq = (int32_t *)malloc(cpl * sizeof(int32_t));
+                        int16_t *R16 = (int16_t *)malloc(cpl * sizeof(int16_t));
                         if (!o->sig || !o->roff || (!ref && g.mc != 0 && !o->mvsym) || !S || !res || !deq || !R16) {
                             free(S); free(res); free(deq); free(R16); rc = ORC_E_OOM; break;
                         }
                         /* SRV = child - reconstructed parent (closed loop) */
-                        const int16_t *child = lev[l] + (((size_t)a * gv + b) * 3 + c) * plane;
-                        const int32_t *par = rec[l + 1] + (((size_t)(a / 2) * pv + b / 2) * 3 + c) * plane;
-                        for (size_t p = 0; p < plane; p++) S[p] = (int32_t)child[p] - par[p];
-                        if (dbg_S) memcpy(dbg_S + (size_t)nc * plane, S, plane * sizeof(int32_t));
+                        const int16_t *child = lev[l] + ((size_t)a * gv + b) * npx + g.coff[c];
+                        const int32_t *par = rec[l + 1] + ((size_t)(a / 2) * pv + b / 2) * npx + g.coff[c];
+                        for (size_t p = 0; p < cpl; p++) S[p] = (int32_t)child[p] - par[p];
+                        if (dbg_S) {
+                            int32_t *d = dbg_S + (size_t)nc * plane;       /* [n_nc][H][W], channel plane top-left */
+                            memset(d, 0, plane * sizeof(int32_t));
+                            for (int y = 0; y < gc.H; y++) memcpy(d + (size_t)y * W, S + (size_t)y * gc.W, gc.W * sizeof(int32_t));
+                        }
                         const int32_t *Rref = NULL;
                         if (!ref) {
-                            Rref = Rhat + (((size_t)(a & ~1) * gv + (b & ~1)) * 3 + c) * plane;
-                            for (size_t p = 0; p < plane; p++) R16[p] = (int16_t)Rref[p];
+                            Rref = Rhat + ((size_t)(a & ~1) * gv + (b & ~1)) * npx + g.coff[c];
+                            for (size_t p = 0; p < cpl; p++) R16[p] = (int16_t)Rref[p];
                         }
-                        int32_t *shat = rec[l] + (((size_t)a * gv + b) * 3 + c) * plane;
-                        int brc = code_nc(&g, o, ref, S, R16, res, deq, shat);
-                        if (ref) {
-                            int32_t *dst = Rhat + (((size_t)a * gv + b) * 3 + c) * plane;
-                            memcpy(dst, shat, plane * sizeof(int32_t));
-                            if (dbg_R) memcpy(dbg_R + (size_t)nc * plane, shat, plane * sizeof(int32_t));
-                        } else if (dbg_R) {
-                            memset(dbg_R + (size_t)nc * plane, 0, plane * sizeof(int32_t));
+                        int32_t *shat = rec[l] + ((size_t)a * gv + b) * npx + g.coff[c];
+                        int brc = code_nc(&gc, o, ref, S, R16, res, deq, shat);
+                        if (dbg_R) {
+                            int32_t *d = dbg_R + (size_t)nc * plane;
+                            memset(d, 0, plane * sizeof(int32_t));
+                            if (ref)
+                                for (int y = 0; y < gc.H; y++)
+                                    memcpy(d + (size_t)y * W, shat + (size_t)y * gc.W, gc.W * sizeof(int32_t));
                         }
+                        if (ref) memcpy(Rhat + ((size_t)a * gv + b) * npx + g.coff[c], shat, cpl * sizeof(int32_t));
                         /* reconstruction of this node: parent + reconstructed SRV */
-                        for (size_t p = 0; p < plane; p++) {
+                        for (size_t p = 0; p < cpl; p++) {
                             int64_t v = (int64_t)par[p] + shat[p];
                             if (v < -32768 || v > 32767) brc = ORC_E_RANGE;
                             shat[p] = (int32_t)v;
@@ -654,19 +717,19 @@ int orc_encode(const orc_params *P, const uint8_t *lf, uint8_t **out, size_t *ou
 
     /* ---- Sec. 4.7: serialise breadth-first ---- */
     {
-        uint64_t nsig = 0, nrecw = 0, npred = 0;
+        uint64_t nsig = 0, nrecw = 0, nmv = 0;
         for (int64_t nc = 0; nc < g.n_nc; nc++) {
-            for (int k = 0; k < g.nblocks; k++) nsig += ncs[nc].sig[k];
+            const int nb = g.cnb[chan_of(nc)];
+            for (int k = 0; k < nb; k++) nsig += ncs[nc].sig[k];
             nrecw += ncs[nc].nrec;
-            if (ncs[nc].mvsym) npred++;
+            if (ncs[nc].mvsym) nmv += (uint64_t)nb;          /* one symbol per block of a predictive node-channel */
         }
-        uint64_t nmv = npred * (uint64_t)g.nblocks;
         int mv_mode = 0, mv_b = 0;
         if (g.mc != 0) orc_bise_choose(mv_range(g.Ws), &mv_mode, &mv_b);
         uint64_t nmvw = g.mc != 0 ? (orc_bise_bits(mv_mode, mv_b, nmv) + 31) / 32 : 0;
         size_t nroot = (size_t)g.gu[L] * g.gv[L];
         size_t off_roots = ORC_HEADER_WORDS * 4;
-        size_t off_groups = align16(off_roots + nroot * 3 * plane * 2);
+        size_t off_groups = align16(off_roots + nroot * npx * 2);
         size_t off_offs = align16(off_groups + (size_t)g.n_nc * g.ngroups * 16);
         size_t off_recs = align16(off_offs + nsig * 2);
         size_t off_mvs = align16(off_recs + nrecw * 4);
@@ -678,15 +741,16 @@ int orc_encode(const orc_params *P, const uint8_t *lf, uint8_t **out, size_t *ou
         hdr[0] = ORC_MAGIC; hdr[1] = ORC_VERSION;
         hdr[2] = (uint32_t)g.nu; hdr[3] = (uint32_t)g.nv; hdr[4] = (uint32_t)W; hdr[5] = (uint32_t)H;
         hdr[6] = (uint32_t)L; hdr[7] = (uint32_t)g.B; hdr[8] = (uint32_t)g.Ws; hdr[9] = (uint32_t)g.q;
-        hdr[10] = (uint32_t)g.t_ref; hdr[11] = (uint32_t)g.t_pred; hdr[12] = g.mc != 0 ? 1u : 0u;
+        hdr[10] = (uint32_t)g.t_ref; hdr[11] = (uint32_t)g.t_pred;
+        hdr[12] = (g.mc != 0 ? 1u : 0u) | (g.sub ? 2u : 0u);
         hdr[13] = (uint32_t)mv_mode; hdr[14] = (uint32_t)mv_b;
         hdr[15] = (uint32_t)g.n_nc; hdr[16] = (uint32_t)g.ngroups; hdr[17] = (uint32_t)nsig;
         hdr[18] = (uint32_t)nrecw; hdr[19] = (uint32_t)nmv; hdr[20] = (uint32_t)nmvw;
         hdr[21] = (uint32_t)off_roots; hdr[22] = (uint32_t)off_groups; hdr[23] = (uint32_t)off_offs;
         hdr[24] = (uint32_t)off_recs; hdr[25] = (uint32_t)off_mvs; hdr[26] = (uint32_t)total;
         for (int i = 0; i < ORC_HEADER_WORDS; i++) put_u32(s + 4 * i, hdr[i]);
-        /* roots: int16 [root][3][H][W] */
-        for (size_t i = 0; i < nroot * 3 * plane; i++) {
+        /* roots: int16, per root its Y, Co, Cg planes at their channel sizes */
+        for (size_t i = 0; i < nroot * npx; i++) {
             int16_t v = lev[L][i];
             memcpy(s + off_roots + 2 * i, &v, 2);
         }
@@ -699,18 +763,21 @@ int orc_encode(const orc_params *P, const uint8_t *lf, uint8_t **out, size_t *ou
         uint64_t mv_cursor = 0;
         for (int64_t nc = 0; nc < g.n_nc; nc++) {
             nc_out *o = &ncs[nc];
+            const geom gc = chan_geom(&g, chan_of(nc));
+            /* ngroups groups per node-channel (the luma block count); a chroma
+             * node-channel with fewer blocks leaves its last groups empty */
             for (int gi = 0; gi < g.ngroups; gi++) {
                 uint32_t bitmap = 0;
                 uint64_t gbase = rec_cursor, obase = sig_cursor;
                 for (int r = 0; r < 32; r++) {
                     int k = gi * 32 + r;
-                    if (k >= g.nblocks || !o->sig[k]) continue;
+                    if (k >= gc.nblocks || !o->sig[k]) continue;
                     bitmap |= 1u << r;
                     /* record length from its header */
                     uint32_t h0 = o->rec[o->roff[k]];
                     int md = (int)((h0 >> 21) & 3u), bb = (int)((h0 >> 16) & 31u);
                     int x0, y0, bw, bh;
-                    block_rect(&g, k, &x0, &y0, &bw, &bh);
+                    block_rect(&gc, k, &x0, &y0, &bw, &bh);
                     uint64_t len = 1 + (orc_bise_bits(md, bb, (uint64_t)bw * bh) + 31) / 32;
                     uint64_t rel = rec_cursor - gbase;
                     if (rel > 0xFFFFu) { free(s); free(mvbuf); free(mvvals); rc = ORC_E_RANGE; goto done; }
@@ -727,7 +794,7 @@ int orc_encode(const orc_params *P, const uint8_t *lf, uint8_t **out, size_t *ou
                 put_u32(ge + 12, 0);
             }
             if (o->mvsym)
-                for (int k = 0; k < g.nblocks; k++) mvvals[mv_cursor++] = o->mvsym[k];
+                for (int k = 0; k < gc.nblocks; k++) mvvals[mv_cursor++] = o->mvsym[k];
         }
         if (nmv) {
             orc_bise_pack(mvbuf, mv_mode, mv_b, mvvals, nmv);
@@ -762,13 +829,13 @@ typedef struct {
     const uint16_t *offs;
     const uint32_t *recs;
     const uint32_t *mvs;
-    int64_t *mv_rank; /* [n_nc]: predictive rank or -1 */
+    int64_t *mv_base; /* [n_nc]: index of the node-channel's first MV symbol, -1 for a reference */
 } orc_stream;
 
 void orc_close(orc_stream *s) {
     if (!s) return;
     free(s->bytes);
-    free(s->mv_rank);
+    free(s->mv_base);
     free(s);
 }
 
@@ -779,8 +846,9 @@ int orc_open(const uint8_t *bytes, size_t n, orc_stream **out) {
     if (h[0] != ORC_MAGIC || h[1] != ORC_VERSION) return ORC_E_CORRUPT;
     orc_stream *s = (orc_stream *)calloc(1, sizeof(orc_stream));
     if (!s) return ORC_E_OOM;
-    if (h[2] > 65536 || h[3] > 65536 || h[4] > 65536 || h[5] > 65536 || h[6] > 30 || h[7] > 64 ||
-        make_geom(&s->g, (int)h[2], (int)h[3], (int)h[4], (int)h[5], (int)h[6], (int)h[7]) != ORC_OK) {
+    if (h[2] > 65536 || h[3] > 65536 || h[4] > 65536 || h[5] > 65536 || h[6] > 30 || h[7] > 64 || (h[12] & ~3u) ||
+        make_geom(&s->g, (int)h[2], (int)h[3], (int)h[4], (int)h[5], (int)h[6], (int)h[7], (int)((h[12] >> 1) & 1u)) !=
+            ORC_OK) {
         free(s); return ORC_E_CORRUPT;
     }
     s->g.Ws = (int)h[8]; s->g.q = (int)h[9]; s->g.t_ref = (int)h[10]; s->g.t_pred = (int)h[11];
@@ -788,20 +856,19 @@ int orc_open(const uint8_t *bytes, size_t n, orc_stream **out) {
     s->mv_mode = (int)h[13]; s->mv_b = (int)h[14];
     s->n_sig = h[17]; s->n_recw = h[18]; s->n_mv = h[19]; s->n_mvw = h[20];
     const geom *g = &s->g;
-    size_t plane = (size_t)g->W * g->H;
     size_t nroot = (size_t)g->gu[g->L] * g->gv[g->L];
     int bad = 0;
     if (s->g.q < 1 || h[8] > 64 || h[15] != (uint32_t)g->n_nc || h[16] != (uint32_t)g->ngroups) bad = 1;
     if (h[26] != n) bad = 1;
-    if (h[21] + nroot * 3 * plane * 2 > n) bad = 1;
+    if (h[21] + nroot * g->npx * 2 > n) bad = 1;
     if (h[22] + (uint64_t)g->n_nc * g->ngroups * 16 > n) bad = 1;
     if (h[23] + (uint64_t)s->n_sig * 2 > n || h[24] + (uint64_t)s->n_recw * 4 > n ||
         h[25] + (uint64_t)s->n_mvw * 4 > n) bad = 1;
     if ((h[21] | h[22] | h[23] | h[24] | h[25]) & 3u) bad = 1;
     if (bad) { free(s); return ORC_E_CORRUPT; }
     s->bytes = (uint8_t *)malloc(n);
-    s->mv_rank = (int64_t *)malloc((size_t)g->n_nc * sizeof(int64_t));
-    if (!s->bytes || !s->mv_rank) { orc_close(s); return ORC_E_OOM; }
+    s->mv_base = (int64_t *)malloc((size_t)g->n_nc * sizeof(int64_t));
+    if (!s->bytes || !s->mv_base) { orc_close(s); return ORC_E_OOM; }
     memcpy(s->bytes, bytes, n);
     s->nbytes = n;
     s->roots = (const int16_t *)(s->bytes + h[21]);
@@ -809,31 +876,32 @@ int orc_open(const uint8_t *bytes, size_t n, orc_stream **out) {
     s->offs = (const uint16_t *)(s->bytes + h[23]);
     s->recs = (const uint32_t *)(s->bytes + h[24]);
     s->mvs = (const uint32_t *)(s->bytes + h[25]);
-    int64_t npred = 0;
+    int64_t nsym = 0;          /* MV symbols before this node-channel: one per block of each predictive one */
     for (int l = g->L - 1; l >= 0; l--)
         for (int a = 0; a < g->gu[l]; a++)
             for (int b = 0; b < g->gv[l]; b++)
                 for (int c = 0; c < 3; c++) {
                     int64_t nc = nc_of(g, l, a, b, c);
-                    s->mv_rank[nc] = is_ref(a, b) ? -1 : npred++;
+                    s->mv_base[nc] = is_ref(a, b) ? -1 : nsym;
+                    if (!is_ref(a, b)) nsym += g->cnb[c];
                 }
     if (s->mcflag) {
         int md, bb;
         orc_bise_choose(mv_range(g->Ws), &md, &bb);
-        if (md != s->mv_mode || bb != s->mv_b || (uint64_t)s->n_mv != (uint64_t)npred * g->nblocks ||
+        if (md != s->mv_mode || bb != s->mv_b || (uint64_t)s->n_mv != (uint64_t)nsym ||
             (orc_bise_bits(md, bb, s->n_mv) + 31) / 32 != s->n_mvw) { orc_close(s); return ORC_E_CORRUPT; }
     } else if (s->n_mv != 0) { orc_close(s); return ORC_E_CORRUPT; }
     *out = s;
     return ORC_OK;
 }
 
-int orc_stream_info(const orc_stream *s, int32_t *info /* [16] */) {
+int orc_stream_info(const orc_stream *s, int32_t *info /* [17] */) {
     const geom *g = &s->g;
     info[0] = g->nu; info[1] = g->nv; info[2] = g->W; info[3] = g->H; info[4] = g->L;
     info[5] = g->B; info[6] = g->Ws; info[7] = g->q; info[8] = s->mcflag;
     info[9] = (int32_t)g->n_nc; info[10] = g->nblocks; info[11] = (int32_t)s->n_sig;
     info[12] = (int32_t)s->n_recw; info[13] = (int32_t)s->n_mv; info[14] = g->gu[g->L] * g->gv[g->L];
-    info[15] = (int32_t)s->nbytes;
+    info[15] = (int32_t)s->nbytes; info[16] = g->sub;
     return ORC_OK;
 }
 
@@ -854,9 +922,11 @@ static const uint32_t *find_record(const orc_stream *s, int64_t nc, int k) {
     return s->recs + ge[1] + off;
 }
 
-/* Dequantised coefficient q * level of pixel (x, y) of node-channel nc. */
+/* Dequantised coefficient q * level of pixel (x, y) of node-channel nc, in
+ * the coordinates and block grid of its channel's plane. */
 static int coef_at(const orc_stream *s, int64_t nc, int x, int y) {
-    const geom *g = &s->g;
+    const geom gc = chan_geom(&s->g, chan_of(nc));
+    const geom *g = &gc;
     int bx = x / g->B, by = y / g->B;
     int k = by * g->nbx + bx;
     const uint32_t *rec = find_record(s, nc, k);
@@ -873,7 +943,7 @@ static int coef_at(const orc_stream *s, int64_t nc, int x, int y) {
 
 static void mv_of(const orc_stream *s, int64_t nc, int k, int *mvx, int *mvy, int *sign) {
     const geom *g = &s->g;
-    uint64_t idx = (uint64_t)s->mv_rank[nc] * g->nblocks + k;
+    uint64_t idx = (uint64_t)s->mv_base[nc] + k;
     uint32_t sym = (uint32_t)orc_bise_get(s->mvs, s->mv_mode, s->mv_b, idx);
     uint32_t side = (uint32_t)(8 * g->Ws + 1);
     *sign = (sym & 1u) ? -1 : 1;
@@ -881,9 +951,11 @@ static void mv_of(const orc_stream *s, int64_t nc, int k, int *mvx, int *mvy, in
     *mvy = (int)((sym / 2u) % side) - 4 * g->Ws;
 }
 
-/* Reconstructed SRV value of node (a, b) at level l, channel c. */
+/* Reconstructed SRV value of node (a, b) at level l, channel c, at (x, y) of
+ * that channel's plane. */
 static int srv_at(const orc_stream *s, int l, int a, int b, int c, int x, int y) {
-    const geom *g = &s->g;
+    const geom gc = chan_geom(&s->g, c);
+    const geom *g = &gc;
     int64_t nc = nc_of(g, l, a, b, c);
     int r = coef_at(s, nc, x, y);
     if (is_ref(a, b) || !s->mcflag) return r;
@@ -908,14 +980,21 @@ static int srv_at(const orc_stream *s, int l, int a, int b, int c, int x, int y)
  * Progressive decoding (Sec. 1, Sec. 4: the upper levels carry what the views
  * share, the lower ones their detail) stops the sum at level lod: the value is
  * then the reconstruction of the level-lod node (i >> lod, j >> lod). */
+/* With chroma sub-sampling, Co and Cg of sample (x, y) are those of chroma
+ * pixel (x >> 1, y >> 1): nearest-pixel reconstruction (the reading fixed
+ * for Sec. 4.5's sub-sampled chroma). */
 static void sample_ycocg(const orc_stream *s, int i, int j, int x, int y, int lod, int v[3]) {
     const geom *g = &s->g;
     int L = g->L;
-    size_t plane = (size_t)g->W * g->H;
     int ra = i >> L, rb = j >> L;
-    for (int c = 0; c < 3; c++) v[c] = s->roots[(((size_t)ra * g->gv[L] + rb) * 3 + c) * plane + (size_t)y * g->W + x];
+    int cx[3], cy[3];
+    for (int c = 0; c < 3; c++) {
+        cx[c] = (g->sub && c > 0) ? x >> 1 : x;
+        cy[c] = (g->sub && c > 0) ? y >> 1 : y;
+        v[c] = s->roots[((size_t)ra * g->gv[L] + rb) * g->npx + g->coff[c] + (size_t)cy[c] * g->cW[c] + cx[c]];
+    }
     for (int l = lod; l < L; l++)
-        for (int c = 0; c < 3; c++) v[c] += srv_at(s, l, i >> l, j >> l, c, x, y);
+        for (int c = 0; c < 3; c++) v[c] += srv_at(s, l, i >> l, j >> l, c, cx[c], cy[c]);
 }
 
 static void sample_rgb(const orc_stream *s, int i, int j, int x, int y, int lod, int rgb[3]) {
@@ -961,9 +1040,11 @@ int orc_decode_samples(const orc_stream *s, const int32_t *coords, int64_t n, ui
 /* by cluster, with a sequential BISE reader (an independent path)     */
 /* ------------------------------------------------------------------ */
 
-/* Decode all dequantised coefficients of node-channel nc into plane[H][W]. */
+/* Decode all dequantised coefficients of node-channel nc into plane[H][W]
+ * (its channel's plane size). */
 static int decode_plane_seq(const orc_stream *s, int64_t nc, int32_t *plane) {
-    const geom *g = &s->g;
+    const geom gc = chan_geom(&s->g, chan_of(nc));
+    const geom *g = &gc;
     uint32_t vals[64 * 64];
     for (int k = 0; k < g->nblocks; k++) {
         int x0, y0, bw, bh;
@@ -989,18 +1070,21 @@ static int decode_plane_seq(const orc_stream *s, int64_t nc, int32_t *plane) {
     return ORC_OK;
 }
 
-/* out: uint8 [nu][nv][H][W][3]; if ycocg != NULL also int32 [nu][nv][3][H][W]. */
+/* out: uint8 [nu][nv][H][W][3]; if ycocg != NULL also int32 [nu][nv][3][H][W]
+ * (with chroma sub-sampling, Co and Cg at (x, y) are those of chroma pixel
+ * (x >> 1, y >> 1)). */
 int orc_decode_all(const orc_stream *s, uint8_t *out, int32_t *ycocg) {
     const geom *g = &s->g;
-    const int L = g->L, W = g->W, H = g->H;
-    const size_t plane = (size_t)W * H;
+    const int L = g->L, W = g->W;
+    const size_t plane = (size_t)W * g->H, npx = g->npx;
     int rc = ORC_OK;
-    int32_t *cur = (int32_t *)malloc((size_t)g->gu[L] * g->gv[L] * 3 * plane * sizeof(int32_t));
+    /* level reconstructions, [node][npx] (channel c's plane at coff[c]) */
+    int32_t *cur = (int32_t *)malloc((size_t)g->gu[L] * g->gv[L] * npx * sizeof(int32_t));
     if (!cur) return ORC_E_OOM;
-    for (size_t i = 0; i < (size_t)g->gu[L] * g->gv[L] * 3 * plane; i++) cur[i] = s->roots[i];
+    for (size_t i = 0; i < (size_t)g->gu[L] * g->gv[L] * npx; i++) cur[i] = s->roots[i];
     for (int l = L - 1; l >= 0 && rc == ORC_OK; l--) {
         int gu = g->gu[l], gv = g->gv[l], pu = g->gu[l + 1], pv = g->gv[l + 1];
-        int32_t *nxt = (int32_t *)malloc((size_t)gu * gv * 3 * plane * sizeof(int32_t));
+        int32_t *nxt = (int32_t *)malloc((size_t)gu * gv * npx * sizeof(int32_t));
         if (!nxt) { rc = ORC_E_OOM; break; }
         #pragma omp parallel for collapse(2) schedule(dynamic, 1)
         for (int A = 0; A < pu; A++)
@@ -1010,33 +1094,35 @@ int orc_decode_all(const orc_stream *s, uint8_t *out, int32_t *ycocg) {
                 int16_t *ref16 = (int16_t *)malloc(plane * sizeof(int16_t));
                 if (!refp || !srv || !ref16) { free(refp); free(srv); free(ref16); rc = ORC_E_OOM; continue; }
                 for (int c = 0; c < 3; c++) {
-                    const int32_t *par = cur + (((size_t)A * pv + Bn) * 3 + c) * plane;
+                    const geom gc = chan_geom(g, c);
+                    const size_t cpl = (size_t)gc.W * gc.H;
+                    const int32_t *par = cur + ((size_t)A * pv + Bn) * npx + g->coff[c];
                     /* the cluster's reference member first */
                     int ra = 2 * A, rb = 2 * Bn;
                     if (decode_plane_seq(s, nc_of(g, l, ra, rb, c), refp) != ORC_OK) rc = ORC_E_CORRUPT;
-                    for (size_t p = 0; p < plane; p++) ref16[p] = (int16_t)refp[p];
+                    for (size_t p = 0; p < cpl; p++) ref16[p] = (int16_t)refp[p];
                     for (int da = 0; da < 2; da++)
                         for (int db = 0; db < 2; db++) {
                             int a = 2 * A + da, b = 2 * Bn + db;
                             if (a >= gu || b >= gv) continue;
                             int64_t nc = nc_of(g, l, a, b, c);
                             if (da == 0 && db == 0) {
-                                memcpy(srv, refp, plane * sizeof(int32_t));
+                                memcpy(srv, refp, cpl * sizeof(int32_t));
                             } else {
                                 if (decode_plane_seq(s, nc, srv) != ORC_OK) rc = ORC_E_CORRUPT;
                                 if (s->mcflag) {
-                                    for (int k = 0; k < g->nblocks; k++) {
+                                    for (int k = 0; k < gc.nblocks; k++) {
                                         int mvx, mvy, sign, x0, y0, bw, bh;
                                         mv_of(s, nc, k, &mvx, &mvy, &sign);
-                                        block_rect(g, k, &x0, &y0, &bw, &bh);
+                                        block_rect(&gc, k, &x0, &y0, &bw, &bh);
                                         for (int y = y0; y < y0 + bh; y++)
                                             for (int x = x0; x < x0 + bw; x++)
-                                                srv[y * W + x] += sign * orc_pred_qpel(ref16, W, H, x, y, mvx, mvy);
+                                                srv[y * gc.W + x] += sign * orc_pred_qpel(ref16, gc.W, gc.H, x, y, mvx, mvy);
                                     }
                                 }
                             }
-                            int32_t *dst = nxt + (((size_t)a * gv + b) * 3 + c) * plane;
-                            for (size_t p = 0; p < plane; p++) dst[p] = par[p] + srv[p];
+                            int32_t *dst = nxt + ((size_t)a * gv + b) * npx + g->coff[c];
+                            for (size_t p = 0; p < cpl; p++) dst[p] = par[p] + srv[p];
                         }
                 }
                 free(refp); free(srv); free(ref16);
@@ -1047,16 +1133,24 @@ int orc_decode_all(const orc_stream *s, uint8_t *out, int32_t *ycocg) {
     if (rc == ORC_OK) {
         for (int i = 0; i < g->nu; i++)
             for (int j = 0; j < g->nv; j++) {
-                const int32_t *src = cur + ((size_t)i * g->nv + j) * 3 * plane;
-                if (ycocg) memcpy(ycocg + ((size_t)i * g->nv + j) * 3 * plane, src, 3 * plane * sizeof(int32_t));
-                for (size_t p = 0; p < plane; p++) {
-                    int r, gg, b;
-                    orc_ycocg_to_rgb(src[p], src[plane + p], src[2 * plane + p], &r, &gg, &b);
-                    uint8_t *o = out + (((size_t)i * g->nv + j) * plane + p) * 3;
-                    o[0] = (uint8_t)clampi(r, 0, 255);
-                    o[1] = (uint8_t)clampi(gg, 0, 255);
-                    o[2] = (uint8_t)clampi(b, 0, 255);
-                }
+                const int32_t *src = cur + ((size_t)i * g->nv + j) * npx;
+                for (int y = 0; y < g->H; y++)
+                    for (int x = 0; x < W; x++) {
+                        int v[3];
+                        for (int c = 0; c < 3; c++) {
+                            int xc = (g->sub && c > 0) ? x >> 1 : x, yc = (g->sub && c > 0) ? y >> 1 : y;
+                            v[c] = src[g->coff[c] + (size_t)yc * g->cW[c] + xc];
+                        }
+                        size_t p = (size_t)y * W + x;
+                        if (ycocg)
+                            for (int c = 0; c < 3; c++) ycocg[(((size_t)i * g->nv + j) * 3 + c) * plane + p] = v[c];
+                        int r, gg, b;
+                        orc_ycocg_to_rgb(v[0], v[1], v[2], &r, &gg, &b);
+                        uint8_t *o = out + (((size_t)i * g->nv + j) * plane + p) * 3;
+                        o[0] = (uint8_t)clampi(r, 0, 255);
+                        o[1] = (uint8_t)clampi(gg, 0, 255);
+                        o[2] = (uint8_t)clampi(b, 0, 255);
+                    }
             }
     }
     free(cur);
@@ -1067,11 +1161,11 @@ int orc_decode_all(const orc_stream *s, uint8_t *out, int32_t *ycocg) {
  * for references or streams without motion compensation). */
 int orc_block_info(const orc_stream *s, int64_t nc, int k, int32_t *out4) {
     const geom *g = &s->g;
-    if (nc < 0 || nc >= g->n_nc || k < 0 || k >= g->nblocks) return ORC_E_ARG;
+    if (nc < 0 || nc >= g->n_nc || k < 0 || k >= g->cnb[chan_of(nc)]) return ORC_E_ARG;
     const uint32_t *ge = s->groups + ((size_t)nc * g->ngroups + k / 32) * 4;
     out4[0] = (ge[0] >> (k % 32)) & 1u;
     out4[1] = 0; out4[2] = 0; out4[3] = 1;
-    if (s->mcflag && s->mv_rank[nc] >= 0) mv_of(s, nc, k, &out4[1], &out4[2], &out4[3]);
+    if (s->mcflag && s->mv_base[nc] >= 0) mv_of(s, nc, k, &out4[1], &out4[2], &out4[3]);
     return ORC_OK;
 }
 
@@ -1079,6 +1173,7 @@ int orc_block_info(const orc_stream *s, int64_t nc, int k, int32_t *out4) {
  * float64 -- the starting point of the differentiable relaxation. */
 int orc_dequant(const orc_stream *s, double *coeff /* [n_nc][H][W] */, double *roots /* [nroot][3][H][W] */) {
     const geom *g = &s->g;
+    if (g->sub) return ORC_E_ARG;          /* the relaxation is defined on full-resolution chroma only */
     size_t plane = (size_t)g->W * g->H;
     int32_t *tmp = (int32_t *)malloc(plane * sizeof(int32_t));
     if (!tmp) return ORC_E_OOM;
@@ -1254,6 +1349,7 @@ static void relax_sample(const orc_stream *s, const double *coeff, const double 
 int orc_relax_render(const orc_stream *s, const double *coeff, const double *roots, const orc_view *views,
                      int nviews, double *out) {
     const geom *g = &s->g;
+    if (g->sub) return ORC_E_ARG;          /* the relaxation is defined on full-resolution chroma only */
     for (int vi = 0; vi < nviews; vi++) {
         const orc_view *v = &views[vi];
         double *o = out + v->out_offset;
@@ -1284,6 +1380,7 @@ int orc_relax_render(const orc_stream *s, const double *coeff, const double *roo
 int orc_relax_adjoint(const orc_stream *s, const orc_view *views, int nviews, const double *grad_out,
                       double *grad_coeff, double *grad_roots) {
     const geom *g = &s->g;
+    if (g->sub) return ORC_E_ARG;          /* the relaxation is defined on full-resolution chroma only */
     size_t plane = (size_t)g->W * g->H;
     int L = g->L;
     for (int vi = 0; vi < nviews; vi++) {
@@ -1336,7 +1433,7 @@ int orc_relax_adjoint(const orc_stream *s, const orc_view *views, int nviews, co
 /* (compulsory traffic) plus its FP32 output, per view                  */
 /* ------------------------------------------------------------------ */
 
-/* bytes[v] = W*H*12 (output) + 6 per unique root pixel + per unique touched
+/* bytes[v] = W*H*12 (output) + 2 per unique root pixel of each channel plane + per unique touched
  * predictive block (16 per unique group entry, 2 + 4*record words if
  * significant, MV bits/8) + per unique touched significant reference block
  * (B*B*2 resident tile + 4 table entry). */
@@ -1345,14 +1442,13 @@ int orc_relax_adjoint(const orc_stream *s, const orc_view *views, int nviews, co
 int orc_touched_bytes_lod(const orc_stream *s, const orc_view *views, int nviews, int lod, double *bytes) {
     const geom *g = &s->g;
     if (lod < 0 || lod > g->L) return ORC_E_ARG;
-    size_t plane = (size_t)g->W * g->H;
     size_t nroot = (size_t)g->gu[g->L] * g->gv[g->L];
     size_t nb_all = (size_t)g->n_nc * g->nblocks;
     double mv_bits = 0;
     if (s->mcflag) mv_bits = (double)orc_bise_bits(s->mv_mode, s->mv_b, 15) / 15.0;
     for (int vi = 0; vi < nviews; vi++) {
         const orc_view *v = &views[vi];
-        uint8_t *root_seen = (uint8_t *)calloc(nroot * plane, 1);
+        uint8_t *root_seen = (uint8_t *)calloc(nroot * g->npx, 1);
         uint8_t *blk_seen = (uint8_t *)calloc(nb_all, 1);
         uint8_t *grp_seen = (uint8_t *)calloc((size_t)g->n_nc * g->ngroups, 1);
         if (!root_seen || !blk_seen || !grp_seen) { free(root_seen); free(blk_seen); free(grp_seen); return ORC_E_OOM; }
@@ -1365,13 +1461,18 @@ int orc_touched_bytes_lod(const orc_stream *s, const orc_view *views, int nviews
                     for (int b = 0; b < 2; b++)
                         for (int xs = 0; xs < 2; xs++)
                             for (int ys = 0; ys < 2; ys++) {
-                                int i = (r.i[a] >> lod) << lod, j = (r.j[b] >> lod) << lod, x = r.x[xs], y = r.y[ys];
-                                size_t rp = ((size_t)(i >> g->L) * g->gv[g->L] + (j >> g->L)) * plane + (size_t)y * g->W + x;
-                                if (!root_seen[rp]) { root_seen[rp] = 1; acc += 6.0; }
-                                int k = (y / g->B) * g->nbx + x / g->B;
-                                for (int l = lod; l < g->L; l++) {
-                                    int na = i >> l, nb = j >> l;
-                                    for (int c = 0; c < 3; c++) {
+                                int i = (r.i[a] >> lod) << lod, j = (r.j[b] >> lod) << lod;
+                                for (int c = 0; c < 3; c++) {
+                                    /* the sample's pixel in channel c's plane (half resolution for sub-sampled chroma) */
+                                    const geom gc = chan_geom(g, c);
+                                    int x = (g->sub && c > 0) ? r.x[xs] >> 1 : r.x[xs];
+                                    int y = (g->sub && c > 0) ? r.y[ys] >> 1 : r.y[ys];
+                                    size_t rp = ((size_t)(i >> g->L) * g->gv[g->L] + (j >> g->L)) * g->npx + g->coff[c] +
+                                                (size_t)y * gc.W + x;
+                                    if (!root_seen[rp]) { root_seen[rp] = 1; acc += 2.0; }
+                                    int k = (y / g->B) * gc.nbx + x / g->B;
+                                    for (int l = lod; l < g->L; l++) {
+                                        int na = i >> l, nb = j >> l;
                                         int64_t nc = nc_of(g, l, na, nb, c);
                                         if (is_ref(na, nb)) {
                                             size_t key = (size_t)nc * g->nblocks + k;
@@ -1389,7 +1490,7 @@ int orc_touched_bytes_lod(const orc_stream *s, const orc_view *views, int nviews
                                             const uint32_t *rec = find_record(s, nc, k);
                                             if (rec) {
                                                 int x0, y0, bw, bh;
-                                                block_rect(g, k, &x0, &y0, &bw, &bh);
+                                                block_rect(&gc, k, &x0, &y0, &bw, &bh);
                                                 int md = (int)((rec[0] >> 21) & 3u), bb = (int)((rec[0] >> 16) & 31u);
                                                 acc += 2.0 + 4.0 * (1 + (orc_bise_bits(md, bb, (uint64_t)bw * bh) + 31) / 32);
                                             }
@@ -1399,10 +1500,10 @@ int orc_touched_bytes_lod(const orc_stream *s, const orc_view *views, int nviews
                                             int mvx, mvy, sign, tx[4], ty[4];
                                             double tw[4];
                                             mv_of(s, nc, k, &mvx, &mvy, &sign);
-                                            relax_taps(g, x, y, mvx, mvy, tx, ty, tw);
+                                            relax_taps(&gc, x, y, mvx, mvy, tx, ty, tw);
                                             int64_t rnc = nc_of(g, l, na & ~1, nb & ~1, c);
                                             for (int t = 0; t < 4; t++) {
-                                                int kk = (ty[t] / g->B) * g->nbx + tx[t] / g->B;
+                                                int kk = (ty[t] / g->B) * gc.nbx + tx[t] / g->B;
                                                 size_t rk = (size_t)rnc * g->nblocks + kk;
                                                 if (!blk_seen[rk]) {
                                                     blk_seen[rk] = 1;

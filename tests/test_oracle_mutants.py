@@ -1,5 +1,6 @@
 """Each test plants one plausible mistake in a copy of the oracle's C source,
-builds it on the CPU, and checks that the pins catch it.  A mistake that is
+builds it on the CPU, and checks that the pins catch it.  Every planted
+mistake keeps the oracle's reads in bounds, so a copy never crashes.  A mistake that is
 consistent between the encoder and the decoder (a swapped motion-vector axis,
 transposed bilinear taps) still round-trips losslessly, so these show which
 pin stands guard over it."""
@@ -26,8 +27,8 @@ MUTANTS = {
     "bise_trit_radix": ("            packed += (val >> b) * mul;\n            mul *= radix;",
                         "            packed += (val >> b) * mul;\n            mul *= radix + 1;",
                         ["bise_golden"]),
-    "decoder_node_axes": ("v[c] += srv_at(s, l, i >> l, j >> l, c, x, y);",
-                          "v[c] += srv_at(s, l, j >> l, i >> l, c, x, y);",
+    "decoder_node_axes": ("v[c] += srv_at(s, l, i >> l, j >> l, c, cx[c], cy[c]);",
+                          "v[c] += srv_at(s, l, j >> l, i >> l, c, cx[c], cy[c]);",
                           ["random_access"]),
     "mv_symbol_axes": ("*mvx = (int)((sym / 2u) / side) - 4 * g->Ws;\n    *mvy = (int)((sym / 2u) % side) - 4 * g->Ws;",
                        "*mvy = (int)((sym / 2u) / side) - 4 * g->Ws;\n    *mvx = (int)((sym / 2u) % side) - 4 * g->Ws;",
@@ -36,8 +37,8 @@ MUTANTS = {
                                ["render_grid"]),
     "adjoint_ycocg_transpose": ("gv[1] = 0.5 * gR - 0.5 * gB;", "gv[1] = 0.5 * gB - 0.5 * gR;",
                                 ["adjoint_dot"]),
-    "touched_root_bytes": ("if (!root_seen[rp]) { root_seen[rp] = 1; acc += 6.0; }",
-                           "if (!root_seen[rp]) { root_seen[rp] = 1; acc += 3.0; }",
+    "touched_root_bytes": ("if (!root_seen[rp]) { root_seen[rp] = 1; acc += 2.0; }",
+                           "if (!root_seen[rp]) { root_seen[rp] = 1; acc += 1.0; }",
                            ["touched"]),
     "touched_record_header_dropped": ("acc += 2.0 + 4.0 * (1 + (orc_bise_bits(md, bb, (uint64_t)bw * bh) + 31) / 32);",
                                       "acc += 2.0 + 4.0 * ((orc_bise_bits(md, bb, (uint64_t)bw * bh) + 31) / 32);",
@@ -48,6 +49,18 @@ MUTANTS = {
     "touched_tap_tile_bytes": ("if (find_record(s, rnc, kk)) acc += g->B * g->B * 2.0 + 4.0;",
                                "if (find_record(s, rnc, kk)) acc += g->B * g->B * 2.0;",
                                ["touched_sig"]),
+    "chroma_filter_rounding": ("d[(size_t)yc * g->cW[c] + xc] = (int16_t)fdiv(sum + k / 2, k);",
+                               "d[(size_t)yc * g->cW[c] + xc] = (int16_t)fdiv(sum, k);",
+                               ["chroma_closed_form"]),
+    "chroma_sample_mapping": ("cx[c] = (g->sub && c > 0) ? x >> 1 : x;",
+                              "cx[c] = (g->sub && c > 0) ? (x >> 2) << 1 : x;",
+                              ["chroma_closed_form"]),
+    "chroma_full_decode_mapping": ("int xc = (g->sub && c > 0) ? x >> 1 : x, yc = (g->sub && c > 0) ? y >> 1 : y;",
+                                   "int xc = (g->sub && c > 0) ? x >> 1 : x, yc = (g->sub && c > 0) ? (y >> 2) << 1 : y;",
+                                   ["chroma_closed_form"]),
+    "chroma_root_bytes": ("size_t rp = ((size_t)(i >> g->L) * g->gv[g->L] + (j >> g->L)) * g->npx + g->coff[c] +",
+                          "size_t rp = ((size_t)(i >> g->L) * g->gv[g->L] + (j >> g->L)) * g->npx + g->coff[0] +",
+                          ["chroma_touched"]),
     "progressive_one_level_too_deep": ("for (int l = lod; l < L; l++)", "for (int l = lod > 0 ? lod - 1 : 0; l < L; l++)",
                                        ["progressive"]),
 }
@@ -86,6 +99,10 @@ def _run(name, tiny_lf, tiny_cfg, ragged_lf):
         pins.test_touched_bytes_significant_blocks_closed_form()
     elif name == "touched_direct_and_taps":
         pins.test_touched_bytes_reference_reached_directly_and_by_taps()
+    elif name == "chroma_closed_form":
+        pins.test_chroma_420_lossless_luma_and_filter_closed_form(tiny_lf, tiny_cfg, ragged_lf, O.MC_QPEL)
+    elif name == "chroma_touched":
+        pins.test_chroma_420_touched_bytes_closed_form(tiny_cfg)
     elif name == "progressive":
         pins.test_progressive_lossless_equals_level_images(tiny_lf, tiny_cfg, ragged_lf, O.MC_QPEL)
     else:

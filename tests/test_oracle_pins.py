@@ -769,3 +769,137 @@ def test_progressive_touched_bytes_closed_form(tiny_cfg):
         assert abs(st.touched_bytes(v, level=k)[0] - 64 * 64 * 18) < 1e-6
     with pytest.raises(Exception):
         st.touched_bytes(v, level=3)
+
+
+# --------------------------------------------------------------------------
+# Sec. 4.5: chroma sub-sampling (4:2:0 stream mode)
+# --------------------------------------------------------------------------
+
+def _ycocg_planes(lf):
+    """YCoCg-R of every sample, written out from its lifting definition
+    (Co = R - B, t = B + floor(Co/2), Cg = G - t, Y = t + floor(Cg/2)):
+    int64 [..., 3]."""
+    r, g, b = (lf[..., k].astype(np.int64) for k in range(3))
+    co = r - b
+    t = b + np.floor_divide(co, 2)
+    cg = g - t
+    y = t + np.floor_divide(cg, 2)
+    return np.stack([y, co, cg], -1)
+
+
+def _subsampled(plane):
+    """The 4:2:0 reading of a chroma plane [..., H, W]: each 2x2 pixel group
+    (1-4 members at odd edges) reduced to floor((sum + floor(k/2)) / k), then
+    replicated back to every pixel of the group (nearest-pixel
+    reconstruction)."""
+    H, W = plane.shape[-2:]
+    Hc, Wc = (H + 1) // 2, (W + 1) // 2
+    pad = np.zeros(plane.shape[:-2] + (2 * Hc, 2 * Wc), np.int64)
+    cnt = np.zeros((2 * Hc, 2 * Wc), np.int64)
+    pad[..., :H, :W] = plane
+    cnt[:H, :W] = 1
+    s = pad.reshape(plane.shape[:-2] + (Hc, 2, Wc, 2)).sum(axis=(-3, -1))
+    k = cnt.reshape(Hc, 2, Wc, 2).sum(axis=(-3, -1))
+    m = np.floor_divide(s + k // 2, k)
+    return np.repeat(np.repeat(m, 2, axis=-2), 2, axis=-1)[..., :H, :W]
+
+
+def _want_ycocg_420(lf):
+    """[nu][nv][H][W][3]: Y of the input, Co and Cg of its 2x2 groups."""
+    ycc = _ycocg_planes(lf)
+    out = ycc.copy()
+    for c in (1, 2):
+        out[..., c] = _subsampled(ycc[..., c])
+    return out
+
+
+@pytest.mark.parametrize("mc", [O.MC_OFF, O.MC_QPEL, O.MC_ZERO, O.MC_INTEGER])
+def test_chroma_420_lossless_luma_and_filter_closed_form(tiny_lf, tiny_cfg, ragged_lf, mc):
+    """At q = 1 with no thresholds the 4:2:0 stream decodes (full decode and
+    random access) to exactly the input's Y and the rounded 2x2 means of its
+    Co and Cg, replicated over each group -- odd sizes included."""
+    c = tiny_cfg
+    for lf, L, B in ((tiny_lf, c.levels, c.block), (ragged_lf, 3, 8)):
+        st = O.Stream(O.encode(lf, L, B, c.search, 1, mc=mc, sub=1).stream)
+        assert st.sub == 1
+        want = _want_ycocg_420(lf)                               # [nu][nv][H][W][3]
+        _, ycc = st.decode_all(with_ycocg=True)                  # [nu][nv][3][H][W]
+        assert np.array_equal(np.moveaxis(ycc, 2, -1), want)
+        nu, nv, H, W = lf.shape[:4]
+        co = _all_coords(nu, nv, W, H)
+        _, ra = st.decode_samples(co, with_ycocg=True)
+        assert np.array_equal(ra, want[co[:, 0], co[:, 1], co[:, 3], co[:, 2]])
+
+
+@pytest.mark.parametrize("q", [2, 4, 8])
+def test_chroma_420_closed_loop_bound(tiny_lf, tiny_cfg, ragged_lf, q):
+    """With q > 1 every decoded Y, Co, Cg stays within floor(q/2) of the
+    4:2:0 reading of the input (the closed loop leaves only the leaf
+    quantiser's error), and random access equals the full decode."""
+    c = tiny_cfg
+    for lf, L, B in ((tiny_lf, c.levels, c.block), (ragged_lf, 3, 8)):
+        st = O.Stream(O.encode(lf, L, B, c.search, q, sub=1).stream)
+        rgb, ycc = st.decode_all(with_ycocg=True)
+        err = np.abs(np.moveaxis(ycc, 2, -1) - _want_ycocg_420(lf))
+        assert err.max() <= q // 2
+        nu, nv, H, W = lf.shape[:4]
+        co = _all_coords(nu, nv, W, H)
+        assert np.array_equal(st.decode_samples(co), rgb[co[:, 0], co[:, 1], co[:, 3], co[:, 2]])
+
+
+def test_chroma_420_stream_layout(tiny_lf, tiny_cfg, ragged_lf):
+    """Header flag bit 1 marks the mode; the root section holds, per root,
+    H x W luma and two ceil(H/2) x ceil(W/2) chroma planes of int16; the MV
+    sequence has one symbol per block of each predictive node-channel at its
+    channel's block grid; and the 4:2:0 stream is the smaller one."""
+    c = tiny_cfg
+    for lf, L, B in ((tiny_lf, c.levels, c.block), (ragged_lf, 3, 8)):
+        nu, nv, H, W = lf.shape[:4]
+        d420 = O.encode(lf, L, B, c.search, 4, sub=1).stream
+        d444 = O.encode(lf, L, B, c.search, 4).stream
+        h = np.frombuffer(d420[:128], np.uint32)
+        assert h[12] == 3                                        # MC on, chroma sub-sampled
+        roots = ((nu + (1 << L) - 1) >> L) * ((nv + (1 << L) - 1) >> L)
+        Hc, Wc = (H + 1) // 2, (W + 1) // 2
+        root_bytes = roots * (H * W + 2 * Hc * Wc) * 2
+        assert h[21] + root_bytes <= h[22] < h[21] + root_bytes + 16
+        nb = lambda w, hh: ((w + B - 1) // B) * ((hh + B - 1) // B)
+        n_pred = sum(((nu + (1 << l) - 1) >> l) * ((nv + (1 << l) - 1) >> l) -
+                     (((nu + (1 << l) - 1) >> l) + 1) // 2 * ((((nv + (1 << l) - 1) >> l) + 1) // 2)
+                     for l in range(L))
+        assert h[19] == n_pred * (nb(W, H) + 2 * nb(Wc, Hc))
+        assert len(d420) < len(d444)
+
+
+def test_chroma_420_touched_bytes_closed_form(tiny_cfg):
+    """The identical-views field of the 4:4:4 closed form, coded 4:2:0 and
+    seen from camera (0, 0) with (s, t) on pixel centres: 12 B per output
+    pixel + 2 B per luma root pixel (64 x 64) + 2 B per chroma root pixel
+    (2 x 32 x 32) + for each of the 3 predictive level-0 nodes its luma
+    (2 groups, 64 blocks) and two chroma node-channels (1 group, 16 blocks
+    each): 16 B per group entry and the MV bits of every block."""
+    c = tiny_cfg
+    one = S.make_lf(7, 1, 1, 64, 64, 3, 0.0, "noise_gradient")[0, 0]
+    lf = np.broadcast_to(one, (4, 4, 64, 64, 3)).copy()
+    st = O.Stream(O.encode(lf, c.levels, c.block, c.search, 4, sub=1).stream)
+    v = _one(S.grid_view(0.0, 0.0, 0.0, 0.0, 64, 64))
+    mode, b = O.bise_choose(2 * (8 * c.search + 1) ** 2)
+    mv_bits = O.bise_bits(mode, b, 15) / 15.0
+    want = (64 * 64 * 12 + 64 * 64 * 2 + 2 * 32 * 32 * 2 + 3 * (2 + 1 + 1) * 16 +
+            3 * (64 + 16 + 16) * mv_bits / 8.0)
+    assert abs(st.touched_bytes(v)[0] - want) < 1e-6
+
+
+def test_chroma_420_render_equals_dense_render(tiny_lf, tiny_cfg):
+    """The random-access render of a 4:2:0 stream equals the FP64 dense
+    render of its full decode (the render sees decoded RGB8 samples only)."""
+    c = tiny_cfg
+    st = O.Stream(O.encode(tiny_lf, c.levels, c.block, c.search, 4, sub=1).stream)
+    geo = S.lf_geometry(c.nu, c.nv, c.width, c.height)
+    views = S.views_to_array(S.random_views(17, geo, 3, [(40, 36)]))
+    dense = O.render_dense(st.decode_all(), views)
+    rng = np.random.default_rng(18)
+    pix = np.stack([rng.integers(0, 3, 600), rng.integers(0, 40, 600), rng.integers(0, 36, 600)], -1).astype(np.int32)
+    got = st.render_pixels(views, pix)
+    idx = (views["out_offset"][pix[:, 0]] + (pix[:, 2] * 40 + pix[:, 1]) * 3)[:, None] + np.arange(3)[None, :]
+    assert np.max(np.abs(got - dense[idx])) < 1e-12
