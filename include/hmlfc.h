@@ -34,7 +34,8 @@
  *     [2] nu  [3] nv   camera grid (u, v)      [4] W  [5] H   view size
  *     [6] L   SRV levels (tree height; roots are the level-L RKVs)
  *     [7] B   block size  [8] Ws search window (px)  [9] q quantiser step
- *     [10] T_ref [11] T_pred block thresholds  [12] flags (bit 0: MC)
+ *     [10] T_ref [11] T_pred block thresholds  [12] flags (bit 0: MC, bit 1:
+ *     chroma sub-sampled 4:2:0)
  *     [13] mv_mode [14] mv_b  BISE alphabet of the motion-vector symbols
  *     [15] n_nc node-channels  [16] groups per node-channel
  *     [17] n_sig significant blocks  [18] record words  [19] MV symbols
@@ -47,11 +48,18 @@
  *     (i, j) lies under node (i >> l, j >> l) at level l.
  *   node-channels: breadth-first from the top (Sec. 4.7): l = L-1 .. 0,
  *     nodes row-major (a major), channels Y, Co, Cg (YCoCg-R, Sec. 4.5).
- *   roots: int16 [roots][3][H][W], roots row-major.
+ *   channel planes: Y is W x H; Co and Cg are W x H too, or, with flag bit
+ *     1, ceil(W/2) x ceil(H/2) (Sec. 4.5 sub-sampled chroma: the rounded mean
+ *     of each 2x2 pixel group; sample (x, y) reads chroma pixel
+ *     (x >> 1, y >> 1)).  Every plane of a channel has that channel's size
+ *     and its own B x B block grid.
+ *   roots: int16, per root (row-major) its Y, Co, Cg planes in turn.
  *   blocks: B x B raster blocks of each node-channel, k = by * nbx + bx;
  *     edge blocks are partial (bw x bh valid pixels, in-block index
  *     (y - y0) * bw + (x - x0)).
- *   groups: per node-channel and run of 32 blocks a {bitmap, record base
+ *   groups: per node-channel ceil(luma blocks / 32) groups (a sub-sampled
+ *     chroma node-channel leaves its last ones empty); per run of 32 blocks
+ *     of the node-channel's plane a {bitmap, record base
  *     word, block-offset base, 0} quadruple; bit r marks block 32g+r
  *     significant (Sec. 4.5 thresholds); its record starts at record word
  *     base + offsets[offset base + popcount(bitmap & ((1 << r) - 1))]
@@ -64,8 +72,8 @@
  *     low bits; value = hi * 2^b + low; bit k is bit k%32 of word k/32.
  *     The dequantised coefficient is q * (m + value).
  *   motion vectors: one BISE sequence (mode, b of the header) with one
- *     symbol per block of every predictive node-channel, in breadth-first
- *     order: ((mvx + 4Ws)(8Ws + 1) + (mvy + 4Ws)) * 2 + (sign < 0), mv in
+ *     symbol per block (of its channel's grid) of every predictive
+ *     node-channel, in breadth-first order: ((mvx + 4Ws)(8Ws + 1) + (mvy + 4Ws)) * 2 + (sign < 0), mv in
  *     quarter pixels within [-4Ws, 4Ws].
  *
  * Decoding one sample (Sec. 4.8.1): value_c = root_c(x, y) + sum over l of
@@ -124,6 +132,7 @@ typedef struct {
 typedef struct {
     int32_t nu, nv, width, height, levels, block, search, qstep, mc;
     int32_t n_roots;
+    int32_t chroma;         /* 1: chroma sub-sampled 4:2:0 */
     int64_t n_nc, n_blocks, n_sig, n_ref_tiles;
     int64_t stream_bytes;   /* size of the compressed stream */
     int64_t device_bytes;   /* device memory held by the stream object */
@@ -318,9 +327,12 @@ int hmlfc_dequant(const hmlfc_stream *s, float *d_coeff, float *d_root, void *cu
 /* Encoder parameters (Sec. 4.5: tree height, block size, two block
  * thresholds, search window) plus the quantiser step and the MC mode
  * (0 = none, 1 = phase-shifted with quarter-pel refinement, 2 = zero
- * motion, 3 = phase-shifted integer-pel as in the paper). */
+ * motion, 3 = phase-shifted integer-pel as in the paper).  chroma: 0 = Co and
+ * Cg at full resolution; 1 = sub-sampled 4:2:0 (Sec. 4.5: Co and Cg coded at
+ * ceil(W/2) x ceil(H/2), each the rounded mean of a 2x2 pixel group, decoded
+ * by nearest-pixel reconstruction; needs an even block size). */
 typedef struct {
-    int32_t levels, block, search, qstep, t_ref, t_pred, mc, threads;
+    int32_t levels, block, search, qstep, t_ref, t_pred, mc, threads, chroma;
 } hmlfc_encode_params;
 
 /*

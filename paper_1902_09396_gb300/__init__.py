@@ -43,14 +43,14 @@ assert C.sizeof(View) == 96
 
 class StreamInfo(C.Structure):
     _fields_ = [(n, C.c_int32) for n in ("nu", "nv", "width", "height", "levels", "block", "search",
-                                          "qstep", "mc", "n_roots")] + \
+                                          "qstep", "mc", "n_roots", "chroma")] + \
                [(n, C.c_int64) for n in ("n_nc", "n_blocks", "n_sig", "n_ref_tiles", "stream_bytes",
                                          "device_bytes")]
 
 
 class EncodeParams(C.Structure):
     _fields_ = [(n, C.c_int32) for n in ("levels", "block", "search", "qstep", "t_ref", "t_pred", "mc",
-                                          "threads")]
+                                          "threads", "chroma")]
 
 
 _lib = None
@@ -334,11 +334,12 @@ def set_block_cache_bytes(n: int):
 
 
 def encode(lf: np.ndarray, levels: int, block: int, search: int, qstep: int, t_ref: int = 0, t_pred: int = 0,
-           mc: int = MC_QPEL, threads: int = 0) -> bytes:
-    """Encode uint8 [nu][nv][H][W][3] into an HMLFC stream (host threads)."""
+           mc: int = MC_QPEL, threads: int = 0, sub: int = 0) -> bytes:
+    """Encode uint8 [nu][nv][H][W][3] into an HMLFC stream (host threads);
+    sub = 1: chroma sub-sampled 4:2:0 (Sec. 4.5)."""
     lf = np.ascontiguousarray(lf, np.uint8)
     nu, nv, H, W, _ = lf.shape
-    prm = EncodeParams(levels, block, search, qstep, t_ref, t_pred, mc, threads)
+    prm = EncodeParams(levels, block, search, qstep, t_ref, t_pred, mc, threads, sub)
     out = C.c_void_p()
     n = C.c_size_t()
     _check(lib().hmlfc_encode(lf.ctypes.data_as(C.c_void_p), nu, nv, W, H, C.byref(prm), C.byref(out), C.byref(n)))
@@ -361,7 +362,7 @@ def encode_device(lf, levels: int, block: int, search: int, qstep: int, t_ref: i
         raise ValueError("lf must be uint8 [nu][nv][H][W][3]")
     lf = lf.contiguous()
     nu, nv, H, W, _ = lf.shape
-    prm = EncodeParams(levels, block, search, qstep, t_ref, t_pred, mc, 0)
+    prm = EncodeParams(levels, block, search, qstep, t_ref, t_pred, mc, 0, 0)
     out = C.c_void_p()
     n = C.c_size_t()
     st = EncodeStats()

@@ -219,7 +219,8 @@ int serialise(const Geometry &g, const std::vector<int16_t> &roots, const std::v
     uint32_t h[kHeaderWords] = {0};
     h[0] = kMagic; h[1] = kVersion; h[2] = (uint32_t)g.nu; h[3] = (uint32_t)g.nv; h[4] = (uint32_t)g.W;
     h[5] = (uint32_t)g.H; h[6] = (uint32_t)g.L; h[7] = (uint32_t)g.B; h[8] = (uint32_t)g.Ws; h[9] = (uint32_t)g.q;
-    h[10] = (uint32_t)g.t_ref; h[11] = (uint32_t)g.t_pred; h[12] = g.mc ? 1u : 0u; h[13] = (uint32_t)mv_mode;
+    h[10] = (uint32_t)g.t_ref; h[11] = (uint32_t)g.t_pred; h[12] = (g.mc ? 1u : 0u) | (g.sub ? 2u : 0u);
+    h[13] = (uint32_t)mv_mode;
     h[14] = (uint32_t)mv_b; h[15] = (uint32_t)g.n_nc; h[16] = (uint32_t)g.ngroups; h[17] = (uint32_t)nsig;
     h[18] = (uint32_t)nrecw; h[19] = (uint32_t)nmv; h[20] = (uint32_t)nmvw; h[21] = (uint32_t)o_roots;
     h[22] = (uint32_t)o_groups; h[23] = (uint32_t)o_offs; h[24] = (uint32_t)o_recs; h[25] = (uint32_t)o_mvs;
@@ -236,7 +237,7 @@ int serialise(const Geometry &g, const std::vector<int16_t> &roots, const std::v
             const uint64_t gbase = rc, obase = sc;
             for (int r = 0; r < 32; r++) {
                 const int k = gi * 32 + r;
-                if (k >= g.nblocks || !o.blocks[k].sig) continue;
+                if (k >= (int)o.blocks.size() || !o.blocks[k].sig) continue;   // the node-channel's own block grid
                 bitmap |= 1u << r;
                 const uint64_t rel = rc - gbase;
                 if (rel > 0xFFFFu) {
@@ -266,10 +267,29 @@ int serialise(const Geometry &g, const std::vector<int16_t> &roots, const std::v
 
 }  // namespace
 
-void hmlfc::fill_geometry(Geometry &g, int nu, int nv, int W, int H, int L, int B, int Ws, int q, int tr, int tp, int mc) {
+void hmlfc::fill_channels(Geometry &g) {
+    int64_t off = 0, mv = 0;
+    for (int c = 0; c < 3; c++) {
+        g.cW[c] = (g.sub && c > 0) ? (g.W + 1) / 2 : g.W;
+        g.cH[c] = (g.sub && c > 0) ? (g.H + 1) / 2 : g.H;
+        g.cnbx[c] = (g.cW[c] + g.B - 1) / g.B;
+        g.cnby[c] = (g.cH[c] + g.B - 1) / g.B;
+        g.cnb[c] = g.cnbx[c] * g.cnby[c];
+        g.coff[c] = off;
+        g.mv_coff[c] = mv;
+        off += (int64_t)g.cW[c] * g.cH[c];
+        mv += g.cnb[c];
+    }
+    g.npx = off;
+    g.mv_node = mv;
+}
+
+void hmlfc::fill_geometry(Geometry &g, int nu, int nv, int W, int H, int L, int B, int Ws, int q, int tr, int tp, int mc,
+                          int sub) {
     std::memset(&g, 0, sizeof g);
     g.nu = nu; g.nv = nv; g.W = W; g.H = H; g.L = L; g.B = B; g.Ws = Ws; g.q = q; g.t_ref = tr; g.t_pred = tp;
     g.mc = mc ? 1 : 0;
+    g.sub = sub ? 1 : 0;
     g.nbx = (W + B - 1) / B;
     g.nby = (H + B - 1) / B;
     g.nblocks = g.nbx * g.nby;
@@ -286,6 +306,7 @@ void hmlfc::fill_geometry(Geometry &g, int nu, int nv, int W, int H, int L, int 
     }
     g.n_nc = nc;
     g.n_roots = (int64_t)g.gu[L] * g.gv[L];
+    fill_channels(g);
 }
 
 extern "C" int hmlfc_encode(const uint8_t *h_lf, int nu, int nv, int W, int H, const hmlfc_encode_params *p,
@@ -295,44 +316,62 @@ extern "C" int hmlfc_encode(const uint8_t *h_lf, int nu, int nv, int W, int H, c
         return fail(HMLFC_E_INVALID_ARG, "light-field size");
     if (p->levels < 1 || p->levels > kMaxLevels || p->block < 1 || p->block > kMaxBlock || p->search < 0 ||
         p->search > 64 || p->qstep < 1 || p->qstep > kCoefLimit || p->t_ref < 0 || p->t_pred < 0 || p->mc < 0 ||
-        p->mc > 3)
+        p->mc > 3 || p->chroma < 0 || p->chroma > 1 || (p->chroma && p->block % 2 != 0))
         return fail(HMLFC_E_INVALID_ARG, "encoder parameters");
     Geometry g;
-    fill_geometry(g, nu, nv, W, H, p->levels, p->block, p->search, p->qstep, p->t_ref, p->t_pred, p->mc != 0);
+    fill_geometry(g, nu, nv, W, H, p->levels, p->block, p->search, p->qstep, p->t_ref, p->t_pred, p->mc != 0,
+                  p->chroma);
     const int L = g.L, B = g.B, q = g.q, threads = p->threads;
-    const size_t plane = (size_t)W * H;
+    const size_t plane = (size_t)W * H, npx = (size_t)g.npx;
 
-    // I_0: YCoCg-R of every view (Sec. 4.5), int16 [node][3][H][W]
+    // I_0: YCoCg-R of every view (Sec. 4.5), int16 [node][npx] with channel c's plane at coff[c]; with
+    // sub-sampled chroma, Co and Cg at ceil(W/2) x ceil(H/2), each the rounded mean of a 2x2 pixel group
     std::vector<std::vector<int16_t>> lev(L + 1);
-    lev[0].resize((size_t)nu * nv * 3 * plane);
+    lev[0].resize((size_t)nu * nv * npx);
     parallel_for((int64_t)nu * nv, threads, [&](int64_t v) {
         const uint8_t *src = h_lf + (size_t)v * plane * 3;
-        int16_t *dst = lev[0].data() + (size_t)v * 3 * plane;
+        int16_t *dst = lev[0].data() + (size_t)v * npx;
+        std::vector<int16_t> full(g.sub ? 2 * plane : 0);
+        int16_t *co_out = g.sub ? full.data() : dst + g.coff[1];
+        int16_t *cg_out = g.sub ? full.data() + plane : dst + g.coff[2];
         for (size_t px = 0; px < plane; px++) {
             const int R = src[3 * px], G = src[3 * px + 1], Bc = src[3 * px + 2];
             const int co = R - Bc;
             const int t = Bc + (co >> 1);
             const int cg = G - t;
             dst[px] = (int16_t)(t + (cg >> 1));
-            dst[plane + px] = (int16_t)co;
-            dst[2 * plane + px] = (int16_t)cg;
+            co_out[px] = (int16_t)co;
+            cg_out[px] = (int16_t)cg;
         }
+        if (g.sub)
+            for (int c = 1; c < 3; c++) {
+                const int16_t *f = full.data() + (size_t)(c - 1) * plane;
+                int16_t *d = dst + g.coff[c];
+                for (int yc = 0; yc < g.cH[c]; yc++)
+                    for (int xc = 0; xc < g.cW[c]; xc++) {
+                        int sum = 0, k = 0;
+                        for (int y = 2 * yc; y < std::min(2 * yc + 2, H); y++)
+                            for (int x = 2 * xc; x < std::min(2 * xc + 2, W); x++, k++) sum += f[(size_t)y * W + x];
+                        d[(size_t)yc * g.cW[c] + xc] = (int16_t)fdiv(sum + k / 2, k);
+                    }
+            }
     });
-    // RKVs: rounded mean of each 2x2 cluster (Sec. 4.3)
+    // RKVs: rounded mean of each 2x2 cluster (Sec. 4.3), per pixel of every channel plane
     for (int l = 0; l < L; l++) {
         const int gv = g.gv[l], pu = g.gu[l + 1], pv = g.gv[l + 1], gu = g.gu[l];
-        lev[l + 1].resize((size_t)pu * pv * 3 * plane);
+        lev[l + 1].resize((size_t)pu * pv * npx);
         parallel_for((int64_t)pu * pv * 3, threads, [&](int64_t e) {
             const int c = (int)(e % 3), node = (int)(e / 3), A = node / pv, Bn = node % pv;
+            const size_t cpl = (size_t)g.cW[c] * g.cH[c];
             const int16_t *mem[4];
             int k = 0;
             for (int da = 0; da < 2; da++)
                 for (int db = 0; db < 2; db++) {
                     const int a = 2 * A + da, b = 2 * Bn + db;
-                    if (a < gu && b < gv) mem[k++] = lev[l].data() + (((size_t)a * gv + b) * 3 + c) * plane;
+                    if (a < gu && b < gv) mem[k++] = lev[l].data() + ((size_t)a * gv + b) * npx + g.coff[c];
                 }
-            int16_t *dst = lev[l + 1].data() + (((size_t)A * pv + Bn) * 3 + c) * plane;
-            for (size_t px = 0; px < plane; px++) {
+            int16_t *dst = lev[l + 1].data() + ((size_t)A * pv + Bn) * npx + g.coff[c];
+            for (size_t px = 0; px < cpl; px++) {
                 int s = 0;
                 for (int t = 0; t < k; t++) s += mem[t][px];
                 dst[px] = (int16_t)fdiv(s + k / 2, k);
@@ -347,8 +386,8 @@ extern "C" int hmlfc_encode(const uint8_t *h_lf, int nu, int nv, int W, int H, c
     int err = HMLFC_OK;
     for (int l = L - 1; l >= 0 && err == HMLFC_OK; l--) {
         const int gu = g.gu[l], gv = g.gv[l], pv = g.gv[l + 1];
-        std::vector<int16_t> recon((size_t)gu * gv * 3 * plane);
-        std::vector<int16_t> rhat((size_t)gu * gv * 3 * plane, 0);
+        std::vector<int16_t> recon((size_t)gu * gv * npx);
+        std::vector<int16_t> rhat((size_t)gu * gv * npx, 0);
         for (int pass = 0; pass < 2; pass++) {
             std::vector<int64_t> items;
             for (int a = 0; a < gu; a++)
@@ -363,31 +402,34 @@ extern "C" int hmlfc_encode(const uint8_t *h_lf, int nu, int nv, int W, int H, c
                 const int c = (int)(e % 3), node = (int)(e / 3), a = node / gv, b = node % gv;
                 const bool ref = pass == 0;
                 const int64_t nc = g.nc_base[l] + e;
+                // every plane of channel c has that channel's size and block grid
+                const int Wc = g.cW[c], Hc = g.cH[c], nbc = g.cnb[c], nbxc = g.cnbx[c];
+                const size_t cpl = (size_t)Wc * Hc;
                 NcOut &o = ncs[nc];
-                o.blocks.assign(g.nblocks, BlockOut());
+                o.blocks.assign(nbc, BlockOut());
                 const bool use_mc = !ref && p->mc != 0;
-                if (use_mc) o.mv.assign(g.nblocks, 0u);
-                const int16_t *child = lev[l].data() + (size_t)e * plane;
-                const int16_t *par = recon_parent.data() + (((size_t)(a / 2) * pv + b / 2) * 3 + c) * plane;
-                std::vector<int32_t> S(plane);
-                for (size_t px = 0; px < plane; px++) S[px] = (int32_t)child[px] - par[px];
-                const Plane R{W, H, rhat.data() + (((size_t)(a & ~1) * gv + (b & ~1)) * 3 + c) * plane};
-                int16_t *rec_out = recon.data() + (size_t)e * plane;
-                int16_t *rhat_out = rhat.data() + (size_t)e * plane;
+                if (use_mc) o.mv.assign(nbc, 0u);
+                const int16_t *child = lev[l].data() + (size_t)node * npx + g.coff[c];
+                const int16_t *par = recon_parent.data() + ((size_t)(a / 2) * pv + b / 2) * npx + g.coff[c];
+                std::vector<int32_t> S(cpl);
+                for (size_t px = 0; px < cpl; px++) S[px] = (int32_t)child[px] - par[px];
+                const Plane R{Wc, Hc, rhat.data() + ((size_t)(a & ~1) * gv + (b & ~1)) * npx + g.coff[c]};
+                int16_t *rec_out = recon.data() + (size_t)node * npx + g.coff[c];
+                int16_t *rhat_out = rhat.data() + (size_t)node * npx + g.coff[c];
                 std::vector<int> lv((size_t)B * B), res((size_t)B * B), pr((size_t)B * B);
-                for (int k = 0; k < g.nblocks; k++) {
-                    const int x0 = (k % g.nbx) * B, y0 = (k / g.nbx) * B;
-                    const int bw = std::min(B, W - x0), bh = std::min(B, H - y0);
+                for (int k = 0; k < nbc; k++) {
+                    const int x0 = (k % nbxc) * B, y0 = (k / nbxc) * B;
+                    const int bw = std::min(B, Wc - x0), bh = std::min(B, Hc - y0);
                     int mvx = 0, mvy = 0, sign = 1;
                     if (use_mc && (p->mc == 1 || p->mc == 3))
-                        search(S.data(), R, W, H, x0, y0, bw, bh, g.Ws, p->mc == 1, mvx, mvy, sign);
+                        search(S.data(), R, Wc, Hc, x0, y0, bw, bh, g.Ws, p->mc == 1, mvx, mvy, sign);
                     int64_t energy = 0;
                     bool any = false;
                     int n = 0;
                     for (int y = y0; y < y0 + bh; y++)
                         for (int x = x0; x < x0 + bw; x++, n++) {
                             pr[n] = use_mc ? sign * qpel(R, x, y, mvx, mvy) : 0;
-                            res[n] = S[(size_t)y * W + x] - pr[n];
+                            res[n] = S[(size_t)y * Wc + x] - pr[n];
                             energy += std::abs(res[n]);
                             lv[n] = quant(res[n], q);
                             any |= lv[n] != 0;
@@ -406,10 +448,10 @@ extern "C" int hmlfc_encode(const uint8_t *h_lf, int nu, int nv, int W, int H, c
                     for (int y = y0; y < y0 + bh; y++)
                         for (int x = x0; x < x0 + bw; x++, n++) {
                             const int shat = pr[n] + (sig ? q * lv[n] : 0);
-                            const int v = par[(size_t)y * W + x] + shat;
+                            const int v = par[(size_t)y * Wc + x] + shat;
                             if (v < -32768 || v > 32767 || shat < -32768 || shat > 32767) errs[it] = HMLFC_E_UNSUPPORTED;
-                            rec_out[(size_t)y * W + x] = (int16_t)v;
-                            if (ref) rhat_out[(size_t)y * W + x] = (int16_t)shat;
+                            rec_out[(size_t)y * Wc + x] = (int16_t)v;
+                            if (ref) rhat_out[(size_t)y * Wc + x] = (int16_t)shat;
                         }
                 }
             });
@@ -427,6 +469,7 @@ extern "C" int hmlfc_encode(const uint8_t *h_lf, int nu, int nv, int W, int H, c
 extern "C" int hmlfc_requantize(const hmlfc_stream *s, const float *h_coeff, const float *h_root, void **h_out,
                                 size_t *nbytes) {
     if (!s || !h_coeff || !h_root || !h_out || !nbytes) return fail(HMLFC_E_INVALID_ARG, "NULL argument");
+    if (s->g.sub) return fail(HMLFC_E_UNSUPPORTED, "re-quantising a stream with sub-sampled chroma");
     const Geometry &g0 = s->g;
     Geometry g;
     fill_geometry(g, g0.nu, g0.nv, g0.W, g0.H, g0.L, g0.B, g0.Ws, g0.q, g0.t_ref, g0.t_pred, g0.mc);

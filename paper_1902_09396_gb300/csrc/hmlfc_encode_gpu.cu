@@ -667,6 +667,7 @@ extern "C" int hmlfc_encode_device(const uint8_t *d_lf, int nu, int nv, int W, i
         return fail(HMLFC_E_UNSUPPORTED, "device search window above %d", kMaxEncSearch);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     Geometry g;
+    if (p->chroma != 0) return fail(HMLFC_E_UNSUPPORTED, "the device encoder codes full-resolution chroma only");
     fill_geometry(g, nu, nv, W, H, p->levels, p->block, p->search, p->qstep, p->t_ref, p->t_pred, p->mc != 0);
     const int L = g.L, B = g.B;
     const int64_t plane = (int64_t)W * H, n_views = (int64_t)nu * nv;

@@ -128,9 +128,12 @@ int hmlfc::parse_header(const uint8_t *p, size_t n, Geometry &g) {
     if (h[7] < 1 || h[7] > (uint32_t)kMaxBlock) return fail(HMLFC_E_UNSUPPORTED, "block size %u", h[7]);
     if (h[8] > 64) return fail(HMLFC_E_UNSUPPORTED, "search window %u", h[8]);
     if (h[9] < 1 || h[9] > (uint32_t)kCoefLimit) return fail(HMLFC_E_UNSUPPORTED, "quantiser step %u", h[9]);
-    if (h[12] > 1) return fail(HMLFC_E_CORRUPT, "flags");
+    if (h[12] > 3) return fail(HMLFC_E_CORRUPT, "flags");
+    if ((h[12] & 2u) && (h[7] % 2) != 0) return fail(HMLFC_E_CORRUPT, "sub-sampled chroma needs an even block size");
     g.nu = (int)h[2]; g.nv = (int)h[3]; g.W = (int)h[4]; g.H = (int)h[5]; g.L = (int)h[6]; g.B = (int)h[7];
-    g.Ws = (int)h[8]; g.q = (int)h[9]; g.t_ref = (int)h[10]; g.t_pred = (int)h[11]; g.mc = (int)h[12];
+    g.Ws = (int)h[8]; g.q = (int)h[9]; g.t_ref = (int)h[10]; g.t_pred = (int)h[11];
+    g.mc = (int)(h[12] & 1u);
+    g.sub = (int)((h[12] >> 1) & 1u);
     g.mv_mode = (int)h[13]; g.mv_b = (int)h[14];
     g.nbx = (g.W + g.B - 1) / g.B;
     g.nby = (g.H + g.B - 1) / g.B;
@@ -156,6 +159,7 @@ int hmlfc::parse_header(const uint8_t *p, size_t n, Geometry &g) {
     g.n_ref_nc = rr;
     g.n_pred_nc = pr;
     g.n_roots = (int64_t)g.gu[g.L] * g.gv[g.L];
+    fill_channels(g);
     if (nc * g.nblocks >= (int64_t)INT32_MAX || (int64_t)g.W * g.H * 3 * std::max<int64_t>(nc, g.n_roots) >= (1ll << 40))
         return fail(HMLFC_E_UNSUPPORTED, "light field too large for one stream object");
     if (h[15] != (uint32_t)nc || h[16] != (uint32_t)g.ngroups) return fail(HMLFC_E_CORRUPT, "node-channel count");
@@ -167,14 +171,13 @@ int hmlfc::parse_header(const uint8_t *p, size_t n, Geometry &g) {
         int md, bb;
         bise_choose(2ull * g.side * g.side, md, bb);
         if (md != g.mv_mode || bb != g.mv_b) return fail(HMLFC_E_CORRUPT, "motion-vector alphabet");
-        if ((uint64_t)g.n_mv != (uint64_t)g.n_pred_nc * g.nblocks) return fail(HMLFC_E_CORRUPT, "motion-vector count");
+        if ((uint64_t)g.n_mv != (uint64_t)(g.n_pred_nc / 3) * g.mv_node) return fail(HMLFC_E_CORRUPT, "motion-vector count");
         if ((uint64_t)g.n_mvw != (bise_bits(md, bb, g.n_mv) + 31) / 32) return fail(HMLFC_E_CORRUPT, "motion-vector words");
     } else if (g.n_mv != 0 || g.n_mvw != 0) {
         return fail(HMLFC_E_CORRUPT, "motion vectors without motion compensation");
     }
-    const uint64_t plane = (uint64_t)g.W * g.H;
     struct Sec { uint64_t off, len; } secs[5] = {
-        {g.off_roots, (uint64_t)g.n_roots * 3 * plane * 2},
+        {g.off_roots, (uint64_t)g.n_roots * g.npx * 2},
         {g.off_groups, (uint64_t)nc * g.ngroups * 16},
         {g.off_offs, (uint64_t)g.n_sig * 2},
         {g.off_recs, (uint64_t)g.n_recw * 4},
@@ -207,8 +210,10 @@ int validate_index(const uint8_t *p, const Geometry &g, std::vector<uint32_t> &r
                     for (int gi = 0; gi < g.ngroups; gi++) {
                         const uint8_t *ge = groups + ((size_t)nc * g.ngroups + gi) * 16;
                         const uint32_t bitmap = rd32(ge), rbase = rd32(ge + 4), obase = rd32(ge + 8);
-                        const int valid = std::min(32, g.nblocks - gi * 32);
-                        if (valid < 32 && (bitmap >> valid) != 0) return fail(HMLFC_E_CORRUPT, "bitmap past the last block");
+                        // the channel's blocks (fewer for sub-sampled chroma, whose last groups stay empty)
+                        const int valid = std::max(0, std::min(32, g.cnb[c] - gi * 32));
+                        if (valid < 32 && (valid == 0 ? bitmap : bitmap >> valid) != 0)
+                            return fail(HMLFC_E_CORRUPT, "bitmap past the last block");
                         if ((uint64_t)obase != sig) return fail(HMLFC_E_CORRUPT, "block-offset base");
                         for (int r = 0; r < valid; r++) {
                             if (!((bitmap >> r) & 1u)) continue;
@@ -222,8 +227,8 @@ int validate_index(const uint8_t *p, const Geometry &g, std::vector<uint32_t> &r
                             const int mode = (int)((hdr >> 21) & 3u), bb = (int)((hdr >> 16) & 31u);
                             if (mode == 3 || bb > 16 || (hdr >> 23) != 0) return fail(HMLFC_E_CORRUPT, "record header");
                             const int k = gi * 32 + r;
-                            const int x0 = (k % g.nbx) * g.B, y0 = (k / g.nbx) * g.B;
-                            const int bw = std::min(g.B, g.W - x0), bh = std::min(g.B, g.H - y0);
+                            const int x0 = (k % g.cnbx[c]) * g.B, y0 = (k / g.cnbx[c]) * g.B;
+                            const int bw = std::min(g.B, g.cW[c] - x0), bh = std::min(g.B, g.cH[c] - y0);
                             const uint64_t words = 1 + (bise_bits(mode, bb, (uint64_t)bw * bh) + 31) / 32;
                             if (rec + words > g.n_recw) return fail(HMLFC_E_CORRUPT, "record overruns the stream");
                             const int64_t m = (int16_t)(hdr & 0xFFFFu);
@@ -540,7 +545,7 @@ int hmlfc_load_stream(const void *h_bytes, size_t nbytes, int device, void *cuda
     const int B2 = g.B * g.B;
     const uint64_t plane = (uint64_t)g.W * g.H;
     // one device allocation, carved into 256-byte aligned sections
-    const size_t sz_roots = (size_t)g.n_roots * 3 * plane * 2;
+    const size_t sz_roots = (size_t)g.n_roots * g.npx * 2;
     const size_t sz_groups = (size_t)g.n_nc * g.ngroups * 16;
     const size_t sz_offs = (size_t)g.n_sig * 2 + 4;
     const size_t sz_recs = ((size_t)g.n_recw + 2) * 4;
@@ -573,6 +578,14 @@ int hmlfc_load_stream(const void *h_bytes, size_t nbytes, int device, void *cuda
     ds.nu = g.nu; ds.nv = g.nv; ds.W = g.W; ds.H = g.H; ds.L = g.L; ds.B = g.B; ds.Ws = g.Ws; ds.q = g.q;
     ds.mc = g.mc; ds.mv_mode = g.mv_mode; ds.mv_b = g.mv_b; ds.nbx = g.nbx; ds.nby = g.nby;
     ds.nblocks = g.nblocks; ds.ngroups = g.ngroups; ds.side = g.side;
+    ds.sub = g.sub;
+    for (int c = 0; c < 3; c++) {
+        ds.cW[c] = g.cW[c]; ds.cH[c] = g.cH[c]; ds.cnbx[c] = g.cnbx[c]; ds.cnb[c] = g.cnb[c];
+        ds.roff[c] = (int)g.coff[c];
+        ds.mv_coff[c] = (int)g.mv_coff[c];
+    }
+    ds.rnpx = g.npx;
+    ds.mv_node = (int)g.mv_node;
     for (int l = 0; l <= kMaxLevels; l++) {
         ds.gu[l] = l <= g.L ? g.gu[l] : 1;
         ds.gv[l] = l <= g.L ? g.gv[l] : 1;
@@ -624,6 +637,7 @@ int hmlfc_stream_info(const hmlfc_stream *s, hmlfc_stream_info_t *out) {
     const Geometry &g = s->g;
     out->nu = g.nu; out->nv = g.nv; out->width = g.W; out->height = g.H; out->levels = g.L; out->block = g.B;
     out->search = g.Ws; out->qstep = g.q; out->mc = g.mc; out->n_roots = (int32_t)g.n_roots;
+    out->chroma = g.sub;
     out->n_nc = g.n_nc; out->n_blocks = g.nblocks; out->n_sig = g.n_sig; out->n_ref_tiles = s->n_tiles;
     out->stream_bytes = (int64_t)s->bytes.size();
     out->device_bytes = (int64_t)s->d_bytes;
@@ -693,7 +707,9 @@ int hmlfc_render_views_lod(const hmlfc_stream *const *streams, int n_streams, co
             if (rc != 1) return rc;
             path = 2;   // no scratch: per-tile staging needs none
         }
-        if (level > 0) path = 1;   // the per-tile staging decodes every level; the direct walk stops at `level`
+        // the per-tile staging decodes every level and full-resolution chroma only; the direct walk stops at
+        // `level` and reads sub-sampled chroma
+        if (level > 0 || streams[lf]->g.sub) path = 1;
         DevStream ds = streams[lf]->ds;
         ds.lod = level;
         for (size_t c = 0; c < chunks.size(); c++) {
@@ -760,7 +776,8 @@ int hmlfc_render_views_host(const hmlfc_stream *const *streams, int n_streams, c
             rc = HMLFC_OK;   // no scratch: per-tile staging needs none
         }
         for (size_t c = 0; c < chunks.size() && e == cudaSuccess; c++) {
-            e = launch_render(streams[lf]->ds, chunks[c], tiles[c], d_out, g_render_path == 1 ? 1 : 0, st);
+            const int mode = (g_render_path == 1 || streams[lf]->g.sub) ? 1 : 0;   // staging: full chroma only
+            e = launch_render(streams[lf]->ds, chunks[c], tiles[c], d_out, mode, st);
             if (e == cudaSuccess) e = sink_chunk(&sink, chunks[c], d_out, st);
         }
     }
@@ -844,8 +861,10 @@ int hmlfc_render_batch(const hmlfc_stream *const *streams, int n_streams, const 
     if (rc != HMLFC_OK) return rc;
     if (n_views > 0 && !d_out) return fail(HMLFC_E_INVALID_ARG, "d_out is NULL");
     if (n_views == 0) return HMLFC_OK;
-    for (int k = 1; k < n_streams; k++)
-        if (streams[k]->g.B != streams[0]->g.B)   // one kernel instantiation per call: equal block sizes only
+    for (int k = 0; k < n_streams; k++)
+        // one kernel instantiation per call: equal block sizes only; the batched decode reads full-resolution
+        // chroma only
+        if (streams[k]->g.B != streams[0]->g.B || streams[k]->g.sub)
             return hmlfc_render_views(streams, n_streams, h_views, n_views, d_out, cuda_stream);
     const int dev = streams[0]->device;
     DeviceGuard guard(dev);
@@ -915,6 +934,7 @@ int hmlfc_render_batch(const hmlfc_stream *const *streams, int n_streams, const 
 int hmlfc_server_create(const hmlfc_stream *s, size_t cache_bytes, void *cuda_stream, hmlfc_server **out) {
     if (!s || !out) return fail(HMLFC_E_INVALID_ARG, "NULL argument");
     *out = nullptr;
+    if (s->g.sub) return fail(HMLFC_E_UNSUPPORTED, "the serving form decodes full-resolution chroma only");
     const Geometry &g = s->g;
     DeviceGuard guard(s->device);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
@@ -1024,6 +1044,8 @@ int hmlfc_render_views_relaxed(const hmlfc_stream *const *streams, int n_streams
     NvtxRange nvtx_range("hmlfc render_views_relaxed");
     int rc = check_views(streams, n_streams, h_views, n_views);
     if (rc != HMLFC_OK) return rc;
+    for (int k = 0; k < n_streams; k++)
+        if (streams[k]->g.sub) return fail(HMLFC_E_UNSUPPORTED, "the relaxation is defined on full-resolution chroma");
     if (n_views == 0) return HMLFC_OK;
     if (!d_out || !d_coeff || !d_root) return fail(HMLFC_E_INVALID_ARG, "NULL buffer");
     DeviceGuard guard(streams[0]->device);
@@ -1046,6 +1068,8 @@ int hmlfc_render_backward(const hmlfc_stream *const *streams, int n_streams, con
     NvtxRange nvtx_range("hmlfc render_backward");
     int rc = check_views(streams, n_streams, h_views, n_views);
     if (rc != HMLFC_OK) return rc;
+    for (int k = 0; k < n_streams; k++)
+        if (streams[k]->g.sub) return fail(HMLFC_E_UNSUPPORTED, "the relaxation is defined on full-resolution chroma");
     if (n_views == 0) return HMLFC_OK;
     if (!d_grad_out || !d_grad_coeff || !d_grad_root) return fail(HMLFC_E_INVALID_ARG, "NULL buffer");
     DeviceGuard guard(streams[0]->device);
@@ -1062,6 +1086,7 @@ int hmlfc_render_backward(const hmlfc_stream *const *streams, int n_streams, con
 
 int hmlfc_dequant(const hmlfc_stream *s, float *d_coeff, float *d_root, void *cuda_stream) {
     if (!s || !d_coeff || !d_root) return fail(HMLFC_E_INVALID_ARG, "NULL argument");
+    if (s->g.sub) return fail(HMLFC_E_UNSUPPORTED, "the relaxation is defined on full-resolution chroma");
     DeviceGuard guard(s->device);
     const cudaError_t e = launch_dequant(s->ds, s->g.n_nc, d_coeff, d_root, static_cast<cudaStream_t>(cuda_stream));
     return e == cudaSuccess ? HMLFC_OK : cuda_fail(e, "dequant launch");

@@ -18,6 +18,14 @@ struct Geometry {
     int gu[kMaxLevels + 1], gv[kMaxLevels + 1];
     int64_t nc_base[kMaxLevels], ref_base[kMaxLevels], pred_base[kMaxLevels];
     int64_t n_nc, n_ref_nc, n_pred_nc, n_roots;
+    // chroma sub-sampling (Sec. 4.5): sub = 1 codes Co and Cg at ceil(W/2) x
+    // ceil(H/2); per channel its plane size and block grid, the offset of its
+    // plane within one root's planes (npx values per root), and the offset of
+    // its blocks' motion-vector symbols within one predictive node's
+    // (mv_node symbols per node)
+    int sub;
+    int cW[3], cH[3], cnbx[3], cnby[3], cnb[3];
+    int64_t coff[3], npx, mv_coff[3], mv_node;
     uint32_t n_sig, n_recw, n_mv, n_mvw;
     uint32_t off_roots, off_groups, off_offs, off_recs, off_mvs, total;
 };
@@ -57,7 +65,11 @@ inline void bise_choose(uint64_t range, int &mode, int &b) {
 
 // Geometry of a stream about to be encoded (header fields, level grids and
 // breadth-first node-channel bases; no section offsets or counts).
-void fill_geometry(Geometry &g, int nu, int nv, int W, int H, int L, int B, int Ws, int q, int tr, int tp, int mc);
+void fill_geometry(Geometry &g, int nu, int nv, int W, int H, int L, int B, int Ws, int q, int tr, int tp, int mc,
+                   int sub = 0);
+
+// The per-channel fields of g from W, H, B and sub.
+void fill_channels(Geometry &g);
 
 // Run fn(item) for item in [0, n) on up to `threads` host threads.
 void parallel_for(int64_t n, int threads, const std::function<void(int64_t)> &fn);

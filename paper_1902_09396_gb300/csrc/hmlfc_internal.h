@@ -41,6 +41,14 @@ struct DevStream {
     const int16_t *planes;          // [n_ref_nc][H][W] the same reference SRVs as dense planes (+ padding)
     uint32_t *status;               // bit 0: an out-of-range coordinate was seen
     int lod;                        // progressive decode: levels below lod are left out (0 = full decode)
+    // chroma sub-sampling (Sec. 4.5): sub = 1 codes Co and Cg at ceil(W/2) x ceil(H/2).  Per channel c:
+    // plane size, block grid, the offset of its plane in a root's planes (rnpx values per root), and the
+    // offset of its blocks' MV symbols in a predictive node's (mv_node symbols per node).  The dense
+    // reference planes keep row stride W for every channel (chroma in their top-left ceil(H/2) x ceil(W/2)).
+    int sub;
+    int cW[3], cH[3], cnbx[3], cnb[3], roff[3], mv_coff[3];
+    int mv_node;
+    int64_t rnpx;
 };
 
 // Views of one launch, by value (kernel parameter space).

@@ -142,28 +142,38 @@ struct Blk {
     __device__ __forceinline__ int size() const { return BS > 0 ? BS : B; }
 };
 
-// Resident reference coefficient R^ at (x, y) of reference node-channel row
-// `row` (= ref rank * nblocks).
+// Resident reference coefficient R^ at (x, y) of channel c's plane of
+// reference node-channel row `row` (= ref rank * nblocks).
 template <int BS>
-__device__ __forceinline__ int ref_coef(const DevStream &S, const Blk<BS> &bk, uint32_t row, int x, int y) {
+__device__ __forceinline__ int ref_coef(const DevStream &S, const Blk<BS> &bk, int c, uint32_t row, int x, int y) {
     const int bx = bk.div(x), by = bk.div(y);
     const int B = bk.size();
-    const uint32_t tile = __ldg(S.ref_tab + row + (uint32_t)(by * S.nbx + bx));
+    const uint32_t tile = __ldg(S.ref_tab + row + (uint32_t)(by * S.cnbx[c] + bx));
     return __ldg(S.tiles + (size_t)tile * (B * B) + (y - by * B) * B + (x - bx * B));
 }
 
-// Sec. 4.4 motion re-compensation with the quarter-pel bilinear predictor.
+// Sec. 4.4 motion re-compensation with the quarter-pel bilinear predictor,
+// taps clamped to channel c's plane.
 template <int BS>
-__device__ __forceinline__ int mc_pred(const DevStream &S, const Blk<BS> &bk, uint32_t row, int x, int y, int mvx,
-                                       int mvy) {
+__device__ __forceinline__ int mc_pred(const DevStream &S, const Blk<BS> &bk, int c, uint32_t row, int x, int y,
+                                       int mvx, int mvy) {
     const int X = 4 * x + mvx, Y = 4 * y + mvy;
     const int x0 = X >> 2, y0 = Y >> 2, fx = X & 3, fy = Y & 3;
-    const int xa = clampi(x0, 0, S.W - 1), xb = clampi(x0 + 1, 0, S.W - 1);
-    const int ya = clampi(y0, 0, S.H - 1), yb = clampi(y0 + 1, 0, S.H - 1);
-    const int a = ref_coef(S, bk, row, xa, ya), b = ref_coef(S, bk, row, xb, ya);
-    const int c = ref_coef(S, bk, row, xa, yb), d = ref_coef(S, bk, row, xb, yb);
-    const int s = (4 - fx) * (4 - fy) * a + fx * (4 - fy) * b + (4 - fx) * fy * c + fx * fy * d;
+    const int xa = clampi(x0, 0, S.cW[c] - 1), xb = clampi(x0 + 1, 0, S.cW[c] - 1);
+    const int ya = clampi(y0, 0, S.cH[c] - 1), yb = clampi(y0 + 1, 0, S.cH[c] - 1);
+    const int a = ref_coef(S, bk, c, row, xa, ya), b = ref_coef(S, bk, c, row, xb, ya);
+    const int cc = ref_coef(S, bk, c, row, xa, yb), d = ref_coef(S, bk, c, row, xb, yb);
+    const int s = (4 - fx) * (4 - fy) * a + fx * (4 - fy) * b + (4 - fx) * fy * cc + fx * fy * d;
     return (s + 8) >> 4;
+}
+
+// Index of the MV symbol of block k of predictive node (a, b), level l,
+// channel c: per predictive node (breadth-first) mv_node symbols, channel
+// c's blocks from mv_coff[c] (pred_rank * nblocks + k without sub-sampling).
+__device__ __forceinline__ uint64_t mv_index(const DevStream &S, const LevelTabs &T, int l, int a, int b, int c,
+                                            int k) {
+    const int pr = pred_rank(T, l, a, b, c);       // pred_base (a multiple of 3) + node * 3 + c
+    return (uint64_t)((pr - c) / 3) * (uint64_t)S.mv_node + (uint64_t)(S.mv_coff[c] + k);
 }
 
 __device__ __forceinline__ void decode_mv(const DevStream &S, uint32_t sym, int &mvx, int &mvy, int &sign) {
@@ -186,25 +196,24 @@ __device__ __forceinline__ int residual(const DevStream &S, int nc, int k, uint3
     return S.q * (m + (int)bise_get_small(S.recs + rec + 1, (hdr >> 21) & 3u, (hdr >> 16) & 31u, idx));
 }
 
-// SRV value of node (a, b) at level l, channel c, pixel (x, y), straight
-// from the index (no staging).
+// SRV value of node (a, b) at level l, channel c, at pixel (x, y) of that
+// channel's plane, straight from the index (no staging).
 template <int BS>
 __device__ int srv_direct(const DevStream &S, const LevelTabs &T, const Blk<BS> &bk, int l, int a, int b, int c, int x,
                           int y) {
     const int B = bk.size();
     const int bx = bk.div(x), by = bk.div(y);
-    const int k = by * S.nbx + bx;
-    if (is_ref(a, b)) return ref_coef(S, bk, (uint32_t)ref_rank(T, l, a, b, c) * S.nblocks, x, y);
+    const int k = by * S.cnbx[c] + bx;
+    if (is_ref(a, b)) return ref_coef(S, bk, c, (uint32_t)ref_rank(T, l, a, b, c) * S.nblocks, x, y);
     const int x0 = bx * B, y0 = by * B;
-    const int bw = min(B, S.W - x0);
+    const int bw = min(B, S.cW[c] - x0);
     const int r = residual(S, nc_index(T, l, a, b, c), k, (uint32_t)((y - y0) * bw + (x - x0)));
     if (!S.mc) return r;
-    const uint32_t sym =
-        bise_get_long(S.mvs, S.mv_mode, S.mv_b, (uint64_t)pred_rank(T, l, a, b, c) * S.nblocks + k);
+    const uint32_t sym = bise_get_long(S.mvs, S.mv_mode, S.mv_b, mv_index(S, T, l, a, b, c, k));
     int mvx, mvy, sign;
     decode_mv(S, sym, mvx, mvy, sign);
     const uint32_t row = (uint32_t)ref_rank(T, l, a & ~1, b & ~1, c) * S.nblocks;
-    return sign * mc_pred(S, bk, row, x, y, mvx, mvy) + r;
+    return sign * mc_pred(S, bk, c, row, x, y, mvx, mvy) + r;
 }
 
 __device__ __forceinline__ uint32_t ycocg_to_rgb8(int Y, int Co, int Cg) {
@@ -222,14 +231,17 @@ template <int BS>
 __device__ uint32_t sample_direct(const DevStream &S, const LevelTabs &T, const Blk<BS> &bk, int i, int j, int x,
                                   int y) {
     const int L = S.L;
-    const size_t plane = (size_t)S.W * S.H;
-    const size_t rbase = ((size_t)(i >> L) * T.gv[L] + (j >> L)) * 3 * plane + (size_t)y * S.W + x;
-    int v0 = __ldg(S.roots + rbase), v1 = __ldg(S.roots + rbase + plane), v2 = __ldg(S.roots + rbase + 2 * plane);
+    // with sub-sampled chroma, Co and Cg of (x, y) are those of chroma pixel (x >> 1, y >> 1)
+    const int xc = S.sub ? x >> 1 : x, yc = S.sub ? y >> 1 : y;
+    const size_t rbase = ((size_t)(i >> L) * T.gv[L] + (j >> L)) * (size_t)S.rnpx;
+    int v0 = __ldg(S.roots + rbase + S.roff[0] + (size_t)y * S.cW[0] + x);
+    int v1 = __ldg(S.roots + rbase + S.roff[1] + (size_t)yc * S.cW[1] + xc);
+    int v2 = __ldg(S.roots + rbase + S.roff[2] + (size_t)yc * S.cW[2] + xc);
     for (int l = S.lod; l < L; l++) {
         const int a = i >> l, b = j >> l;
         v0 += srv_direct(S, T, bk, l, a, b, 0, x, y);
-        v1 += srv_direct(S, T, bk, l, a, b, 1, x, y);
-        v2 += srv_direct(S, T, bk, l, a, b, 2, x, y);
+        v1 += srv_direct(S, T, bk, l, a, b, 1, xc, yc);
+        v2 += srv_direct(S, T, bk, l, a, b, 2, xc, yc);
     }
     return ycocg_to_rgb8(v0, v1, v2);
 }
@@ -260,14 +272,18 @@ __global__ void k_decode_tiles(const DevStream S, const uint4 *__restrict__ src,
 }
 
 // Dense copy of the resident reference SRVs for the block decode: plane r
-// (reference node-channel rank r, [H][W] int16) holds every block's tile, the
-// zero tile where the block is insignificant.  One CTA per (block, plane).
+// (reference node-channel rank r, [H][W] int16, channel r % 3) holds every
+// block's tile, the zero tile where the block is insignificant; a sub-sampled
+// chroma plane fills its top-left ceil(H/2) x ceil(W/2).  One CTA per
+// (block, plane).
 __global__ void __launch_bounds__(256) k_build_planes(const DevStream S, int n_ref, int16_t *__restrict__ planes) {
     const int k = blockIdx.x;
     const int B = S.B;
-    const int bx = k % S.nbx, by = k / S.nbx;
-    const int bw = min(B, S.W - bx * B), bh = min(B, S.H - by * B);
     for (int r = blockIdx.y; r < n_ref; r += gridDim.y) {
+        const int c = r % 3;                                     // ranks: a multiple of 3 per level + node * 3 + c
+        if (k >= S.cnb[c]) continue;
+        const int bx = k % S.cnbx[c], by = k / S.cnbx[c];
+        const int bw = min(B, S.cW[c] - bx * B), bh = min(B, S.cH[c] - by * B);
         const uint32_t tile = __ldg(S.ref_tab + (size_t)r * S.nblocks + k);
         const int16_t *src = S.tiles + (size_t)tile * B * B;
         int16_t *dst = planes + (size_t)r * S.W * S.H + (size_t)by * B * S.W + (size_t)bx * B;
@@ -663,7 +679,7 @@ __global__ void __launch_bounds__(TW *TH, 4) k_render(const __grid_constant__ De
                     }
                     if (S.mc) {
                         const uint32_t sym = bise_get_long(S.mvs, S.mv_mode, S.mv_b,
-                                                           (uint64_t)pred_rank(T, l, a, b, c) * S.nblocks + k);
+                                                           mv_index(S, T, l, a, b, c, k));
                         int mvx, mvy, sign;
                         decode_mv(S, sym, mvx, mvy, sign);
                         D.d0.z = (uint32_t)(mvx + 512) | ((uint32_t)(mvy + 512) << 10) | ((sign < 0 ? 1u : 0u) << 20);
@@ -840,7 +856,7 @@ __global__ void __launch_bounds__(256) k_relax(const __grid_constant__ DevStream
                     v[c] += coeff[(size_t)nc * plane + pix];
                     if (!is_ref(na, nb) && S.mc) {
                         const uint32_t sym = bise_get_long(S.mvs, S.mv_mode, S.mv_b,
-                                                           (uint64_t)pred_rank(T, l, na, nb, c) * S.nblocks + k);
+                                                           mv_index(S, T, l, na, nb, c, k));
                         int mvx, mvy, sign;
                         decode_mv(S, sym, mvx, mvy, sign);
                         RelaxTap t;
@@ -869,7 +885,7 @@ __global__ void __launch_bounds__(256) k_relax(const __grid_constant__ DevStream
                     atomicAdd(gcoeff + (size_t)nc * plane + pix, gv3[c]);
                     if (!is_ref(na, nb) && S.mc) {
                         const uint32_t sym = bise_get_long(S.mvs, S.mv_mode, S.mv_b,
-                                                           (uint64_t)pred_rank(T, l, na, nb, c) * S.nblocks + k);
+                                                           mv_index(S, T, l, na, nb, c, k));
                         int mvx, mvy, sign;
                         decode_mv(S, sym, mvx, mvy, sign);
                         RelaxTap t;
@@ -924,7 +940,7 @@ __global__ void __launch_bounds__(256) k_dequant(const __grid_constant__ DevStre
         const int bx = bk.div(x), by = bk.div(y);
         int v;
         if (is_ref(s_a, s_b)) {
-            v = ref_coef(S, bk, (uint32_t)ref_rank(T, s_l, s_a, s_b, s_c) * S.nblocks, x, y);
+            v = ref_coef(S, bk, s_c, (uint32_t)ref_rank(T, s_l, s_a, s_b, s_c) * S.nblocks, x, y);
         } else {
             const int bw = min(B, S.W - bx * B);
             v = residual(S, (int)row, by * S.nbx + bx, (uint32_t)((y - by * B) * bw + (x - bx * B)));
@@ -972,7 +988,7 @@ __device__ Desc make_desc(const DevStream &S, const LevelTabs &T, const Blk<BS> 
     }
     if (S.mc) {
         const uint32_t sym =
-            bise_get_long(S.mvs, S.mv_mode, S.mv_b, (uint64_t)pred_rank(T, l, a, b, c) * S.nblocks + k);
+            bise_get_long(S.mvs, S.mv_mode, S.mv_b, mv_index(S, T, l, a, b, c, k));
         int mvx, mvy, sign;
         decode_mv(S, sym, mvx, mvy, sign);
         D.d0.z = (uint32_t)(mvx + 512) | ((uint32_t)(mvy + 512) << 10) | ((sign < 0 ? 1u : 0u) << 20);
@@ -1179,13 +1195,20 @@ struct NDesc {
 };
 static_assert(sizeof(NDesc) == 32, "descriptor size");
 
+// Descriptor of luma block (bx, by)'s region in channel c of node (a, b),
+// level l.  Without sub-sampling, or for luma, the region is the block
+// itself; for sub-sampled chroma it is the (B/2) x (B/2) chroma pixels under
+// the luma block, at (bx * B/2, by * B/2) of the half-resolution plane, inside
+// chroma block (bx >> 1, by >> 1) (B is even).
 template <int BS>
 __device__ NDesc make_ndesc(const DevStream &S, const LevelTabs &T, const Blk<BS> &bk, int l, int a, int b, int c,
                             int bx, int by) {
     const int B = bk.size();
-    const int k = by * S.nbx + bx;
-    const int x0 = bx * B, y0 = by * B;
-    const size_t plane = (size_t)S.W * S.H;
+    const bool half = S.sub && c > 0;
+    const int span = half ? B / 2 : B;                         // extent of the region
+    const int k = half ? (by >> 1) * S.cnbx[c] + (bx >> 1) : by * S.nbx + bx;
+    const int x0 = bx * span, y0 = by * span;                  // region origin in the channel's plane
+    const size_t plane = (size_t)S.W * S.H;                    // dense planes keep row stride W
     NDesc D;
     D.rec = kNone;
     D.hdr = 0u;
@@ -1209,7 +1232,7 @@ __device__ NDesc make_ndesc(const DevStream &S, const LevelTabs &T, const Blk<BS
         D.flags = kDNoMC;
         return D;
     }
-    const uint32_t sym = bise_get_long(S.mvs, S.mv_mode, S.mv_b, (uint64_t)pred_rank(T, l, a, b, c) * S.nblocks + k);
+    const uint32_t sym = bise_get_long(S.mvs, S.mv_mode, S.mv_b, mv_index(S, T, l, a, b, c, k));
     int mvx, mvy, sign;
     decode_mv(S, sym, mvx, mvy, sign);
     const int fx = mvx & 3, fy = mvy & 3;     // X = 4x + mvx: floor(X / 4) = x + (mvx >> 2), X & 3 = mvx & 3
@@ -1219,8 +1242,8 @@ __device__ NDesc make_ndesc(const DevStream &S, const LevelTabs &T, const Blk<BS
     D.oy = y0 + (mvy >> 2);
     const int16_t *rp = S.planes + (size_t)ref_rank(T, l, a & ~1, b & ~1, c) * plane;
     D.flags = sign < 0 ? kDNeg : 0u;
-    // unclamped: every tap (x .. x + 2 of a pixel pair, y .. y + 1) of every pixel of the block lies in the image
-    if (D.ox >= 0 && D.oy >= 0 && D.ox + B + 1 <= S.W - 1 && D.oy + B <= S.H - 1) {
+    // unclamped: every tap (x .. x + 2 of a pixel pair, y .. y + 1) of every pixel of the region lies in the plane
+    if (D.ox >= 0 && D.oy >= 0 && D.ox + span + 1 <= S.cW[c] - 1 && D.oy + span <= S.cH[c] - 1) {
         D.base = rp + (size_t)D.oy * S.W + D.ox;
         if (fx == 0 && fy == 0) D.flags |= kDInt;
     } else {
@@ -1255,8 +1278,8 @@ __device__ __forceinline__ void bise_pair(const uint32_t *__restrict__ w, uint32
 // sign * P + r^, P the quarter-pel bilinear of the reference's R^ with
 // weights summing to 16, + 8, >> 4.
 template <int BS>
-__device__ __forceinline__ void eval_pair(const DevStream &S, const NDesc &D, int p, int xi, int yi, uint32_t idx0,
-                                          uint32_t idx1, int &o0, int &o1) {
+__device__ __forceinline__ void eval_pair(const DevStream &S, const NDesc &D, int c, int p, int xi, int yi,
+                                          uint32_t idx0, uint32_t idx1, int &o0, int &o1) {
     const uint32_t f = D.flags;
     if (f & kDRef) {
         o0 = __ldg(D.base + p);
@@ -1292,10 +1315,10 @@ __device__ __forceinline__ void eval_pair(const DevStream &S, const NDesc &D, in
             b1 = __ldg(t + 1);
             b2 = __ldg(t + 2);
         } else {
-            const int X = D.ox + xi, Y = D.oy + yi;
-            const int c0 = clampi(X, 0, S.W - 1), c1 = clampi(X + 1, 0, S.W - 1), c2 = clampi(X + 2, 0, S.W - 1);
-            const int16_t *ra = D.base + (size_t)clampi(Y, 0, S.H - 1) * S.W;
-            const int16_t *rb = D.base + (size_t)clampi(Y + 1, 0, S.H - 1) * S.W;
+            const int X = D.ox + xi, Y = D.oy + yi, Wc = S.cW[c], Hc = S.cH[c];
+            const int c0 = clampi(X, 0, Wc - 1), c1 = clampi(X + 1, 0, Wc - 1), c2 = clampi(X + 2, 0, Wc - 1);
+            const int16_t *ra = D.base + (size_t)clampi(Y, 0, Hc - 1) * S.W;
+            const int16_t *rb = D.base + (size_t)clampi(Y + 1, 0, Hc - 1) * S.W;
             a0 = __ldg(ra + c0);
             a1 = __ldg(ra + c1);
             a2 = __ldg(ra + c2);
@@ -1411,12 +1434,23 @@ __global__ void __launch_bounds__(256, 4) k_decode_blocks(const __grid_constant_
             const int p = yi * S.W + xi;
             const uint32_t idx0 = (uint32_t)(yi * bw + xi), idx1 = in1 ? idx0 + 1u : idx0;
             const int gx = bx * B + xi, gy = by * B + yi;
-            const size_t rb = ((size_t)(aK >> (L - K)) * T.gv[L] + (bK >> (L - K))) * 3 * plane + (size_t)gy * S.W + gx;
+            // sub-sampled chroma: both pixels of the pair are chroma pixel (gx >> 1, gy >> 1), at (xi >> 1,
+            // yi >> 1) of the descriptors' half-size regions, inside chroma block (bx >> 1, by >> 1)
+            const int xic = xi >> 1, yic = yi >> 1, pc = yic * S.W + xic;
+            const int bwc = min(B, S.cW[1] - (bx >> 1) * B);
+            const uint32_t idxc = (uint32_t)(((by & 1) * (B / 2) + yic) * bwc + (bx & 1) * (B / 2) + xic);
+            const size_t rb = ((size_t)(aK >> (L - K)) * T.gv[L] + (bK >> (L - K))) * (size_t)S.rnpx;
             int v0[3], v1[3];
+            v0[0] = __ldg(S.roots + rb + S.roff[0] + (size_t)gy * S.W + gx);
+            v1[0] = __ldg(S.roots + rb + S.roff[0] + (size_t)gy * S.W + gx + 1);
 #pragma unroll
-            for (int c = 0; c < 3; c++) {
-                v0[c] = __ldg(S.roots + rb + c * plane);
-                v1[c] = __ldg(S.roots + rb + c * plane + 1);
+            for (int c = 1; c < 3; c++) {
+                if (S.sub) {
+                    v0[c] = v1[c] = __ldg(S.roots + rb + S.roff[c] + (size_t)(gy >> 1) * S.cW[c] + (gx >> 1));
+                } else {
+                    v0[c] = __ldg(S.roots + rb + S.roff[c] + (size_t)gy * S.W + gx);
+                    v1[c] = __ldg(S.roots + rb + S.roff[c] + (size_t)gy * S.W + gx + 1);
+                }
             }
             const NDesc *dd = s_desc + gi * kDescPer;
             const uint32_t *slots = s_slot[gi];
@@ -1475,7 +1509,15 @@ __global__ void __launch_bounds__(256, 4) k_decode_blocks(const __grid_constant_
                 }
                 int s0[3], s1[3];
 #pragma unroll
-                for (int c = 0; c < 3; c++) eval_pair<BS>(S, d[c], p, xi, yi, idx0, idx1, s0[c], s1[c]);
+                for (int c = 0; c < 3; c++) {
+                    if (c > 0 && S.sub) {
+                        int unused;
+                        eval_pair<BS>(S, d[c], c, pc, xic, yic, idxc, idxc, s0[c], unused);
+                        s1[c] = s0[c];
+                    } else {
+                        eval_pair<BS>(S, d[c], c, p, xi, yi, idx0, idx1, s0[c], s1[c]);
+                    }
+                }
                 if (phase == 0) {
 #pragma unroll
                     for (int c = 0; c < 3; c++) {

@@ -1,7 +1,8 @@
 // Compulsory traffic of a render: the bytes a view's rays must move at least
 // once (a measurement aid for the roofline, host threads only).
 //
-// Per view: FP32 output (12 B per pixel) + 6 B per distinct root pixel + per
+// Per view: FP32 output (12 B per pixel) + 2 B per distinct root pixel of each
+// channel plane (6 B per sample without chroma sub-sampling) + per
 // distinct predictive block (16 B group entry once per group, 2 B offset and
 // the record if significant, the motion-vector symbol's bits) + per distinct
 // significant reference block reached directly or by a motion-compensation
@@ -63,8 +64,9 @@ struct Counter {
         uint16_t off;
         std::memcpy(&off, bytes + g.off_offs + 2 * ((size_t)rd32(ge + 8) + rank), 2);
         const uint32_t hdr = rd32(bytes + g.off_recs + 4 * ((size_t)rd32(ge + 4) + off));
-        const int x0 = (k % g.nbx) * g.B, y0 = (k / g.nbx) * g.B;
-        const int bw = std::min(g.B, g.W - x0), bh = std::min(g.B, g.H - y0);
+        const int c = (int)(nc % 3);                            // the node-channel's channel: its block grid
+        const int x0 = (k % g.cnbx[c]) * g.B, y0 = (k / g.cnbx[c]) * g.B;
+        const int bw = std::min(g.B, g.cW[c] - x0), bh = std::min(g.B, g.cH[c] - y0);
         return 4 * (1 + (int64_t)((bise_bits((hdr >> 21) & 3, (hdr >> 16) & 31, (uint64_t)bw * bh) + 31) / 32));
     }
 };
@@ -95,7 +97,7 @@ struct Bits {
 struct Seen {
     Bits sample, root, blk, grp;
     explicit Seen(const Geometry &g)
-        : sample((size_t)g.nu * g.nv * g.W * g.H), root((size_t)g.n_roots * g.W * g.H),
+        : sample((size_t)g.nu * g.nv * g.W * g.H), root((size_t)g.n_roots * g.npx),
           blk((size_t)g.n_nc * g.nblocks), grp((size_t)g.n_nc * g.ngroups) {}
 };
 
@@ -133,13 +135,16 @@ double count_view(const Counter &C, const hmlfc_view &V, Seen &seen, int lod = 0
                 const int x = xx[(q >> 1) & 1], y = yy[q & 1];
                 const size_t sk = ((size_t)i * g.nv + j) * plane + (size_t)y * g.W + x;
                 if (!seen.sample.set(sk)) continue;
-                const size_t rp = ((size_t)(i >> g.L) * g.gv[g.L] + (j >> g.L)) * plane + (size_t)y * g.W + x;
-                if (seen.root.set(rp)) acc += 6.0;
-                const int k = (y / g.B) * g.nbx + x / g.B;
-                for (int l = lod; l < g.L; l++) {
-                    const int a = i >> l, b = j >> l;
-                    const bool ref = (a % 2 == 0) && (b % 2 == 0);
-                    for (int c = 0; c < 3; c++) {
+                const size_t root_node = (size_t)(i >> g.L) * g.gv[g.L] + (j >> g.L);
+                for (int c = 0; c < 3; c++) {
+                    // the sample's pixel in channel c's plane (half resolution for sub-sampled chroma)
+                    const bool half = g.sub && c > 0;
+                    const int xc = half ? x >> 1 : x, yc = half ? y >> 1 : y;
+                    if (seen.root.set(root_node * g.npx + g.coff[c] + (size_t)yc * g.cW[c] + xc)) acc += 2.0;
+                    const int k = (yc / g.B) * g.cnbx[c] + xc / g.B;
+                    for (int l = lod; l < g.L; l++) {
+                        const int a = i >> l, b = j >> l;
+                        const bool ref = (a % 2 == 0) && (b % 2 == 0);
                         const int64_t nc = nc_of(l, a, b, c);
                         if (ref) {
                             touch_ref(nc, k);
@@ -153,20 +158,21 @@ double count_view(const Counter &C, const hmlfc_view &V, Seen &seen, int lod = 0
                             acc += C.mv_bits / 8.0;
                         }
                         if (!g.mc) continue;
-                        // predictive rank of (l, a, b, c) in breadth-first order
+                        // predictive node rank of (l, a, b) in breadth-first order; its symbols start at
+                        // rank * mv_node, channel c's at mv_coff[c]
                         const int gv = g.gv[l];
                         const int64_t before = (int64_t)((a + 1) / 2) * ((gv + 1) / 2) + ((a % 2 == 0) ? (b + 1) / 2 : 0);
-                        const int64_t prank = g.pred_base[l] + ((int64_t)a * gv + b - before) * 3 + c;
-                        const uint32_t sym = C.mv_symbol((uint64_t)prank * g.nblocks + k);
+                        const int64_t pnode = g.pred_base[l] / 3 + ((int64_t)a * gv + b - before);
+                        const uint32_t sym = C.mv_symbol((uint64_t)pnode * g.mv_node + g.mv_coff[c] + k);
                         const int mvx = (int)((sym >> 1) / (uint32_t)g.side) - 4 * g.Ws;
                         const int mvy = (int)((sym >> 1) % (uint32_t)g.side) - 4 * g.Ws;
-                        const int Xq = 4 * x + mvx, Yq = 4 * y + mvy;
+                        const int Xq = 4 * xc + mvx, Yq = 4 * yc + mvy;
                         const int x0 = Xq >> 2, y0 = Yq >> 2;
-                        const int xa = std::min(std::max(x0, 0), g.W - 1), xb = std::min(std::max(x0 + 1, 0), g.W - 1);
-                        const int ya = std::min(std::max(y0, 0), g.H - 1), yb = std::min(std::max(y0 + 1, 0), g.H - 1);
+                        const int xa = std::min(std::max(x0, 0), g.cW[c] - 1), xb = std::min(std::max(x0 + 1, 0), g.cW[c] - 1);
+                        const int ya = std::min(std::max(y0, 0), g.cH[c] - 1), yb = std::min(std::max(y0 + 1, 0), g.cH[c] - 1);
                         const int64_t rnc = nc_of(l, a & ~1, b & ~1, c);
                         const int tx[4] = {xa, xb, xa, xb}, ty[4] = {ya, ya, yb, yb};
-                        for (int tp = 0; tp < 4; tp++) touch_ref(rnc, (ty[tp] / g.B) * g.nbx + tx[tp] / g.B);
+                        for (int tp = 0; tp < 4; tp++) touch_ref(rnc, (ty[tp] / g.B) * g.cnbx[c] + tx[tp] / g.B);
                     }
                 }
             }

@@ -51,6 +51,21 @@ def test_encoder_matches_oracle_block_sizes(block):
         assert H.encode(lf, 2, block, 3, q, t_ref=tr, t_pred=tp, threads=4) == a
 
 
+@pytest.mark.parametrize("mc", [O.MC_OFF, O.MC_QPEL, O.MC_ZERO, O.MC_INTEGER])
+def test_encoder_matches_oracle_bytes_chroma_420(tiny_lf, tiny_cfg, ragged_lf, mc):
+    """Chroma sub-sampled 4:2:0 streams (Sec. 4.5): the product encoder
+    writes the oracle's bytes, odd image sizes and block sizes 4-32 included;
+    an odd block size is refused."""
+    c = tiny_cfg
+    for lf, L, B, q, tr, tp in [(tiny_lf, c.levels, c.block, 1, 0, 0), (tiny_lf, c.levels, c.block, 4, 0, 0),
+                                (ragged_lf, 2, 8, 4, 40, 90), (ragged_lf, 3, 4, 2, 0, 0), (ragged_lf, 1, 32, 3, 0, 0)]:
+        a = O.encode(lf, L, B, c.search, q, t_ref=tr, t_pred=tp, mc=mc, sub=1).stream
+        b = H.encode(lf, L, B, c.search, q, t_ref=tr, t_pred=tp, mc=mc, threads=3, sub=1)
+        assert a == b
+    with pytest.raises(H.HmlfcError):
+        H.encode(ragged_lf, 2, 5, c.search, 4, sub=1)
+
+
 def test_encoder_thread_count_does_not_change_output(ragged_lf):
     a = H.encode(ragged_lf, 2, 8, 4, 4, threads=1)
     b = H.encode(ragged_lf, 2, 8, 4, 4, threads=7)
