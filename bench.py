@@ -550,6 +550,18 @@ def run_study(args):
                 "nonzero_coefficients": nnz, "block_sparse_bytes": tiles, "csr_bytes": csr,
                 "dense_bytes": len(ref_nc) * c.width * c.height * 2}
 
+    def point420(q, tr=0, tp=0):
+        """Quarter-pel HMLFC with chroma sub-sampled 4:2:0 (Sec. 4.5), from the
+        host encoder (the device encoder codes full-resolution chroma only)."""
+        t0 = time.perf_counter()
+        data = H.encode(lf, c.levels, c.block, c.search, q, t_ref=tr, t_pred=tp, sub=1)
+        t_enc = time.perf_counter() - t0
+        out = H.Stream(data).decode_pixels(coords).float()
+        mse = float(torch.mean((out - ref) ** 2))
+        return {"mc": 1, "q": q, "T": [tr, tp], "chroma": "4:2:0", "bpp": len(data) * 8.0 / n_px,
+                "psnr_db": float("inf") if mse == 0 else 10.0 * math.log10(255.0 ** 2 / mse), "encode_s": t_enc}
+
+    rd420 = [point420(q) for q in (1, 2, 4, 8, 16)] + [point420(4, 400, 800)]
     sweeps = {
         "block": [point(1, 4, B=b) for b in (8, 16, 32)],
         "window": [point(1, 4, Ws=w) for w in (1, 2, 4, 8)],
@@ -564,6 +576,8 @@ def run_study(args):
         "config": {"workload": f"{c.name}: {c.nu}x{c.nv} grid of {c.width}x{c.height} RGB8 views, {c.n_planes} planes "
                                f"0-{c.disp_max:g} px disparity; q in 2..16, T=0 unless stated"},
         "psnr_target_db": target, "bpp_ratio_at_target": ratios, "rd": rd, "sweeps": sweeps,
+        "chroma_420": {"rd": rd420, "bpp_ratio_at_target": (bpp_at(rd420[:5], target) / bpp_q
+                                                             if bpp_at(rd420[:5], target) else None)},
         "reference_store": [ref_store(0, 0), ref_store(400, 800)],
         "gpu_launches": None, "cpu_baseline": None,
     }), flush=True)
@@ -885,13 +899,13 @@ def main():
     points = {}
     if args.path == 0 and not args.no_points:
         k_steps = max(3, min(args.steps, 100))
-        for q, pr, pp in ((2, tr, tp), (8, tr, tp), (args.qstep, 0, 0)):
-            d2 = H.encode(lf, c.levels, c.block, c.search, q, t_ref=pr, t_pred=pp)
+        for q, pr, pp, sub in ((2, tr, tp, 0), (8, tr, tp, 0), (args.qstep, 0, 0, 0), (args.qstep, tr, tp, 1)):
+            d2 = H.encode(lf, c.levels, c.block, c.search, q, t_ref=pr, t_pred=pp, sub=sub)
             s2 = H.Stream(d2, device=local)
             ms2, ph2 = time_steps(H, s2, arr, out, flush, stream, k_steps, 3, 0)
             ms2 = float(np.mean(ms2))
             r2, rs2, b2, cb2 = rooflines(H, s2, arr, n_out, ms2, ph2, 0, peak, peak_kind)
-            points[f"q={q} T=({pr},{pp})"] = {
+            points[f"q={q} T=({pr},{pp})" + (" chroma 4:2:0" if sub else "")] = {
                 "views_per_s": views_per_step / (ms2 / 1000.0), "ms_per_step": ms2, "steps": k_steps,
                 "phases_ms": {"mark+assign": ph2[0], "decode": ph2[1], "blend": ph2[2]},
                 "bpp": len(d2) * 8.0 / (c.nu * c.nv * c.width * c.height),
