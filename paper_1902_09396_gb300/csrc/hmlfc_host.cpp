@@ -586,6 +586,15 @@ int hmlfc_load_stream(const void *h_bytes, size_t nbytes, int device, void *cuda
     }
     ds.rnpx = g.npx;
     ds.mv_node = (int)g.mv_node;
+    ds.lim_roots = (int64_t)g.n_roots * g.npx;
+    ds.lim_groups = g.n_nc * g.ngroups;
+    ds.lim_offs = g.n_sig;
+    ds.lim_recs = (int64_t)g.n_recw + 2;          // with the padding words a funnel-shift read may touch
+    ds.lim_mvs = (int64_t)g.n_mvw + 2;
+    ds.lim_ref_tab = g.n_ref_nc * g.nblocks;
+    ds.lim_tiles = (s->n_tiles + 1) * B2;
+    ds.lim_planes = (int64_t)g.n_ref_nc * (int64_t)plane + 128;   // + the padding (256 B)
+    ds.lim_mv = g.n_mv;
     for (int l = 0; l <= kMaxLevels; l++) {
         ds.gu[l] = l <= g.L ? g.gu[l] : 1;
         ds.gv[l] = l <= g.L ? g.gv[l] : 1;
@@ -673,7 +682,9 @@ int hmlfc_check_status(const hmlfc_stream *s, void *cuda_stream) {
     if (e == cudaSuccess && v) e = cudaMemsetAsync(s->ds.status, 0, 4, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "status read");
-    if (v & 1u) return fail(HMLFC_E_INVALID_ARG, "a decoded coordinate was outside the light field");
+    if (v & kStatusBounds)
+        return fail(HMLFC_E_CORRUPT, "a kernel index fell outside its stream array (bounds-checked build)");
+    if (v & kStatusCoord) return fail(HMLFC_E_INVALID_ARG, "a decoded coordinate was outside the light field");
     return HMLFC_OK;
 }
 

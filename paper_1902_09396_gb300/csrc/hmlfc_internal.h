@@ -49,7 +49,15 @@ struct DevStream {
     int cW[3], cH[3], cnbx[3], cnb[3], roff[3], mv_coff[3];
     int mv_node;
     int64_t rnpx;
+    // element counts of the arrays above (the bounds a HMLFC_CHECK build checks every read against) and of
+    // the motion-vector symbols
+    int64_t lim_roots, lim_groups, lim_offs, lim_recs, lim_mvs, lim_ref_tab, lim_tiles, lim_planes, lim_mv;
 };
+
+// Status bits of a stream object: kStatusCoord, a decode_pixels coordinate
+// outside the light field; kStatusBounds, a read that a HMLFC_CHECK build
+// found outside its array (the read was skipped).
+constexpr uint32_t kStatusCoord = 1u, kStatusBounds = 2u;
 
 // Views of one launch, by value (kernel parameter space).
 constexpr int kMaxViewsPerLaunch = 128;

@@ -22,6 +22,46 @@ namespace hmlfc {
 namespace {
 
 // ---------------------------------------------------------------------------
+// checked reads (HMLFC_CHECK builds)
+// ---------------------------------------------------------------------------
+//
+// A build with HMLFC_CHECK defined bounds-checks every index into the stream
+// object's arrays before the read: an index outside [0, n) sets
+// kStatusBounds in the stream's status word (hmlfc_check_status reports it)
+// and reads element 0 instead.  Other builds compile the checks away.
+
+__device__ __forceinline__ int64_t chk(const DevStream &S, int64_t i, int64_t n) {
+#ifdef HMLFC_CHECK
+    if (i < 0 || i >= n) {
+        atomicOr(S.status, kStatusBounds);
+        return 0;
+    }
+#else
+    (void)S;
+    (void)n;
+#endif
+    return i;
+}
+
+// true when [p, p + span) lies inside array [base, base + n) (always in other builds)
+template <class T>
+__device__ __forceinline__ bool chk_span(const DevStream &S, const T *base, int64_t n, const T *p, int64_t span) {
+#ifdef HMLFC_CHECK
+    const int64_t o = p - base;
+    if (o < 0 || o + span > n) {
+        atomicOr(S.status, kStatusBounds);
+        return false;
+    }
+#else
+    (void)S; (void)base; (void)n; (void)p; (void)span;
+#endif
+    return true;
+}
+
+// __ldg of element `idx` of stream array `arr`, bounds-checked in HMLFC_CHECK builds
+#define SLD(S, arr, idx) __ldg((S).arr + chk((S), (int64_t)(idx), (S).lim_##arr))
+
+// ---------------------------------------------------------------------------
 // bit fields and BISE (Sec. 4.6)
 // ---------------------------------------------------------------------------
 
@@ -148,8 +188,8 @@ template <int BS>
 __device__ __forceinline__ int ref_coef(const DevStream &S, const Blk<BS> &bk, int c, uint32_t row, int x, int y) {
     const int bx = bk.div(x), by = bk.div(y);
     const int B = bk.size();
-    const uint32_t tile = __ldg(S.ref_tab + row + (uint32_t)(by * S.cnbx[c] + bx));
-    return __ldg(S.tiles + (size_t)tile * (B * B) + (y - by * B) * B + (x - bx * B));
+    const uint32_t tile = SLD(S, ref_tab, row + (uint32_t)(by * S.cnbx[c] + bx));
+    return SLD(S, tiles, (size_t)tile * (B * B) + (y - by * B) * B + (x - bx * B));
 }
 
 // Sec. 4.4 motion re-compensation with the quarter-pel bilinear predictor,
@@ -173,7 +213,25 @@ __device__ __forceinline__ int mc_pred(const DevStream &S, const Blk<BS> &bk, in
 __device__ __forceinline__ uint64_t mv_index(const DevStream &S, const LevelTabs &T, int l, int a, int b, int c,
                                             int k) {
     const int pr = pred_rank(T, l, a, b, c);       // pred_base (a multiple of 3) + node * 3 + c
-    return (uint64_t)((pr - c) / 3) * (uint64_t)S.mv_node + (uint64_t)(S.mv_coff[c] + k);
+    return (uint64_t)chk(S, (int64_t)((pr - c) / 3) * S.mv_node + S.mv_coff[c] + k, S.lim_mv);
+}
+
+// HMLFC_CHECK builds: true when the record at word `rec` (header hdr) with n
+// values ends inside the record words (otherwise kStatusBounds is set and the
+// caller treats the block as insignificant); always true in other builds.
+__device__ __forceinline__ bool rec_ok(const DevStream &S, uint32_t rec, uint32_t hdr, int n) {
+#ifdef HMLFC_CHECK
+    const uint32_t mode = (hdr >> 21) & 3u, b = (hdr >> 16) & 31u;
+    const uint64_t bits = mode == 0 ? (uint64_t)n * b
+                                    : (mode == 1 ? (uint64_t)((n + 4) / 5) * (8 + 5 * b) : (uint64_t)((n + 2) / 3) * (7 + 3 * b));
+    if (mode == 3 || (uint64_t)rec + 1 + (bits + 31) / 32 > (uint64_t)S.lim_recs - 2) {
+        atomicOr(S.status, kStatusBounds);
+        return false;
+    }
+#else
+    (void)S; (void)rec; (void)hdr; (void)n;
+#endif
+    return true;
 }
 
 __device__ __forceinline__ void decode_mv(const DevStream &S, uint32_t sym, int &mvx, int &mvy, int &sign) {
@@ -184,14 +242,16 @@ __device__ __forceinline__ void decode_mv(const DevStream &S, uint32_t sym, int 
     mvy = (int)(s2 - qx * (uint32_t)S.side) - 4 * S.Ws;
 }
 
-// Residual r^ of block k (record lookup through the group index).
-__device__ __forceinline__ int residual(const DevStream &S, int nc, int k, uint32_t idx) {
-    const uint4 g = __ldg(S.groups + (size_t)nc * S.ngroups + (k >> 5));
+// Residual r^ of block k, n values, at value index idx (record lookup through
+// the group index).
+__device__ __forceinline__ int residual(const DevStream &S, int nc, int k, uint32_t idx, int n) {
+    const uint4 g = SLD(S, groups, (size_t)nc * S.ngroups + (k >> 5));
     const uint32_t bit = (uint32_t)k & 31u;
     if (!((g.x >> bit) & 1u)) return 0;
     const uint32_t rank = __popc(g.x & ((1u << bit) - 1u));
-    const uint32_t rec = g.y + __ldg(S.offs + g.z + rank);
-    const uint32_t hdr = __ldg(S.recs + rec);
+    const uint32_t rec = g.y + SLD(S, offs, g.z + rank);
+    const uint32_t hdr = SLD(S, recs, rec);
+    if (!rec_ok(S, rec, hdr, n)) return 0;
     const int m = (int)(int16_t)(hdr & 0xFFFFu);
     return S.q * (m + (int)bise_get_small(S.recs + rec + 1, (hdr >> 21) & 3u, (hdr >> 16) & 31u, idx));
 }
@@ -206,8 +266,8 @@ __device__ int srv_direct(const DevStream &S, const LevelTabs &T, const Blk<BS> 
     const int k = by * S.cnbx[c] + bx;
     if (is_ref(a, b)) return ref_coef(S, bk, c, (uint32_t)ref_rank(T, l, a, b, c) * S.nblocks, x, y);
     const int x0 = bx * B, y0 = by * B;
-    const int bw = min(B, S.cW[c] - x0);
-    const int r = residual(S, nc_index(T, l, a, b, c), k, (uint32_t)((y - y0) * bw + (x - x0)));
+    const int bw = min(B, S.cW[c] - x0), bh = min(B, S.cH[c] - y0);
+    const int r = residual(S, nc_index(T, l, a, b, c), k, (uint32_t)((y - y0) * bw + (x - x0)), bw * bh);
     if (!S.mc) return r;
     const uint32_t sym = bise_get_long(S.mvs, S.mv_mode, S.mv_b, mv_index(S, T, l, a, b, c, k));
     int mvx, mvy, sign;
@@ -234,9 +294,9 @@ __device__ uint32_t sample_direct(const DevStream &S, const LevelTabs &T, const 
     // with sub-sampled chroma, Co and Cg of (x, y) are those of chroma pixel (x >> 1, y >> 1)
     const int xc = S.sub ? x >> 1 : x, yc = S.sub ? y >> 1 : y;
     const size_t rbase = ((size_t)(i >> L) * T.gv[L] + (j >> L)) * (size_t)S.rnpx;
-    int v0 = __ldg(S.roots + rbase + S.roff[0] + (size_t)y * S.cW[0] + x);
-    int v1 = __ldg(S.roots + rbase + S.roff[1] + (size_t)yc * S.cW[1] + xc);
-    int v2 = __ldg(S.roots + rbase + S.roff[2] + (size_t)yc * S.cW[2] + xc);
+    int v0 = SLD(S, roots, rbase + S.roff[0] + (size_t)y * S.cW[0] + x);
+    int v1 = SLD(S, roots, rbase + S.roff[1] + (size_t)yc * S.cW[1] + xc);
+    int v2 = SLD(S, roots, rbase + S.roff[2] + (size_t)yc * S.cW[2] + xc);
     for (int l = S.lod; l < L; l++) {
         const int a = i >> l, b = j >> l;
         v0 += srv_direct(S, T, bk, l, a, b, 0, x, y);
@@ -257,7 +317,8 @@ __global__ void k_decode_tiles(const DevStream S, const uint4 *__restrict__ src,
     const int t = blockIdx.x;
     if (t >= n_tiles) return;
     const uint4 s = src[t];
-    const uint32_t hdr = __ldg(S.recs + s.x);
+    const uint32_t hdr = SLD(S, recs, s.x);
+    if (!rec_ok(S, s.x, hdr, (int)(s.y * s.z))) return;
     const int m = (int)(int16_t)(hdr & 0xFFFFu);
     const uint32_t mode = (hdr >> 21) & 3u, b = (hdr >> 16) & 31u;
     const int B = S.B;
@@ -284,7 +345,7 @@ __global__ void __launch_bounds__(256) k_build_planes(const DevStream S, int n_r
         if (k >= S.cnb[c]) continue;
         const int bx = k % S.cnbx[c], by = k / S.cnbx[c];
         const int bw = min(B, S.cW[c] - bx * B), bh = min(B, S.cH[c] - by * B);
-        const uint32_t tile = __ldg(S.ref_tab + (size_t)r * S.nblocks + k);
+        const uint32_t tile = SLD(S, ref_tab, (size_t)r * S.nblocks + k);
         const int16_t *src = S.tiles + (size_t)tile * B * B;
         int16_t *dst = planes + (size_t)r * S.W * S.H + (size_t)by * B * S.W + (size_t)bx * B;
         for (int e = threadIdx.x; e < bw * bh; e += blockDim.x) {
@@ -309,7 +370,7 @@ __global__ void __launch_bounds__(256) k_decode_pixels(const DevStream S, const 
         const int4 c = __ldg(coords + k);
         uint32_t v = 0;
         if (c.x < 0 || c.x >= S.nu || c.y < 0 || c.y >= S.nv || c.z < 0 || c.z >= S.W || c.w < 0 || c.w >= S.H) {
-            atomicOr(S.status, 1u);
+            atomicOr(S.status, kStatusCoord);
         } else {
             v = sample_direct(S, T, bk, c.x, c.y, c.z, c.w);
         }
@@ -474,7 +535,7 @@ __device__ __forceinline__ int tap(const DevStream &S, const Blk<BS> &bk, const 
     const int B = bk.size();
     const int tx = bk.div(x), ty = bk.div(y);
     const uint32_t tile = (ty == cy) ? (tx == cx ? t.x : t.y) : (tx == cx ? t.z : t.w);
-    return __ldg(S.tiles + (size_t)tile * (B * B) + (y - ty * B) * B + (x - tx * B));
+    return SLD(S, tiles, (size_t)tile * (B * B) + (y - ty * B) * B + (x - tx * B));
 }
 
 // SRV of one node-channel at a pixel, from its staged descriptor.
@@ -482,7 +543,7 @@ template <int BS>
 __device__ __forceinline__ int srv_desc(const DevStream &S, const Blk<BS> &bk, const Desc &D, bool ref,
                                         const PixGeom &g) {
     const int B = bk.size();
-    if (ref) return __ldg(S.tiles + (size_t)D.d1.x * (B * B) + g.toff);
+    if (ref) return SLD(S, tiles, (size_t)D.d1.x * (B * B) + g.toff);
     int r = 0;
     if (D.d0.x != kNone) {
         const int m = (int)(int16_t)(D.d0.y & 0xFFFFu);
@@ -667,15 +728,16 @@ __global__ void __launch_bounds__(TW *TH, 4) k_render(const __grid_constant__ De
             D.d1 = make_uint4(0u, 0u, 0u, 0u);
             if (a < T.gu[l] && b < T.gv[l] && bx < S.nbx && by < S.nby) {
                 if (is_ref(a, b)) {
-                    D.d1.x = __ldg(S.ref_tab + (size_t)ref_rank(T, l, a, b, c) * S.nblocks + k);
+                    D.d1.x = SLD(S, ref_tab, (size_t)ref_rank(T, l, a, b, c) * S.nblocks + k);
                 } else {
                     const int nc = nc_index(T, l, a, b, c);
-                    const uint4 g = __ldg(S.groups + (size_t)nc * S.ngroups + (k >> 5));
+                    const uint4 g = SLD(S, groups, (size_t)nc * S.ngroups + (k >> 5));
                     const uint32_t bit = (uint32_t)k & 31u;
                     if ((g.x >> bit) & 1u) {
-                        const uint32_t rec = g.y + __ldg(S.offs + g.z + __popc(g.x & ((1u << bit) - 1u)));
+                        const uint32_t rec = g.y + SLD(S, offs, g.z + __popc(g.x & ((1u << bit) - 1u)));
                         D.d0.x = rec;
-                        D.d0.y = __ldg(S.recs + rec);
+                        D.d0.y = SLD(S, recs, rec);
+                        if (!rec_ok(S, rec, D.d0.y, min(B, S.W - bx * B) * min(B, S.H - by * B))) D.d0.x = kNone;
                     }
                     if (S.mc) {
                         const uint32_t sym = bise_get_long(S.mvs, S.mv_mode, S.mv_b,
@@ -689,10 +751,10 @@ __global__ void __launch_bounds__(TW *TH, 4) k_render(const __grid_constant__ De
                         const size_t row = (size_t)ref_rank(T, l, a & ~1, b & ~1, c) * S.nblocks;
                         const int cx1 = min(cx + 1, S.nbx - 1), cy1 = min(cy + 1, S.nby - 1);
                         D.d0.w = (uint32_t)cx | ((uint32_t)cy << 16);
-                        D.d1.x = __ldg(S.ref_tab + row + cy * S.nbx + cx);
-                        D.d1.y = __ldg(S.ref_tab + row + cy * S.nbx + cx1);
-                        D.d1.z = __ldg(S.ref_tab + row + cy1 * S.nbx + cx);
-                        D.d1.w = __ldg(S.ref_tab + row + cy1 * S.nbx + cx1);
+                        D.d1.x = SLD(S, ref_tab, row + cy * S.nbx + cx);
+                        D.d1.y = SLD(S, ref_tab, row + cy * S.nbx + cx1);
+                        D.d1.z = SLD(S, ref_tab, row + cy1 * S.nbx + cx);
+                        D.d1.w = SLD(S, ref_tab, row + cy1 * S.nbx + cx1);
                     }
                 }
             }
@@ -716,9 +778,9 @@ __global__ void __launch_bounds__(TW *TH, 4) k_render(const __grid_constant__ De
                 int v[3];
                 if (l == L - 1) {
                     const size_t rb = ((size_t)(a >> 1) * T.gv[L] + (b >> 1)) * 3 * plane + (size_t)g.y * S.W + g.x;
-                    v[0] = __ldg(S.roots + rb);
-                    v[1] = __ldg(S.roots + rb + plane);
-                    v[2] = __ldg(S.roots + rb + 2 * plane);
+                    v[0] = SLD(S, roots, rb);
+                    v[1] = SLD(S, roots, rb + plane);
+                    v[2] = SLD(S, roots, rb + 2 * plane);
                 } else {
                     const int pn = ((a >> 1) - F.a0[l + 1]) * F.nnv[l + 1] + ((b >> 1) - F.b0[l + 1]);
                     const int *pp = par + pn * 3 * kMaxPx + p;
@@ -746,9 +808,9 @@ __global__ void __launch_bounds__(TW *TH, 4) k_render(const __grid_constant__ De
             int v[3];
             if (L == 1) {
                 const size_t rb = ((size_t)(i >> 1) * T.gv[1] + (j >> 1)) * 3 * plane + (size_t)g.y * S.W + g.x;
-                v[0] = __ldg(S.roots + rb);
-                v[1] = __ldg(S.roots + rb + plane);
-                v[2] = __ldg(S.roots + rb + 2 * plane);
+                v[0] = SLD(S, roots, rb);
+                v[1] = SLD(S, roots, rb + plane);
+                v[2] = SLD(S, roots, rb + 2 * plane);
             } else {
                 const int pn = ((i >> 1) - F.a0[1]) * F.nnv[1] + ((j >> 1) - F.b0[1]);
                 const int *pp = acc1 + pn * 3 * kMaxPx + p;
@@ -942,8 +1004,8 @@ __global__ void __launch_bounds__(256) k_dequant(const __grid_constant__ DevStre
         if (is_ref(s_a, s_b)) {
             v = ref_coef(S, bk, s_c, (uint32_t)ref_rank(T, s_l, s_a, s_b, s_c) * S.nblocks, x, y);
         } else {
-            const int bw = min(B, S.W - bx * B);
-            v = residual(S, (int)row, by * S.nbx + bx, (uint32_t)((y - by * B) * bw + (x - bx * B)));
+            const int bw = min(B, S.W - bx * B), bh = min(B, S.H - by * B);
+            v = residual(S, (int)row, by * S.nbx + bx, (uint32_t)((y - by * B) * bw + (x - bx * B)), bw * bh);
         }
         coeff[row * plane + p] = (float)v;
     }
@@ -975,16 +1037,17 @@ __device__ Desc make_desc(const DevStream &S, const LevelTabs &T, const Blk<BS> 
     D.d0 = make_uint4(kNone, 0u, 0u, 0u);
     D.d1 = make_uint4(0u, 0u, 0u, 0u);
     if (is_ref(a, b)) {
-        D.d1.x = __ldg(S.ref_tab + (size_t)ref_rank(T, l, a, b, c) * S.nblocks + k);
+        D.d1.x = SLD(S, ref_tab, (size_t)ref_rank(T, l, a, b, c) * S.nblocks + k);
         return D;
     }
     const int nc = nc_index(T, l, a, b, c);
-    const uint4 g = __ldg(S.groups + (size_t)nc * S.ngroups + (k >> 5));
+    const uint4 g = SLD(S, groups, (size_t)nc * S.ngroups + (k >> 5));
     const uint32_t bit = (uint32_t)k & 31u;
     if ((g.x >> bit) & 1u) {
-        const uint32_t rec = g.y + __ldg(S.offs + g.z + __popc(g.x & ((1u << bit) - 1u)));
+        const uint32_t rec = g.y + SLD(S, offs, g.z + __popc(g.x & ((1u << bit) - 1u)));
         D.d0.x = rec;
-        D.d0.y = __ldg(S.recs + rec);
+        D.d0.y = SLD(S, recs, rec);
+        if (!rec_ok(S, rec, D.d0.y, min(B, S.W - bx * B) * min(B, S.H - by * B))) D.d0.x = kNone;
     }
     if (S.mc) {
         const uint32_t sym =
@@ -997,10 +1060,10 @@ __device__ Desc make_desc(const DevStream &S, const LevelTabs &T, const Blk<BS> 
         const size_t row = (size_t)ref_rank(T, l, a & ~1, b & ~1, c) * S.nblocks;
         const int cx1 = min(cx + 1, S.nbx - 1), cy1 = min(cy + 1, S.nby - 1);
         D.d0.w = (uint32_t)cx | ((uint32_t)cy << 16);
-        D.d1.x = __ldg(S.ref_tab + row + cy * S.nbx + cx);
-        D.d1.y = __ldg(S.ref_tab + row + cy * S.nbx + cx1);
-        D.d1.z = __ldg(S.ref_tab + row + cy1 * S.nbx + cx);
-        D.d1.w = __ldg(S.ref_tab + row + cy1 * S.nbx + cx1);
+        D.d1.x = SLD(S, ref_tab, row + cy * S.nbx + cx);
+        D.d1.y = SLD(S, ref_tab, row + cy * S.nbx + cx1);
+        D.d1.z = SLD(S, ref_tab, row + cy1 * S.nbx + cx);
+        D.d1.w = SLD(S, ref_tab, row + cy1 * S.nbx + cx1);
     }
     return D;
 }
@@ -1221,11 +1284,13 @@ __device__ NDesc make_ndesc(const DevStream &S, const LevelTabs &T, const Blk<BS
         return D;
     }
     const int nc = nc_index(T, l, a, b, c);
-    const uint4 g = __ldg(S.groups + (size_t)nc * S.ngroups + (k >> 5));
+    const uint4 g = SLD(S, groups, (size_t)nc * S.ngroups + (k >> 5));
     const uint32_t bit = (uint32_t)k & 31u;
     if ((g.x >> bit) & 1u) {
-        D.rec = g.y + __ldg(S.offs + g.z + __popc(g.x & ((1u << bit) - 1u)));
-        D.hdr = __ldg(S.recs + D.rec);
+        D.rec = g.y + SLD(S, offs, g.z + __popc(g.x & ((1u << bit) - 1u)));
+        D.hdr = SLD(S, recs, D.rec);
+        const int cx0 = (k % S.cnbx[c]) * B, cy0 = (k / S.cnbx[c]) * B;
+        if (!rec_ok(S, D.rec, D.hdr, min(B, S.cW[c] - cx0) * min(B, S.cH[c] - cy0))) D.rec = kNone;
     }
     D.base = S.planes;
     if (!S.mc) {
@@ -1281,6 +1346,21 @@ template <int BS>
 __device__ __forceinline__ void eval_pair(const DevStream &S, const NDesc &D, int c, int p, int xi, int yi,
                                           uint32_t idx0, uint32_t idx1, int &o0, int &o1) {
     const uint32_t f = D.flags;
+#ifdef HMLFC_CHECK
+    {   // the dense-plane reads below: [base + p, base + p + 2) or, unclamped, up to base + p + W + 3
+        const bool near = (f & (kDRef | kDInt)) || (f & kDNoMC);
+        const bool clamped = (f & kDClamp) && !(f & (kDRef | kDInt));
+        if (!clamped && !(f & kDNoMC) &&
+            !chk_span(S, S.planes, S.lim_planes, D.base + p, near ? 2 : (int64_t)S.W + 3)) {
+            o0 = o1 = 0;
+            return;
+        }
+        if (clamped && !chk_span(S, S.planes, S.lim_planes, D.base, (int64_t)S.cH[c] * S.W)) {
+            o0 = o1 = 0;
+            return;
+        }
+    }
+#endif
     if (f & kDRef) {
         o0 = __ldg(D.base + p);
         o1 = __ldg(D.base + p + 1);
@@ -1441,15 +1521,16 @@ __global__ void __launch_bounds__(256, 4) k_decode_blocks(const __grid_constant_
             const uint32_t idxc = (uint32_t)(((by & 1) * (B / 2) + yic) * bwc + (bx & 1) * (B / 2) + xic);
             const size_t rb = ((size_t)(aK >> (L - K)) * T.gv[L] + (bK >> (L - K))) * (size_t)S.rnpx;
             int v0[3], v1[3];
-            v0[0] = __ldg(S.roots + rb + S.roff[0] + (size_t)gy * S.W + gx);
-            v1[0] = __ldg(S.roots + rb + S.roff[0] + (size_t)gy * S.W + gx + 1);
+            const int gx1 = in1 ? gx + 1 : gx;                 // the second pixel, when it is in the image
+            v0[0] = SLD(S, roots, rb + S.roff[0] + (size_t)gy * S.W + gx);
+            v1[0] = SLD(S, roots, rb + S.roff[0] + (size_t)gy * S.W + gx1);
 #pragma unroll
             for (int c = 1; c < 3; c++) {
                 if (S.sub) {
-                    v0[c] = v1[c] = __ldg(S.roots + rb + S.roff[c] + (size_t)(gy >> 1) * S.cW[c] + (gx >> 1));
+                    v0[c] = v1[c] = SLD(S, roots, rb + S.roff[c] + (size_t)(gy >> 1) * S.cW[c] + (gx >> 1));
                 } else {
-                    v0[c] = __ldg(S.roots + rb + S.roff[c] + (size_t)gy * S.W + gx);
-                    v1[c] = __ldg(S.roots + rb + S.roff[c] + (size_t)gy * S.W + gx + 1);
+                    v0[c] = SLD(S, roots, rb + S.roff[c] + (size_t)gy * S.W + gx);
+                    v1[c] = SLD(S, roots, rb + S.roff[c] + (size_t)gy * S.W + gx1);
                 }
             }
             const NDesc *dd = s_desc + gi * kDescPer;
@@ -1934,8 +2015,8 @@ __device__ __forceinline__ void decode_pair_l1(const DevStream &S, const LevelTa
     int v0[3], v1[3];
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        v0[c] = __ldg(S.roots + rb + c * plane + g.x);
-        v1[c] = __ldg(S.roots + rb + c * plane + x1);
+        v0[c] = SLD(S, roots, rb + c * plane + g.x);
+        v1[c] = SLD(S, roots, rb + c * plane + x1);
     }
     const size_t o0 = (size_t)yy * B + xx;
     int l = L - 1;
