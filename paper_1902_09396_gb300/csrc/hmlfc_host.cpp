@@ -193,13 +193,20 @@ int hmlfc::parse_header(const uint8_t *p, size_t n, Geometry &g) {
 namespace {
 
 // Walk the block index; check every significant block's record against the
-// stream bounds and the coefficient limit; build the reference tile table.
-int validate_index(const uint8_t *p, const Geometry &g, std::vector<uint32_t> &ref_tab, std::vector<uint32_t> &tile_src) {
+// stream bounds and the coefficient limit; build the reference tile table
+// and the record list of the reference tiles (tile_src) and of the
+// predictive residual tiles (ptile_src, {record, width, height, 0} each),
+// with the first residual tile of every group (gtile, 0 for the groups of
+// reference node-channels).
+int validate_index(const uint8_t *p, const Geometry &g, std::vector<uint32_t> &ref_tab, std::vector<uint32_t> &tile_src,
+                   std::vector<uint32_t> &ptile_src, std::vector<uint32_t> &gtile) {
     const uint8_t *groups = p + g.off_groups;
     const uint8_t *offs = p + g.off_offs;
     const uint8_t *recs = p + g.off_recs;
     ref_tab.assign((size_t)g.n_ref_nc * g.nblocks, 0u);
     tile_src.clear();
+    ptile_src.clear();
+    gtile.assign((size_t)g.n_nc * g.ngroups, 0u);
     uint64_t sig = 0;
     int64_t nc = 0, rr = 0;
     for (int l = g.L - 1; l >= 0; l--)
@@ -215,6 +222,7 @@ int validate_index(const uint8_t *p, const Geometry &g, std::vector<uint32_t> &r
                         if (valid < 32 && (valid == 0 ? bitmap : bitmap >> valid) != 0)
                             return fail(HMLFC_E_CORRUPT, "bitmap past the last block");
                         if ((uint64_t)obase != sig) return fail(HMLFC_E_CORRUPT, "block-offset base");
+                        if (!ref) gtile[(size_t)nc * g.ngroups + gi] = (uint32_t)(ptile_src.size() / 4);
                         for (int r = 0; r < valid; r++) {
                             if (!((bitmap >> r) & 1u)) continue;
                             if (sig >= g.n_sig) return fail(HMLFC_E_CORRUPT, "more significant blocks than offsets");
@@ -241,6 +249,11 @@ int validate_index(const uint8_t *p, const Geometry &g, std::vector<uint32_t> &r
                                 tile_src.push_back((uint32_t)bh);
                                 tile_src.push_back(0u);
                                 ref_tab[(size_t)(rr + c) * g.nblocks + k] = (uint32_t)(tile_src.size() / 4);
+                            } else {
+                                ptile_src.push_back((uint32_t)rec);
+                                ptile_src.push_back((uint32_t)bw);
+                                ptile_src.push_back((uint32_t)bh);
+                                ptile_src.push_back(0u);
                             }
                         }
                     }
@@ -526,8 +539,8 @@ int hmlfc_load_stream(const void *h_bytes, size_t nbytes, int device, void *cuda
     Geometry g{};
     int rc = parse_header(p, nbytes, g);
     if (rc != HMLFC_OK) return rc;
-    std::vector<uint32_t> ref_tab, tile_src;
-    rc = validate_index(p, g, ref_tab, tile_src);
+    std::vector<uint32_t> ref_tab, tile_src, ptile_src, gtile;
+    rc = validate_index(p, g, ref_tab, tile_src, ptile_src, gtile);
     if (rc != HMLFC_OK) return rc;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
@@ -541,8 +554,10 @@ int hmlfc_load_stream(const void *h_bytes, size_t nbytes, int device, void *cuda
     s->g = g;
     s->bytes.assign(p, p + nbytes);
     s->n_tiles = (int64_t)tile_src.size() / 4;
+    s->n_ptiles = (int64_t)ptile_src.size() / 4;
     s->ref_tab = ref_tab;
     const int B2 = g.B * g.B;
+    const int pstride = g.B + (g.B & 1);
     const uint64_t plane = (uint64_t)g.W * g.H;
     // one device allocation, carved into 256-byte aligned sections
     const size_t sz_roots = (size_t)g.n_roots * g.npx * 2;
@@ -554,10 +569,13 @@ int hmlfc_load_stream(const void *h_bytes, size_t nbytes, int device, void *cuda
     const size_t sz_tiles = (size_t)(s->n_tiles + 1) * B2 * 2;
     const size_t sz_src = tile_src.size() * 4 + 16;
     const size_t sz_planes = (size_t)g.n_ref_nc * plane * 2 + 256;   // padded: a pixel pair may read one past
+    const size_t sz_ptiles = (size_t)s->n_ptiles * g.B * pstride * 2;
+    const size_t sz_psrc = ptile_src.size() * 4 + 16;
     size_t o_roots = 0, o_groups = up256(o_roots + sz_roots), o_offs = up256(o_groups + sz_groups),
            o_recs = up256(o_offs + sz_offs), o_mvs = up256(o_recs + sz_recs), o_tab = up256(o_mvs + sz_mvs),
            o_tiles = up256(o_tab + sz_tab), o_src = up256(o_tiles + sz_tiles), o_status = up256(o_src + sz_src),
-           o_planes = up256(o_status + 256), total = up256(o_planes + sz_planes);
+           o_planes = up256(o_status + 256), o_ptiles = up256(o_planes + sz_planes),
+           o_psrc = up256(o_ptiles + sz_ptiles), total = up256(o_psrc + sz_psrc);
     cudaError_t e = cudaMalloc(&s->d_mem, total);
     if (e != cudaSuccess) {
         delete s;
@@ -569,6 +587,8 @@ int hmlfc_load_stream(const void *h_bytes, size_t nbytes, int device, void *cuda
     std::vector<uint8_t> img(o_tiles, 0);
     std::memcpy(img.data() + o_roots, p + g.off_roots, sz_roots);
     std::memcpy(img.data() + o_groups, p + g.off_groups, sz_groups);
+    for (size_t e = 0; e < gtile.size(); e++)      // word 3 of each group entry: its first residual tile
+        std::memcpy(img.data() + o_groups + e * 16 + 12, &gtile[e], 4);
     std::memcpy(img.data() + o_offs, p + g.off_offs, (size_t)g.n_sig * 2);
     std::memcpy(img.data() + o_recs, p + g.off_recs, (size_t)g.n_recw * 4);
     std::memcpy(img.data() + o_mvs, p + g.off_mvs, (size_t)g.n_mvw * 4);
@@ -595,6 +615,8 @@ int hmlfc_load_stream(const void *h_bytes, size_t nbytes, int device, void *cuda
     ds.lim_tiles = (s->n_tiles + 1) * B2;
     ds.lim_planes = (int64_t)g.n_ref_nc * (int64_t)plane + 128;   // + the padding (256 B)
     ds.lim_mv = g.n_mv;
+    ds.lim_ptiles = s->n_ptiles * g.B * pstride;
+    ds.pstride = pstride;
     for (int l = 0; l <= kMaxLevels; l++) {
         ds.gu[l] = l <= g.L ? g.gu[l] : 1;
         ds.gv[l] = l <= g.L ? g.gv[l] : 1;
@@ -613,14 +635,20 @@ int hmlfc_load_stream(const void *h_bytes, size_t nbytes, int device, void *cuda
     ds.tiles = reinterpret_cast<const int16_t *>(base + o_tiles);
     ds.status = reinterpret_cast<uint32_t *>(base + o_status);
     ds.planes = reinterpret_cast<const int16_t *>(base + o_planes);
+    ds.ptiles = reinterpret_cast<const int16_t *>(base + o_ptiles);
     e = cudaMemcpyAsync(base, img.data(), img.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !tile_src.empty())
         e = cudaMemcpyAsync(base + o_src, tile_src.data(), tile_src.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !ptile_src.empty())
+        e = cudaMemcpyAsync(base + o_psrc, ptile_src.data(), ptile_src.size() * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_tiles, 0, (size_t)B2 * 2, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_status, 0, 256, st);
     if (e == cudaSuccess)
         e = launch_decode_tiles(ds, reinterpret_cast<const uint32_t *>(base + o_src), (int)s->n_tiles,
-                                reinterpret_cast<int16_t *>(base + o_tiles), st);
+                                reinterpret_cast<int16_t *>(base + o_tiles), g.B, 1, st);
+    if (e == cudaSuccess)
+        e = launch_decode_tiles(ds, reinterpret_cast<const uint32_t *>(base + o_psrc), (int)s->n_ptiles,
+                                reinterpret_cast<int16_t *>(base + o_ptiles), pstride, 0, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_planes + sz_planes - 256, 0, 256, st);
     if (e == cudaSuccess) e = launch_build_planes(ds, g.n_ref_nc, reinterpret_cast<int16_t *>(base + o_planes), st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

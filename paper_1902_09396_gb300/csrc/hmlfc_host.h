@@ -84,6 +84,7 @@ struct hmlfc_stream {
     size_t d_bytes = 0;
     std::vector<uint8_t> bytes;      // host copy of the stream (re-encoding, counting)
     int64_t n_tiles = 0;
+    int64_t n_ptiles = 0;           // predictive residual tiles (significant predictive blocks)
     std::vector<uint32_t> ref_tab;   // host copy of the tile table
 };
 

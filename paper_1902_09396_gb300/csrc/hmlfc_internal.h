@@ -32,13 +32,18 @@ struct DevStream {
     int ref_base[kMaxLevels];       // rank of level l's first reference node-channel
     int pred_base[kMaxLevels];      // rank of level l's first predictive node-channel
     const int16_t *roots;           // [roots][3][H][W]
-    const uint4 *groups;            // [n_nc][ngroups] {bitmap, record base, offset base, 0}
+    const uint4 *groups;            // [n_nc][ngroups] {bitmap, record base, offset base, first residual tile}
     const uint16_t *offs;           // [n_sig]
     const uint32_t *recs;           // [n_rec_words + 2]
     const uint32_t *mvs;            // [n_mv_words + 2]
     const uint32_t *ref_tab;        // [n_ref_nc][nblocks] tile index, 0 = the zero tile
     const int16_t *tiles;           // [n_tiles + 1][B * B]
     const int16_t *planes;          // [n_ref_nc][H][W] the same reference SRVs as dense planes (+ padding)
+    // the dequantised residual r^ of every significant predictive block, decoded at load: tile t at
+    // ptiles + t * B * pstride, row stride pstride = B rounded up to even (4-byte aligned pixel pairs),
+    // zero outside the block's valid pixels; a predictive group's first tile is word 3 of its entry
+    const int16_t *ptiles;
+    int pstride;
     uint32_t *status;               // bit 0: an out-of-range coordinate was seen
     int lod;                        // progressive decode: levels below lod are left out (0 = full decode)
     // chroma sub-sampling (Sec. 4.5): sub = 1 codes Co and Cg at ceil(W/2) x ceil(H/2).  Per channel c:
@@ -52,6 +57,7 @@ struct DevStream {
     // element counts of the arrays above (the bounds a HMLFC_CHECK build checks every read against) and of
     // the motion-vector symbols
     int64_t lim_roots, lim_groups, lim_offs, lim_recs, lim_mvs, lim_ref_tab, lim_tiles, lim_planes, lim_mv;
+    int64_t lim_ptiles;
 };
 
 // Status bits of a stream object: kStatusCoord, a decode_pixels coordinate
@@ -80,8 +86,10 @@ constexpr int kMaxDevices = 64;
 cudaError_t fixed_scratch(int device, void **ptr);
 
 // Launchers implemented in hmlfc_kernels.cu.
+// Decode n_tiles records into B-row tiles of row stride `stride`, tile t of
+// the list at d_tiles + (t + first) * B * stride.
 cudaError_t launch_decode_tiles(const DevStream &ds, const uint32_t *d_src, int n_tiles, int16_t *d_tiles,
-                                cudaStream_t st);
+                                int stride, int first, cudaStream_t st);
 cudaError_t launch_build_planes(const DevStream &ds, int64_t n_ref, int16_t *d_planes, cudaStream_t st);
 cudaError_t launch_decode_pixels(const DevStream &ds, const int32_t *d_coords, int64_t n, uint8_t *d_rgb,
                                  cudaStream_t st);

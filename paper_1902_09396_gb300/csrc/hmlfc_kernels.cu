@@ -311,9 +311,12 @@ __device__ uint32_t sample_direct(const DevStream &S, const LevelTabs &T, const 
 // ---------------------------------------------------------------------------
 
 // src[t] = {record word, block valid width, block valid height, unused} for
-// tile t + 1 (tile 0 is the shared zero tile).
+// tile t + first, B rows of `stride` values (the reference tiles: stride B,
+// first 1, tile 0 being the shared zero tile; the predictive residual tiles:
+// stride B rounded up to even, first 0).  Values outside the block's valid
+// pixels are zero.
 __global__ void k_decode_tiles(const DevStream S, const uint4 *__restrict__ src, int n_tiles,
-                               int16_t *__restrict__ tiles) {
+                               int16_t *__restrict__ tiles, int stride, int first) {
     const int t = blockIdx.x;
     if (t >= n_tiles) return;
     const uint4 s = src[t];
@@ -322,9 +325,9 @@ __global__ void k_decode_tiles(const DevStream S, const uint4 *__restrict__ src,
     const int m = (int)(int16_t)(hdr & 0xFFFFu);
     const uint32_t mode = (hdr >> 21) & 3u, b = (hdr >> 16) & 31u;
     const int B = S.B;
-    int16_t *dst = tiles + (size_t)(t + 1) * B * B;
-    for (int p = threadIdx.x; p < B * B; p += blockDim.x) {
-        const int yy = p / B, xx = p - yy * B;
+    int16_t *dst = tiles + (size_t)(t + first) * B * stride;
+    for (int p = threadIdx.x; p < B * stride; p += blockDim.x) {
+        const int yy = p / stride, xx = p - yy * stride;
         int v = 0;
         if (xx < (int)s.y && yy < (int)s.z)
             v = S.q * (m + (int)bise_get_small(S.recs + s.x + 1, mode, b, (uint32_t)(yy * (int)s.y + xx)));
@@ -1245,13 +1248,14 @@ __global__ void __launch_bounds__(256) k_assign(const __grid_constant__ DevStrea
 // by the integer part of the motion vector for a predictive one -- so every
 // tap of every pixel is base + (pixel offset in the block) + a constant.
 // Blocks whose taps would leave the image take the clamped path instead,
-// with base at the plane origin and the tap origin in (ox, oy).
+// with base at the plane origin and the tap origin in (ox, oy).  A
+// significant predictive block's residual r^ is read from its resident tile
+// (decoded at load), `res` pointing at the tile's first value.
 constexpr uint32_t kDRef = 1u, kDNeg = 2u, kDClamp = 4u, kDInt = 8u, kDNoMC = 16u;
 
 struct NDesc {
     const int16_t *base;
-    uint32_t rec;          // residual record word, kNone when insignificant (r^ = 0)
-    uint32_t hdr;          // record header (min level, BISE mode and bits)
+    const int16_t *res;    // residual tile, nullptr when insignificant (r^ = 0)
     uint32_t w;            // bilinear weights w00 | w10 << 8 | w01 << 16 | w11 << 24 (sum 16)
     uint32_t flags;        // kD*
     int32_t ox, oy;        // clamped path: block origin + integer part of the motion vector
@@ -1273,8 +1277,7 @@ __device__ NDesc make_ndesc(const DevStream &S, const LevelTabs &T, const Blk<BS
     const int x0 = bx * span, y0 = by * span;                  // region origin in the channel's plane
     const size_t plane = (size_t)S.W * S.H;                    // dense planes keep row stride W
     NDesc D;
-    D.rec = kNone;
-    D.hdr = 0u;
+    D.res = nullptr;
     D.w = 16u;
     D.ox = x0;
     D.oy = y0;
@@ -1286,12 +1289,7 @@ __device__ NDesc make_ndesc(const DevStream &S, const LevelTabs &T, const Blk<BS
     const int nc = nc_index(T, l, a, b, c);
     const uint4 g = SLD(S, groups, (size_t)nc * S.ngroups + (k >> 5));
     const uint32_t bit = (uint32_t)k & 31u;
-    if ((g.x >> bit) & 1u) {
-        D.rec = g.y + SLD(S, offs, g.z + __popc(g.x & ((1u << bit) - 1u)));
-        D.hdr = SLD(S, recs, D.rec);
-        const int cx0 = (k % S.cnbx[c]) * B, cy0 = (k / S.cnbx[c]) * B;
-        if (!rec_ok(S, D.rec, D.hdr, min(B, S.cW[c] - cx0) * min(B, S.cH[c] - cy0))) D.rec = kNone;
-    }
+    if ((g.x >> bit) & 1u) D.res = S.ptiles + (size_t)(g.w + __popc(g.x & ((1u << bit) - 1u))) * B * S.pstride;
     D.base = S.planes;
     if (!S.mc) {
         D.flags = kDNoMC;
@@ -1318,33 +1316,17 @@ __device__ NDesc make_ndesc(const DevStream &S, const LevelTabs &T, const Blk<BS
     return D;
 }
 
-// Values idx0 and idx1 of a block's BISE payload (Sec. 4.6).  The mode is
-// the same for every lane of a warp (one block per warp), so the power-of-two
-// alphabet reads both values from one three-word window.
-__device__ __forceinline__ void bise_pair(const uint32_t *__restrict__ w, uint32_t mode, uint32_t b, uint32_t idx0,
-                                          uint32_t idx1, uint32_t &v0, uint32_t &v1) {
-    if (mode == 0) {
-        const uint32_t pos0 = idx0 * b, pos1 = idx1 * b, k = pos0 >> 5;
-        const uint32_t lo = __ldg(w + k), mid = __ldg(w + k + 1), hi = __ldg(w + k + 2);
-        const uint32_t mask = (1u << b) - 1u;
-        v0 = __funnelshift_r(lo, mid, pos0 & 31u) & mask;
-        const bool nxt = (pos1 >> 5) != k;
-        v1 = __funnelshift_r(nxt ? mid : lo, nxt ? hi : mid, pos1 & 31u) & mask;
-    } else {
-        v0 = bise_get_small(w, mode, b, idx0);
-        v1 = bise_get_small(w, mode, b, idx1);
-    }
-}
-
 // SRV of one node-channel at a horizontally adjacent pixel pair of a block
 // (Sec. 4.4, Sec. 4.8.1): p = in-block offset y * W + x of the first pixel,
-// (xi, yi) its in-block position, idx0 / idx1 the payload indices of the
-// two pixels.  A reference node gives its resident R^; a predictive node
-// sign * P + r^, P the quarter-pel bilinear of the reference's R^ with
-// weights summing to 16, + 8, >> 4.
-template <int BS>
-__device__ __forceinline__ void eval_pair(const DevStream &S, const NDesc &D, int c, int p, int xi, int yi,
-                                          uint32_t idx0, uint32_t idx1, int &o0, int &o1) {
+// (xi, yi) its in-block position, ti its residual-tile index.  With `pair`
+// the two pixels' residuals are one aligned 32-bit read at ti (even);
+// without it (a sub-sampled chroma pixel shared by the pair) one value.  A
+// reference node gives its resident R^; a predictive node sign * P + r^, P
+// the quarter-pel bilinear of the reference's R^ with weights summing to
+// 16, + 8, >> 4.
+template <int BS, bool pair>
+__device__ __forceinline__ void eval_pair(const DevStream &S, const NDesc &D, int c, int p, int xi, int yi, int ti,
+                                          int &o0, int &o1) {
     const uint32_t f = D.flags;
 #ifdef HMLFC_CHECK
     {   // the dense-plane reads below: [base + p, base + p + 2) or, unclamped, up to base + p + W + 3
@@ -1359,6 +1341,10 @@ __device__ __forceinline__ void eval_pair(const DevStream &S, const NDesc &D, in
             o0 = o1 = 0;
             return;
         }
+        if (D.res && !(f & kDRef) && !chk_span(S, S.ptiles, S.lim_ptiles, D.res + ti, pair ? 2 : 1)) {
+            o0 = o1 = 0;
+            return;
+        }
     }
 #endif
     if (f & kDRef) {
@@ -1367,12 +1353,14 @@ __device__ __forceinline__ void eval_pair(const DevStream &S, const NDesc &D, in
         return;
     }
     int r0 = 0, r1 = 0;
-    if (D.rec != kNone) {
-        const int m = (int)(int16_t)(D.hdr & 0xFFFFu);
-        uint32_t v0, v1;
-        bise_pair(S.recs + D.rec + 1, (D.hdr >> 21) & 3u, (D.hdr >> 16) & 31u, idx0, idx1, v0, v1);
-        r0 = S.q * (m + (int)v0);
-        r1 = S.q * (m + (int)v1);
+    if (D.res) {
+        if (pair) {
+            const uint32_t rr = __ldg(reinterpret_cast<const uint32_t *>(D.res + ti));
+            r0 = (int)(int16_t)(rr & 0xFFFFu);
+            r1 = (int)rr >> 16;
+        } else {
+            r0 = r1 = __ldg(D.res + ti);
+        }
     }
     if (f & kDNoMC) {
         o0 = r0;
@@ -1512,13 +1500,12 @@ __global__ void __launch_bounds__(256, 4) k_decode_blocks(const __grid_constant_
             const bool in0 = xx < bw && yy < bh, in1 = xx + 1 < bw && yy < bh;
             const int xi = min(xx, bw - 1), yi = min(yy, bh - 1);   // pixels outside the image compute a copy
             const int p = yi * S.W + xi;
-            const uint32_t idx0 = (uint32_t)(yi * bw + xi), idx1 = in1 ? idx0 + 1u : idx0;
+            const int ti = yy * S.pstride + xx;                 // even; rows and columns past the block read zeros
             const int gx = bx * B + xi, gy = by * B + yi;
             // sub-sampled chroma: both pixels of the pair are chroma pixel (gx >> 1, gy >> 1), at (xi >> 1,
             // yi >> 1) of the descriptors' half-size regions, inside chroma block (bx >> 1, by >> 1)
             const int xic = xi >> 1, yic = yi >> 1, pc = yic * S.W + xic;
-            const int bwc = min(B, S.cW[1] - (bx >> 1) * B);
-            const uint32_t idxc = (uint32_t)(((by & 1) * (B / 2) + yic) * bwc + (bx & 1) * (B / 2) + xic);
+            const int tic = ((by & 1) * (B / 2) + yic) * S.pstride + (bx & 1) * (B / 2) + xic;
             const size_t rb = ((size_t)(aK >> (L - K)) * T.gv[L] + (bK >> (L - K))) * (size_t)S.rnpx;
             int v0[3], v1[3];
             const int gx1 = in1 ? gx + 1 : gx;                 // the second pixel, when it is in the image
@@ -1593,10 +1580,10 @@ __global__ void __launch_bounds__(256, 4) k_decode_blocks(const __grid_constant_
                 for (int c = 0; c < 3; c++) {
                     if (c > 0 && S.sub) {
                         int unused;
-                        eval_pair<BS>(S, d[c], c, pc, xic, yic, idxc, idxc, s0[c], unused);
+                        eval_pair<BS, false>(S, d[c], c, pc, xic, yic, tic, s0[c], unused);
                         s1[c] = s0[c];
                     } else {
-                        eval_pair<BS>(S, d[c], c, p, xi, yi, idx0, idx1, s0[c], s1[c]);
+                        eval_pair<BS, true>(S, d[c], c, p, xi, yi, ti, s0[c], s1[c]);
                     }
                 }
                 if (phase == 0) {
@@ -2331,9 +2318,10 @@ __global__ void __launch_bounds__(256) k_decode_resident(const __grid_constant__
 // ---------------------------------------------------------------------------
 
 cudaError_t launch_decode_tiles(const DevStream &ds, const uint32_t *d_src, int n_tiles, int16_t *d_tiles,
-                                cudaStream_t st) {
+                                int stride, int first, cudaStream_t st) {
     if (n_tiles <= 0) return cudaSuccess;
-    k_decode_tiles<<<n_tiles, 256, 0, st>>>(ds, reinterpret_cast<const uint4 *>(d_src), n_tiles, d_tiles);
+    k_decode_tiles<<<n_tiles, 256, 0, st>>>(ds, reinterpret_cast<const uint4 *>(d_src), n_tiles, d_tiles, stride,
+                                            first);
     return cudaGetLastError();
 }
 
