@@ -569,7 +569,7 @@ int hmlfc_load_stream(const void *h_bytes, size_t nbytes, int device, void *cuda
     const size_t sz_tiles = (size_t)(s->n_tiles + 1) * B2 * 2;
     const size_t sz_src = tile_src.size() * 4 + 16;
     const size_t sz_planes = (size_t)g.n_ref_nc * plane * 2 + 256;   // padded: a pixel pair may read one past
-    const size_t sz_ptiles = (size_t)s->n_ptiles * g.B * pstride * 2;
+    const size_t sz_ptiles = (size_t)(s->n_ptiles + 1) * g.B * pstride * 2;   // tile 0: zeros
     const size_t sz_psrc = ptile_src.size() * 4 + 16;
     size_t o_roots = 0, o_groups = up256(o_roots + sz_roots), o_offs = up256(o_groups + sz_groups),
            o_recs = up256(o_offs + sz_offs), o_mvs = up256(o_recs + sz_recs), o_tab = up256(o_mvs + sz_mvs),
@@ -587,7 +587,7 @@ int hmlfc_load_stream(const void *h_bytes, size_t nbytes, int device, void *cuda
     std::vector<uint8_t> img(o_tiles, 0);
     std::memcpy(img.data() + o_roots, p + g.off_roots, sz_roots);
     std::memcpy(img.data() + o_groups, p + g.off_groups, sz_groups);
-    for (size_t e = 0; e < gtile.size(); e++)      // word 3 of each group entry: its first residual tile
+    for (size_t e = 0; e < gtile.size(); e++)      // word 3 of each group entry: its residual tiles' first rank
         std::memcpy(img.data() + o_groups + e * 16 + 12, &gtile[e], 4);
     std::memcpy(img.data() + o_offs, p + g.off_offs, (size_t)g.n_sig * 2);
     std::memcpy(img.data() + o_recs, p + g.off_recs, (size_t)g.n_recw * 4);
@@ -615,7 +615,7 @@ int hmlfc_load_stream(const void *h_bytes, size_t nbytes, int device, void *cuda
     ds.lim_tiles = (s->n_tiles + 1) * B2;
     ds.lim_planes = (int64_t)g.n_ref_nc * (int64_t)plane + 128;   // + the padding (256 B)
     ds.lim_mv = g.n_mv;
-    ds.lim_ptiles = s->n_ptiles * g.B * pstride;
+    ds.lim_ptiles = (s->n_ptiles + 1) * g.B * pstride;
     ds.pstride = pstride;
     for (int l = 0; l <= kMaxLevels; l++) {
         ds.gu[l] = l <= g.L ? g.gu[l] : 1;
@@ -647,8 +647,10 @@ int hmlfc_load_stream(const void *h_bytes, size_t nbytes, int device, void *cuda
         e = launch_decode_tiles(ds, reinterpret_cast<const uint32_t *>(base + o_src), (int)s->n_tiles,
                                 reinterpret_cast<int16_t *>(base + o_tiles), g.B, 1, st);
     if (e == cudaSuccess)
+        e = cudaMemsetAsync(base + o_ptiles, 0, (size_t)g.B * pstride * 2, st);
+    if (e == cudaSuccess)
         e = launch_decode_tiles(ds, reinterpret_cast<const uint32_t *>(base + o_psrc), (int)s->n_ptiles,
-                                reinterpret_cast<int16_t *>(base + o_ptiles), pstride, 0, st);
+                                reinterpret_cast<int16_t *>(base + o_ptiles), pstride, 1, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_planes + sz_planes - 256, 0, 256, st);
     if (e == cudaSuccess) e = launch_build_planes(ds, g.n_ref_nc, reinterpret_cast<int16_t *>(base + o_planes), st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -32,7 +32,7 @@ struct DevStream {
     int ref_base[kMaxLevels];       // rank of level l's first reference node-channel
     int pred_base[kMaxLevels];      // rank of level l's first predictive node-channel
     const int16_t *roots;           // [roots][3][H][W]
-    const uint4 *groups;            // [n_nc][ngroups] {bitmap, record base, offset base, first residual tile}
+    const uint4 *groups;            // [n_nc][ngroups] {bitmap, record base, offset base, residual rank}
     const uint16_t *offs;           // [n_sig]
     const uint32_t *recs;           // [n_rec_words + 2]
     const uint32_t *mvs;            // [n_mv_words + 2]
@@ -41,7 +41,8 @@ struct DevStream {
     const int16_t *planes;          // [n_ref_nc][H][W] the same reference SRVs as dense planes (+ padding)
     // the dequantised residual r^ of every significant predictive block, decoded at load: tile t at
     // ptiles + t * B * pstride, row stride pstride = B rounded up to even (4-byte aligned pixel pairs),
-    // zero outside the block's valid pixels; a predictive group's first tile is word 3 of its entry
+    // zero outside the block's valid pixels; tile 0 is all zeros; a predictive group's first tile is 1 +
+    // word 3 of its entry
     const int16_t *ptiles;
     int pstride;
     uint32_t *status;               // bit 0: an out-of-range coordinate was seen

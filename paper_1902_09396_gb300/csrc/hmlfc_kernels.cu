@@ -281,7 +281,9 @@ __device__ __forceinline__ uint32_t ycocg_to_rgb8(int Y, int Co, int Cg) {
     const int G = Cg + t;
     const int Bc = t - (Co >> 1);
     const int R = Bc + Co;
-    return (uint32_t)clampi(R, 0, 255) | ((uint32_t)clampi(G, 0, 255) << 8) | ((uint32_t)clampi(Bc, 0, 255) << 16);
+    // __vimin_s32_relu(x, 255) = max(min(x, 255), 0)
+    return (uint32_t)__vimin_s32_relu(R, 255) | ((uint32_t)__vimin_s32_relu(G, 255) << 8) |
+           ((uint32_t)__vimin_s32_relu(Bc, 255) << 16);
 }
 
 // Random-access decoding of one sample (Sec. 4.8.1): root + SRV levels
@@ -1250,12 +1252,13 @@ __global__ void __launch_bounds__(256) k_assign(const __grid_constant__ DevStrea
 // Blocks whose taps would leave the image take the clamped path instead,
 // with base at the plane origin and the tap origin in (ox, oy).  A
 // significant predictive block's residual r^ is read from its resident tile
-// (decoded at load), `res` pointing at the tile's first value.
+// (decoded at load), `res` pointing at the tile's first value; every other
+// descriptor points at the shared zero tile, so the read needs no branch.
 constexpr uint32_t kDRef = 1u, kDNeg = 2u, kDClamp = 4u, kDInt = 8u, kDNoMC = 16u;
 
 struct NDesc {
     const int16_t *base;
-    const int16_t *res;    // residual tile, nullptr when insignificant (r^ = 0)
+    const int16_t *res;    // residual tile; the zero tile when insignificant (r^ = 0)
     uint32_t w;            // bilinear weights w00 | w10 << 8 | w01 << 16 | w11 << 24 (sum 16)
     uint32_t flags;        // kD*
     int32_t ox, oy;        // clamped path: block origin + integer part of the motion vector
@@ -1277,7 +1280,7 @@ __device__ NDesc make_ndesc(const DevStream &S, const LevelTabs &T, const Blk<BS
     const int x0 = bx * span, y0 = by * span;                  // region origin in the channel's plane
     const size_t plane = (size_t)S.W * S.H;                    // dense planes keep row stride W
     NDesc D;
-    D.res = nullptr;
+    D.res = S.ptiles;                                          // tile 0: zeros
     D.w = 16u;
     D.ox = x0;
     D.oy = y0;
@@ -1289,7 +1292,7 @@ __device__ NDesc make_ndesc(const DevStream &S, const LevelTabs &T, const Blk<BS
     const int nc = nc_index(T, l, a, b, c);
     const uint4 g = SLD(S, groups, (size_t)nc * S.ngroups + (k >> 5));
     const uint32_t bit = (uint32_t)k & 31u;
-    if ((g.x >> bit) & 1u) D.res = S.ptiles + (size_t)(g.w + __popc(g.x & ((1u << bit) - 1u))) * B * S.pstride;
+    if ((g.x >> bit) & 1u) D.res = S.ptiles + (size_t)(1u + g.w + __popc(g.x & ((1u << bit) - 1u))) * B * S.pstride;
     D.base = S.planes;
     if (!S.mc) {
         D.flags = kDNoMC;
@@ -1341,7 +1344,7 @@ __device__ __forceinline__ void eval_pair(const DevStream &S, const NDesc &D, in
             o0 = o1 = 0;
             return;
         }
-        if (D.res && !(f & kDRef) && !chk_span(S, S.ptiles, S.lim_ptiles, D.res + ti, pair ? 2 : 1)) {
+        if (!(f & kDRef) && !chk_span(S, S.ptiles, S.lim_ptiles, D.res + ti, pair ? 2 : 1)) {
             o0 = o1 = 0;
             return;
         }
@@ -1352,16 +1355,10 @@ __device__ __forceinline__ void eval_pair(const DevStream &S, const NDesc &D, in
         o1 = __ldg(D.base + p + 1);
         return;
     }
-    int r0 = 0, r1 = 0;
-    if (D.res) {
-        if (pair) {
-            const uint32_t rr = __ldg(reinterpret_cast<const uint32_t *>(D.res + ti));
-            r0 = (int)(int16_t)(rr & 0xFFFFu);
-            r1 = (int)rr >> 16;
-        } else {
-            r0 = r1 = __ldg(D.res + ti);
-        }
-    }
+    // the residual, issued before the branches below so that its latency overlaps the taps'
+    const uint32_t rr = pair ? __ldg(reinterpret_cast<const uint32_t *>(D.res + ti))
+                             : (uint32_t)(uint16_t)__ldg(D.res + ti);
+    const int r0 = (int)(int16_t)(rr & 0xFFFFu), r1 = pair ? (int)rr >> 16 : r0;
     if (f & kDNoMC) {
         o0 = r0;
         o1 = r1;
@@ -1600,8 +1597,14 @@ __global__ void __launch_bounds__(256, 4) k_decode_blocks(const __grid_constant_
                     }
                 } else {                                            // a camera's level 0
                     uint32_t *dst = cache + (size_t)slots[q] * plane + o0;
-                    if (in0) dst[0] = ycocg_to_rgb8(w0[0] + s0[0], w0[1] + s0[1], w0[2] + s0[2]);
-                    if (in1) dst[1] = ycocg_to_rgb8(w1[0] + s1[0], w1[1] + s1[1], w1[2] + s1[2]);
+                    const uint32_t c0 = ycocg_to_rgb8(w0[0] + s0[0], w0[1] + s0[1], w0[2] + s0[2]);
+                    const uint32_t c1 = ycocg_to_rgb8(w1[0] + s1[0], w1[1] + s1[1], w1[2] + s1[2]);
+                    if (in1 && !(reinterpret_cast<uintptr_t>(dst) & 7u)) {
+                        *reinterpret_cast<uint2 *>(dst) = make_uint2(c0, c1);   // both pixels, one store
+                    } else {
+                        if (in0) dst[0] = c0;
+                        if (in1) dst[1] = c1;
+                    }
                 }
             }
         }
@@ -1678,7 +1681,7 @@ __device__ __forceinline__ void blend_cached_ray(const DevStream &S, const hmlfc
 }
 
 template <int BS, int TW, int TH, bool kFallback>
-__global__ void __launch_bounds__(TW *TH / 2, 12) k_render_cached(const __grid_constant__ DevStream S,
+__global__ void __launch_bounds__(TW *TH / 4, 24) k_render_cached(const __grid_constant__ DevStream S,
                                                              const __grid_constant__ LaunchViews LV,
                                                              const uint32_t *__restrict__ camslot,
                                                              const uint32_t *__restrict__ cache, float *__restrict__ out) {
@@ -1692,8 +1695,9 @@ __global__ void __launch_bounds__(TW *TH / 2, 12) k_render_cached(const __grid_c
     const int px = (local - ty * ((V.width + TW - 1) / TW)) * TW + (int)threadIdx.x % TW;
     const int py = ty * TH + (int)threadIdx.x / TW;
     if (px >= V.width) return;
-    if (py < V.height) blend_cached_ray<BS, kFallback>(S, V, px, py, camslot, cache, out);
-    if (py + TH / 2 < V.height) blend_cached_ray<BS, kFallback>(S, V, px, py + TH / 2, camslot, cache, out);
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        if (py + k * (TH / 4) < V.height) blend_cached_ray<BS, kFallback>(S, V, px, py + k * (TH / 4), camslot, cache, out);
 }
 
 // Blend from a decoded-block cache with one slot per (camera, block) pair
@@ -2391,10 +2395,10 @@ cudaError_t launch_render_cached(const DevStream &ds, const LaunchViews &lv, int
                                  const uint32_t *cache, bool all_cameras, float *d_out, cudaStream_t st) {
     if (total_tiles <= 0) return cudaSuccess;
     if (all_cameras) {
-        HMLFC_DISPATCH_B(ds.B, (k_render_cached<BS, 16, 16, false><<<total_tiles, 128, 0, st>>>(ds, lv, camslot, cache,
+        HMLFC_DISPATCH_B(ds.B, (k_render_cached<BS, 16, 16, false><<<total_tiles, 64, 0, st>>>(ds, lv, camslot, cache,
                                                                                                  d_out)));
     } else {
-        HMLFC_DISPATCH_B(ds.B, (k_render_cached<BS, 16, 16, true><<<total_tiles, 128, 0, st>>>(ds, lv, camslot, cache,
+        HMLFC_DISPATCH_B(ds.B, (k_render_cached<BS, 16, 16, true><<<total_tiles, 64, 0, st>>>(ds, lv, camslot, cache,
                                                                                                 d_out)));
     }
     return cudaGetLastError();
