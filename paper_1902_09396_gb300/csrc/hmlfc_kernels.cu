@@ -1085,32 +1085,30 @@ __device__ __forceinline__ size_t flag_index(const DevStream &S, int i, int j, i
     return ((node * S.nblocks + k) << (2 * K)) + (size_t)(((i & (cpa - 1)) << K) | (j & (cpa - 1)));
 }
 
-// Mark the (camera, block) pairs of one tile's footprint; one warp per tile.
-// Under a projective map with w > 0 over the tile, each coordinate's extremes
-// over the tile's pixel centres are at its corner pixels, so the 4 corner
-// rays bound the footprint; the box is widened by a small margin against
-// fp32 rounding of interior rays (a pair missed all the same only sends its
-// rays to the direct decode).  A tile whose w is not positive at all corners
-// is marked ray by ray.  The lanes share the box's (camera, block) pairs.
+// Mark the (camera, block) pairs of the tiles' footprints; eight tiles per
+// warp, one per group of 4 lanes.  Under a projective map with w > 0 over the
+// tile, each coordinate's extremes over the tile's pixel centres are at its
+// corner pixels, so the 4 corner rays bound the footprint; the box is widened
+// by a margin (1e-3 in u and v, 1e-2 in s and t) orders of magnitude above
+// the fp32 rounding of interior rays.  A tile whose w is not positive at all
+// corners is marked ray by ray, with the blend's own ray arithmetic, by the
+// whole warp.  A group's lanes share its box's (camera, block) pairs.
 template <int BS, int TW, int TH, bool kSuper>
 __global__ void __launch_bounds__(256) k_mark(const __grid_constant__ DevStream S,
                                              const __grid_constant__ LaunchViews LV, int total_tiles,
                                              uint8_t *__restrict__ flags) {
-    const int lane = threadIdx.x & 31;
-    const int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (tile >= total_tiles) return;                       // uniform over the warp
-    int vi = 0;
-    if (lane == 0) vi = find_view(LV, tile);
-    vi = __shfl_sync(0xFFFFFFFFu, vi, 0);
+    const int lane = threadIdx.x & 31, q = lane & 3;
+    // eight tiles per warp, one per group of 4 lanes; each lane evaluates one corner ray of its group's tile
+    const int tile = (int)((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 8) + (lane >> 2);
+    const bool valid = tile < total_tiles;
+    const int vi = find_view(LV, valid ? tile : total_tiles - 1);
     const hmlfc_view &V = LV.views[vi];
     const int tiles_x = (V.width + TW - 1) / TW;
-    const int local = tile - LV.tile_start[vi];
+    const int local = (valid ? tile : total_tiles - 1) - LV.tile_start[vi];
     const int x0 = (local % tiles_x) * TW, y0 = (local / tiles_x) * TH;
     const int x1 = min(x0 + TW, V.width) - 1, y1 = min(y0 + TH, V.height) - 1;
     const Blk<BS> bk(S.B);
     const float eps_uv = 1e-3f, eps_st = 1e-2f;
-    // every group of 4 lanes evaluates the 4 corner rays, then a butterfly gives all lanes the extremes
-    const int q = lane & 3;
     const float X = (float)((q & 1) ? x1 : x0) + 0.5f, Y = (float)((q & 2) ? y1 : y0) + 0.5f;
     const float *h = V.H_uv, *g = V.H_st;
     const float wu = h[6] * X + h[7] * Y + h[8], ws = g[6] * X + g[7] * Y + g[8];
@@ -1120,28 +1118,37 @@ __global__ void __launch_bounds__(256) k_mark(const __grid_constant__ DevStream 
     bool ok = wu > 0.f && ws > 0.f;
 #pragma unroll
     for (int k = 0; k < 4; k++) ok = ok && lo[k] == lo[k];   // NaN
+    // a butterfly over the group's 4 lanes gives each the extremes of its tile's corners
 #pragma unroll
-    for (int o = 1; o < 4; o <<= 1)
+    for (int o = 1; o < 4; o <<= 1) {
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             lo[k] = fminf(lo[k], __shfl_xor_sync(0xFFFFFFFFu, lo[k], o));
             hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xFFFFFFFFu, hi[k], o));
         }
-    ok = __all_sync(0xFFFFFFFFu, ok);
-    if (!ok) {                                             // ray by ray
-        const int tw = x1 - x0 + 1, n = tw * (y1 - y0 + 1);
+        const int ok_other = __shfl_xor_sync(0xFFFFFFFFu, (int)ok, o);   // every lane takes part
+        ok = ok && ok_other != 0;
+    }
+    // tiles whose w is not positive at every corner: the whole warp marks them ray by ray, one at a time
+    for (unsigned bad = __ballot_sync(0xFFFFFFFFu, valid && !ok) & 0x11111111u; bad; bad &= bad - 1u) {
+        const int src = __ffs(bad) - 1;                    // the tile's group leader
+        const int bvi = __shfl_sync(0xFFFFFFFFu, vi, src);
+        const int bx0 = __shfl_sync(0xFFFFFFFFu, x0, src), by0 = __shfl_sync(0xFFFFFFFFu, y0, src);
+        const int bx1 = __shfl_sync(0xFFFFFFFFu, x1, src), by1 = __shfl_sync(0xFFFFFFFFu, y1, src);
+        const hmlfc_view &BV = LV.views[bvi];
+        const int tw = bx1 - bx0 + 1, n = tw * (by1 - by0 + 1);
         for (int e = lane; e < n; e += 32) {
-            const int py = y0 + e / tw, px = x0 + e % tw;
+            const int py = by0 + e / tw, px = bx0 + e % tw;
             Ray r;
-            ray_setup(V, S.nu, S.nv, S.W, S.H, px, py, r);
+            ray_setup(BV, S.nu, S.nv, S.W, S.H, px, py, r);
             const int ci[2] = {(r.i0 >> S.lod) << S.lod, (r.i1 >> S.lod) << S.lod};
             const int cj[2] = {(r.j0 >> S.lod) << S.lod, (r.j1 >> S.lod) << S.lod};
             const int kb[4] = {bk.div(r.y0) * S.nbx + bk.div(r.x0), bk.div(r.y0) * S.nbx + bk.div(r.x1),
                                bk.div(r.y1) * S.nbx + bk.div(r.x0), bk.div(r.y1) * S.nbx + bk.div(r.x1)};
             for (int k = 0; k < 16; k++) flags[flag_index<kSuper>(S, ci[k >> 3], cj[(k >> 2) & 1], kb[k & 3])] = 1;
         }
-        return;
     }
+    if (!valid || !ok) return;                             // no warp-wide operation follows
     const int n[4] = {S.nu, S.nv, S.W, S.H};
     int bl[4], bh[4];
 #pragma unroll
@@ -1154,21 +1161,20 @@ __global__ void __launch_bounds__(256) k_mark(const __grid_constant__ DevStream 
         bh[k] = b1;
     }
     const int bx0 = bk.div(bl[2]), by0 = bk.div(bl[3]);
-    const int nbx = bk.div(bh[2]) - bx0 + 1, nby = bk.div(bh[3]) - by0 + 1;
+    const int nbx = bk.div(bh[2]) - bx0 + 1, by1 = bk.div(bh[3]);
     const int sh = S.lod;                                  // progressive decode: one representative camera per node
     const int i0 = (bl[0] >> sh) << sh, j0 = (bl[1] >> sh) << sh;
-    const int ni = ((bh[0] - i0) >> sh) + 1, nj = ((bh[1] - j0) >> sh) + 1;
-    // lanes over the box's (camera, block row) pairs; each stores its row's blocks, whose flags lie a fixed
-    // stride apart (one block further in either layout)
-    const int n_rows = ni * nj * nby;
+    // the group's lanes take the box's (camera, block row) pairs in turn; each stores its row's blocks, whose
+    // flags lie a fixed stride apart (one block further in either layout)
     const size_t stride = kSuper ? (size_t)1 << (2 * (S.L < 2 ? S.L : 2)) : 1;
-    for (int e = lane; e < n_rows; e += 32) {
-        const int cam = e / nby, by = by0 + (e - cam * nby);
-        const int ci = cam / nj;
-        const int i = i0 + (ci << sh), j = j0 + ((cam - ci * nj) << sh);
-        uint8_t *f = flags + flag_index<kSuper>(S, i, j, by * S.nbx + bx0);
-        for (int bx = 0; bx < nbx; bx++) f[bx * stride] = 1;
-    }
+    int e = 0;
+    for (int i = i0; i <= bh[0]; i += 1 << sh)
+        for (int j = j0; j <= bh[1]; j += 1 << sh)
+            for (int by = by0; by <= by1; by++, e++) {
+                if ((e & 3) != q) continue;
+                uint8_t *f = flags + flag_index<kSuper>(S, i, j, by * S.nbx + bx0);
+                for (int bx = 0; bx < nbx; bx++) f[bx * stride] = 1;
+            }
 }
 
 // Per-camera decoded images: a call gives every camera its views reach (a
@@ -2366,7 +2372,7 @@ cudaError_t launch_render(const DevStream &ds, const LaunchViews &lv, int total_
 cudaError_t launch_mark(const DevStream &ds, const LaunchViews &lv, int total_tiles, uint8_t *flags, bool super_layout,
                         cudaStream_t st) {
     if (total_tiles <= 0) return cudaSuccess;
-    const unsigned grid = (unsigned)((total_tiles + 7) / 8);
+    const unsigned grid = (unsigned)((total_tiles + 63) / 64);   // 8 warps of 8 tiles
     if (super_layout) {
         HMLFC_DISPATCH_B(ds.B, (k_mark<BS, 16, 16, true><<<grid, 256, 0, st>>>(ds, lv, total_tiles, flags)));
     } else {

@@ -184,6 +184,38 @@ def test_render_clamped_and_degenerate_views(H, torch_cuda, tiny_streams, tiny_c
     assert np.max(np.abs(got - want)) <= RENDER_TOL
 
 
+def _sign_change_view(width, height, x_zero):
+    """A view whose projective maps share the denominator w = (X - x_zero) / 64,
+    negative left of column x_zero and positive right of it (x_zero a quarter
+    pixel off the pixel centres, so |w| >= 1/256 at every ray).  Numerators
+    c * w + a small term keep most rays inside the light field on both sides."""
+    wr = np.array([1.0 / 64.0, 0.0, -x_zero / 64.0])
+    rows_uv = [1.5 * wr + np.array([0.0, 0.002, -0.048]), 2.0 * wr + np.array([0.001, 0.0, -0.02])]
+    rows_st = [30.0 * wr + np.array([0.0, 0.2 / 64.0, -4.8 / 64.0]), 25.0 * wr + np.array([0.1 / 64.0, 0.0, -3.0 / 64.0])]
+    H_uv = np.concatenate(rows_uv + [wr]).astype(np.float32)
+    H_st = np.concatenate(rows_st + [wr]).astype(np.float32)
+    return S.View(0, width, height, H_uv, H_st)
+
+
+@pytest.mark.parametrize("path", [0, 1, 2])
+def test_render_views_whose_w_changes_sign(H, torch_cuda, tiny_streams, tiny_cfg, path):
+    """Tiles whose corner rays do not all have w > 0 are marked ray by ray;
+    the views (ragged 96x40 and 37x23, w changing sign inside) render within
+    the bound of the oracle's FP64 render on every path."""
+    c = tiny_cfg
+    enc = tiny_streams[c.qstep]
+    dec = O.Stream(enc.stream).decode_all()
+    views = [_sign_change_view(96, 40, 40.25), _sign_change_view(37, 23, 20.75), S.grid_view(1.2, 2.3, 3.5, 1.25, 48, 17)]
+    arr = S.views_to_array(views)
+    want = O.render_dense(dec, arr)
+    try:
+        H.set_render_path(path)
+        got = _render_gpu(H, torch_cuda, [H.Stream(enc.stream)], arr)
+    finally:
+        H.set_render_path(0)
+    assert np.max(np.abs(got - want)) <= RENDER_TOL
+
+
 def test_render_multiple_streams(H, torch_cuda, tiny_streams, tiny_cfg, ragged_lf):
     """Views of different light fields in one call."""
     c = tiny_cfg
