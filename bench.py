@@ -258,6 +258,14 @@ def run_diff(args):
     co_q, ro_q, losses_q = refine(st, views, target, steps=steps, quantise_aware=True, lr=0.025 * args.qstep)
     q_data = requantized_stream(st, co_q, ro_q)
     after_q = H.render_views([H.Stream(q_data)], views)
+    # the relaxation carrying the integer decode's expected rounding (HMLFC_RELAX_BIAS)
+    co0, ro0 = st.dequant()
+    relaxed_before = relaxed_render(co0, ro0, st, views).detach()
+    relaxed_before_b = relaxed_render(co0, ro0, st, views, bias=True).detach()
+    co_b, ro_b, losses_b = refine(st, views, target, steps=steps, bias=True)
+    b_data = requantized_stream(st, co_b, ro_b)
+    after_b = H.render_views([H.Stream(b_data)], views)
+    relaxed_after_b = relaxed_render(co_b, ro_b, st, views, bias=True).detach()
     n_px = c.nu * c.nv * c.width * c.height
     print(json.dumps({
         "metric": "Adam steps/s of the differentiable render (relaxed forward + adjoint + update, 32 views of 256x256)",
@@ -272,6 +280,11 @@ def run_diff(args):
         "bpp_before": len(data) * 8.0 / n_px, "bpp_after": len(new_data) * 8.0 / n_px,
         "quantise_aware": {"lr": 0.025 * args.qstep, "loss_first": losses_q[0], "loss_last": losses_q[-1],
                            "psnr_db_after_requantised": psnr(after_q, target), "bpp_after": len(q_data) * 8.0 / n_px},
+        "psnr_db_relaxed_vs_integer_before": psnr(relaxed_before, before),
+        "bias_carrying": {"psnr_db_relaxed_vs_integer_before": psnr(relaxed_before_b, before),
+                          "loss_first": losses_b[0], "loss_last": losses_b[-1],
+                          "psnr_db_relaxed_after": psnr(relaxed_after_b, target),
+                          "psnr_db_after_requantised": psnr(after_b, target), "bpp_after": len(b_data) * 8.0 / n_px},
         "gpu_launches": 2 * steps,
     }), flush=True)
 

@@ -307,6 +307,23 @@ int hmlfc_render_views_relaxed(const hmlfc_stream *const *streams, int n_streams
                                void *cuda_stream);
 
 /*
+ * hmlfc_render_views_relaxed with flags.  HMLFC_RELAX_BIAS: every rounding
+ * the relaxation drops carries its expected value, so that at the stream's
+ * own coefficients the relaxed render has no mean offset from the integer
+ * render.  A predictor with quarter-pel phase (fx, fy) = (mvx & 3, mvy & 3)
+ * adds g / 32, g = gcd(4 - fx, fx) * gcd(4 - fy, fy) (the mean of
+ * floor((S + 8) / 16) - S / 16 when S is equally likely in each residue
+ * class its weights allow; 0 for integer motion), times its sign; each >> 1
+ * of the YCoCg-R inverse becomes v / 2 - 1/4, which adds (1/2, 1/4, 1/2)
+ * levels to (R, G, B).  The terms are constants, so hmlfc_render_backward
+ * is the adjoint of both forms.  Other flag bits: HMLFC_E_INVALID_ARG.
+ */
+#define HMLFC_RELAX_BIAS 1u
+int hmlfc_render_views_relaxed_ex(const hmlfc_stream *const *streams, int n_streams, const float *const *d_coeff,
+                                  const float *const *d_root, const hmlfc_view *h_views, int n_views, uint32_t flags,
+                                  float *d_out, void *cuda_stream);
+
+/*
  * Adjoint of hmlfc_render_views_relaxed: ACCUMULATES d(<out, grad_out>) into
  * d_grad_coeff[k] (float [n_nc][H][W]) and d_grad_root[k] (float
  * [n_roots][3][H][W]) for every stream k.  Decoded tiles are recomputed,

@@ -106,6 +106,9 @@ def _bind(L):
     L.orc_render_dense.argtypes = [P, I, I, I, I, P, I, P]
     L.orc_render_pixels.argtypes = [P, P, I, P, I64, P]
     L.orc_relax_render.argtypes = [P, P, P, P, I, P]
+    L.orc_relax_render_ex.argtypes = [P, P, P, P, I, I, P]
+    L.orc_mc_rounding_bias.argtypes = [I, I]
+    L.orc_mc_rounding_bias.restype = C.c_double
     L.orc_relax_adjoint.argtypes = [P, P, I, P, P, P]
     L.orc_touched_bytes.argtypes = [P, P, I, P]
     L.orc_rgb_to_ycocg.argtypes = [I, I, I, P, P, P]
@@ -330,12 +333,15 @@ class Stream:
         _check(lib().orc_render_pixels_lod(self._h, _p(v), len(v), _p(p), len(p), level, _p(out)), "render_pixels")
         return out
 
-    def relax_render(self, coeff: np.ndarray, roots: np.ndarray, views) -> np.ndarray:
+    def relax_render(self, coeff: np.ndarray, roots: np.ndarray, views, bias: bool = False) -> np.ndarray:
+        """The relaxed render; with bias, every dropped rounding carries its
+        expected value (orc_mc_rounding_bias per predictor, -1/4 per >> 1)."""
         v = _views(views)
         co = np.ascontiguousarray(coeff, np.float64)
         ro = np.ascontiguousarray(roots, np.float64)
         out = np.zeros(_out_len(v), np.float64)
-        _check(lib().orc_relax_render(self._h, _p(co), _p(ro), _p(v), len(v), _p(out)), "relax_render")
+        _check(lib().orc_relax_render_ex(self._h, _p(co), _p(ro), _p(v), len(v), int(bool(bias)), _p(out)),
+               "relax_render")
         return out
 
     def relax_adjoint(self, views, grad_out: np.ndarray):
@@ -369,3 +375,9 @@ def psnr(a: np.ndarray, b: np.ndarray, peak: float = 255.0) -> float:
     d = a.astype(np.float64) - b.astype(np.float64)
     mse = float(np.mean(d * d))
     return float("inf") if mse == 0 else 10.0 * np.log10(peak * peak / mse)
+
+
+def mc_rounding_bias(mvx: int, mvy: int) -> float:
+    """Expected rounding of the integer predictor at quarter-pel motion
+    (mvx, mvy) against its exact weighted sum (orc_mc_rounding_bias)."""
+    return float(lib().orc_mc_rounding_bias(int(mvx), int(mvy)))

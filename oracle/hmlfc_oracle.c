@@ -1314,8 +1314,26 @@ static void relax_taps(const geom *g, int x, int y, int mvx, int mvy, int tx[4],
     tx[3] = xb; ty[3] = yb; tw[3] = fx * fy / 16.0;
 }
 
+/* Expected rounding of the integer predictor (Sec. 4.4 filter, +8 >> 4)
+ * against the exact weighted sum S / 16, over reference values whose sum
+ * is equally likely in every residue class its weights allow: the four
+ * weights (4 - fx)(4 - fy), fx(4 - fy), (4 - fx)fy, fx fy share the factor
+ * g = gcd(4 - fx, fx) * gcd(4 - fy, fy), S + 8 takes the residues 0, g, ..,
+ * 16 - g mod 16 (mean 8 - g/2), so floor((S + 8) / 16) - S / 16 averages
+ * g / 32.  Integer motion (g = 16) rounds nothing. */
+static int gcd4(int f) { return f == 0 ? 4 : (f == 2 ? 2 : 1); }
+
+double orc_mc_rounding_bias(int mvx, int mvy) {
+    int fx = mvx & 3, fy = mvy & 3;
+    if (fx == 0 && fy == 0) return 0.0;
+    return gcd4(fx) * gcd4(fy) / 32.0;
+}
+
+/* with `bias`, each operation the relaxation drops carries its expected
+ * value: every predictor its rounding bias above, each >> 1 of the YCoCg-R
+ * inverse -1/4 (floor(v/2) - v/2 over both parities). */
 static void relax_sample(const orc_stream *s, const double *coeff, const double *roots, int i, int j, int x, int y,
-                         double rgb[3]) {
+                         int bias, double rgb[3]) {
     const geom *g = &s->g;
     size_t plane = (size_t)g->W * g->H;
     int L = g->L;
@@ -1334,20 +1352,22 @@ static void relax_sample(const orc_stream *s, const double *coeff, const double 
                 mv_of(s, nc, k, &mvx, &mvy, &sign);
                 relax_taps(g, x, y, mvx, mvy, tx, ty, tw);
                 int64_t rnc = nc_of(g, l, a & ~1, b & ~1, c);
-                for (int t = 0; t < 4; t++) v[c] += sign * tw[t] * coeff[(size_t)rnc * plane + (size_t)ty[t] * g->W + tx[t]];
+                double p = bias ? orc_mc_rounding_bias(mvx, mvy) : 0.0;
+                for (int t = 0; t < 4; t++) p += tw[t] * coeff[(size_t)rnc * plane + (size_t)ty[t] * g->W + tx[t]];
+                v[c] += sign * p;
             }
         }
     }
-    double t = v[0] - v[2] / 2.0;
+    double t = v[0] - v[2] / 2.0 + (bias ? 0.25 : 0.0);
     double G = v[2] + t;
-    double Bb = t - v[1] / 2.0;
+    double Bb = t - v[1] / 2.0 + (bias ? 0.25 : 0.0);
     rgb[0] = Bb + v[1];
     rgb[1] = G;
     rgb[2] = Bb;
 }
 
-int orc_relax_render(const orc_stream *s, const double *coeff, const double *roots, const orc_view *views,
-                     int nviews, double *out) {
+int orc_relax_render_ex(const orc_stream *s, const double *coeff, const double *roots, const orc_view *views,
+                        int nviews, int bias, double *out) {
     const geom *g = &s->g;
     if (g->sub) return ORC_E_ARG;          /* the relaxation is defined on full-resolution chroma only */
     for (int vi = 0; vi < nviews; vi++) {
@@ -1365,13 +1385,18 @@ int orc_relax_render(const orc_stream *s, const double *coeff, const double *roo
                             for (int ys = 0; ys < 2; ys++) {
                                 double w = r.wu[a] * r.wv[b] * r.ws[xs] * r.wt[ys];
                                 double rgb[3];
-                                relax_sample(s, coeff, roots, r.i[a], r.j[b], r.x[xs], r.y[ys], rgb);
+                                relax_sample(s, coeff, roots, r.i[a], r.j[b], r.x[xs], r.y[ys], bias, rgb);
                                 for (int c = 0; c < 3; c++) acc[c] += w * rgb[c];
                             }
                 for (int c = 0; c < 3; c++) o[((size_t)py * v->width + px) * 3 + c] = acc[c] / 255.0;
             }
     }
     return ORC_OK;
+}
+
+int orc_relax_render(const orc_stream *s, const double *coeff, const double *roots, const orc_view *views,
+                     int nviews, double *out) {
+    return orc_relax_render_ex(s, coeff, roots, views, nviews, 0, out);
 }
 
 /* Transpose of orc_relax_render: accumulates into grad_coeff [n_nc][H][W]

@@ -84,6 +84,7 @@ def lib() -> C.CDLL:
     L.hmlfc_check_status.argtypes = [P, P]
     L.hmlfc_render_views.argtypes = [P, I, P, I, P, P]
     L.hmlfc_render_views_relaxed.argtypes = [P, I, P, P, P, I, P, P]
+    L.hmlfc_render_views_relaxed_ex.argtypes = [P, I, P, P, P, I, C.c_uint32, P, P]
     L.hmlfc_render_backward.argtypes = [P, I, P, I, P, P, P, P]
     L.hmlfc_dequant.argtypes = [P, P, P, P]
     L.hmlfc_encode.argtypes = [P, I, I, I, I, C.POINTER(EncodeParams), C.POINTER(P), C.POINTER(SZ)]
@@ -270,15 +271,20 @@ def set_batch_tuning(tile_shape: int = 0, group: int = 4, ctas_per_sm: int = 8, 
     _check(lib().hmlfc_set_batch_tuning(int(tile_shape), int(group), int(ctas_per_sm), int(cache_bytes)))
 
 
-def render_views_relaxed(streams, coeffs, roots, views, out=None, cuda_stream=None):
+RELAX_BIAS = 1
+
+
+def render_views_relaxed(streams, coeffs, roots, views, out=None, cuda_stream=None, bias: bool = False):
+    """The relaxed render; with bias, each rounding it drops carries its
+    expected value (HMLFC_RELAX_BIAS)."""
     import torch
     va = _views_array(views)
     if out is None:
         out = torch.empty(out_size(views), dtype=torch.float32, device=torch.device("cuda", streams[0].device))
     cp = (C.c_void_p * len(streams))(*[int(t.data_ptr()) for t in coeffs])
     rp = (C.c_void_p * len(streams))(*[int(t.data_ptr()) for t in roots])
-    _check(lib().hmlfc_render_views_relaxed(_streams_array(streams), len(streams), cp, rp, va, len(va), _ptr(out),
-                                            _stream_handle(cuda_stream)))
+    _check(lib().hmlfc_render_views_relaxed_ex(_streams_array(streams), len(streams), cp, rp, va, len(va),
+                                               RELAX_BIAS if bias else 0, _ptr(out), _stream_handle(cuda_stream)))
     return out
 
 

@@ -1082,7 +1082,16 @@ int hmlfc_server_stats(const hmlfc_server *sv, void *cuda_stream, int64_t *out3)
 int hmlfc_render_views_relaxed(const hmlfc_stream *const *streams, int n_streams, const float *const *d_coeff,
                                const float *const *d_root, const hmlfc_view *h_views, int n_views, float *d_out,
                                void *cuda_stream) {
+    return hmlfc_render_views_relaxed_ex(streams, n_streams, d_coeff, d_root, h_views, n_views, 0u, d_out,
+                                         cuda_stream);
+}
+
+int hmlfc_render_views_relaxed_ex(const hmlfc_stream *const *streams, int n_streams, const float *const *d_coeff,
+                                  const float *const *d_root, const hmlfc_view *h_views, int n_views, uint32_t flags,
+                                  float *d_out, void *cuda_stream) {
     NvtxRange nvtx_range("hmlfc render_views_relaxed");
+    if (flags & ~HMLFC_RELAX_BIAS) return fail(HMLFC_E_INVALID_ARG, "unknown relaxation flags 0x%x", flags);
+    const bool bias = (flags & HMLFC_RELAX_BIAS) != 0;
     int rc = check_views(streams, n_streams, h_views, n_views);
     if (rc != HMLFC_OK) return rc;
     for (int k = 0; k < n_streams; k++)
@@ -1098,7 +1107,7 @@ int hmlfc_render_views_relaxed(const hmlfc_stream *const *streams, int n_streams
                                const int k = lv.views[0].lf;
                                if (!d_coeff[k] || !d_root[k]) return fail(HMLFC_E_INVALID_ARG, "NULL coefficients");
                                const cudaError_t e =
-                                   launch_render_relaxed(s->ds, lv, tiles, d_coeff[k], d_root[k], d_out, st);
+                                   launch_render_relaxed(s->ds, lv, tiles, d_coeff[k], d_root[k], d_out, bias, st);
                                return e == cudaSuccess ? HMLFC_OK : cuda_fail(e, "relaxed render launch");
                            });
 }

@@ -132,8 +132,9 @@ cudaError_t launch_batch(int B, int tile_shape, const void *image, const int *pt
                          uint8_t *flags, uint32_t *slotmap, uint4 *items, unsigned long long *counters,
                          unsigned int *work, uint32_t *cache, uint32_t capacity, int64_t n_ck, int group,
                          int persistent_ctas, float *d_out, cudaEvent_t const *phase, cudaStream_t st);
+// bias: the forward carries the expected rounding of the integer decode.
 cudaError_t launch_render_relaxed(const DevStream &ds, const LaunchViews &lv, int total_tiles, const float *coeff,
-                                  const float *root, float *d_out, cudaStream_t st);
+                                  const float *root, float *d_out, bool bias, cudaStream_t st);
 cudaError_t launch_render_backward(const DevStream &ds, const LaunchViews &lv, int total_tiles,
                                    const float *grad_out, float *grad_coeff, float *grad_root, cudaStream_t st);
 cudaError_t launch_dequant(const DevStream &ds, int64_t n_nc, float *coeff, float *root, cudaStream_t st);

@@ -870,12 +870,26 @@ __device__ __forceinline__ void relax_taps(const DevStream &S, int x, int y, int
     t.x[3] = xb; t.y[3] = yb; t.w[3] = (float)(fx * fy) * 0.0625f;
 }
 
+// Expected rounding of the integer predictor (+8 >> 4) against its exact
+// weighted sum S / 16 when S is equally likely in every residue class its
+// weights allow: the weights share g = gcd(4 - fx, fx) * gcd(4 - fy, fy),
+// so floor((S + 8) / 16) - S / 16 averages g / 32 (0 for integer motion).
+__device__ __forceinline__ float mc_rounding_bias(int mvx, int mvy) {
+    const int fx = mvx & 3, fy = mvy & 3;
+    if ((fx | fy) == 0) return 0.f;
+    const int gx = fx == 0 ? 4 : (fx == 2 ? 2 : 1), gy = fy == 0 ? 4 : (fy == 2 ? 2 : 1);
+    return (float)(gx * gy) * (1.0f / 32.0f);
+}
+
+// bias (forward only): every rounding the relaxation drops carries its
+// expected value -- each predictor mc_rounding_bias, each >> 1 of the YCoCg-R
+// inverse -1/4.  The adjoint does not depend on it (the terms are constant).
 template <int BS, bool kBackward>
 __global__ void __launch_bounds__(256) k_relax(const __grid_constant__ DevStream S,
                                               const __grid_constant__ LaunchViews LV, const float *__restrict__ coeff,
                                               const float *__restrict__ root, float *__restrict__ out,
                                               const float *__restrict__ gout, float *__restrict__ gcoeff,
-                                              float *__restrict__ groot) {
+                                              float *__restrict__ groot, int bias) {
     constexpr int TW = 16, TH = 16;
     __shared__ LevelTabs T;
     __shared__ int s_view;
@@ -929,15 +943,16 @@ __global__ void __launch_bounds__(256) k_relax(const __grid_constant__ DevStream
                         RelaxTap t;
                         relax_taps(S, x, y, mvx, mvy, t);
                         const int rnc = nc_index(T, l, na & ~1, nb & ~1, c);
-                        float p = 0.f;
+                        float p = bias ? mc_rounding_bias(mvx, mvy) : 0.f;
                         for (int q = 0; q < 4; q++) p += t.w[q] * coeff[(size_t)rnc * plane + (size_t)t.y[q] * S.W + t.x[q]];
                         v[c] += (float)sign * p;
                     }
                 }
             }
-            const float tt = v[0] - 0.5f * v[2];
+            const float rb2 = bias ? 0.25f : 0.f;
+            const float tt = v[0] - 0.5f * v[2] + rb2;
             const float G = v[2] + tt;
-            const float Bc = tt - 0.5f * v[1];
+            const float Bc = tt - 0.5f * v[1] + rb2;
             acc[0] += w * (Bc + v[1]);
             acc[1] += w * G;
             acc[2] += w * Bc;
@@ -2542,10 +2557,10 @@ cudaError_t launch_resident(const DevStream &ds, const uint8_t *flags, int64_t n
 }
 
 cudaError_t launch_render_relaxed(const DevStream &ds, const LaunchViews &lv, int total_tiles, const float *coeff,
-                                  const float *root, float *d_out, cudaStream_t st) {
+                                  const float *root, float *d_out, bool bias, cudaStream_t st) {
     if (total_tiles <= 0) return cudaSuccess;
     HMLFC_DISPATCH_B(ds.B, (k_relax<BS, false><<<total_tiles, 256, 0, st>>>(ds, lv, coeff, root, d_out, nullptr,
-                                                                            nullptr, nullptr)));
+                                                                            nullptr, nullptr, bias ? 1 : 0)));
     return cudaGetLastError();
 }
 
@@ -2553,7 +2568,7 @@ cudaError_t launch_render_backward(const DevStream &ds, const LaunchViews &lv, i
                                    const float *grad_out, float *grad_coeff, float *grad_root, cudaStream_t st) {
     if (total_tiles <= 0) return cudaSuccess;
     HMLFC_DISPATCH_B(ds.B, (k_relax<BS, true><<<total_tiles, 256, 0, st>>>(ds, lv, nullptr, nullptr, nullptr,
-                                                                           grad_out, grad_coeff, grad_root)));
+                                                                           grad_out, grad_coeff, grad_root, 0)));
     return cudaGetLastError();
 }
 

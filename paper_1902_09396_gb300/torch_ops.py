@@ -19,13 +19,14 @@ from . import Stream, render_backward, render_views_relaxed, requantize
 
 class RelaxedRender(torch.autograd.Function):
     """out = render(coeff, root) for one stream; views is a numpy array of
-    96-byte view records (lf = 0)."""
+    96-byte view records (lf = 0).  bias adds the expected rounding of the
+    integer decode (constant terms: the same adjoint)."""
 
     @staticmethod
-    def forward(ctx, coeff: torch.Tensor, root: torch.Tensor, stream: Stream, views):
+    def forward(ctx, coeff: torch.Tensor, root: torch.Tensor, stream: Stream, views, bias: bool = False):
         coeff = coeff.contiguous()
         root = root.contiguous()
-        out = render_views_relaxed([stream], [coeff], [root], views)
+        out = render_views_relaxed([stream], [coeff], [root], views, bias=bias)
         ctx.stream = stream
         ctx.views = views
         ctx.shapes = (coeff.shape, root.shape)
@@ -36,11 +37,11 @@ class RelaxedRender(torch.autograd.Function):
         gc = torch.zeros(ctx.shapes[0], dtype=torch.float32, device=grad_out.device)
         gr = torch.zeros(ctx.shapes[1], dtype=torch.float32, device=grad_out.device)
         render_backward([ctx.stream], ctx.views, grad_out.contiguous().float(), [gc], [gr])
-        return gc, gr, None, None
+        return gc, gr, None, None, None
 
 
-def relaxed_render(coeff, root, stream, views):
-    return RelaxedRender.apply(coeff, root, stream, views)
+def relaxed_render(coeff, root, stream, views, bias: bool = False):
+    return RelaxedRender.apply(coeff, root, stream, views, bias)
 
 
 def _ste_round(x: torch.Tensor, step: float) -> torch.Tensor:
@@ -49,14 +50,16 @@ def _ste_round(x: torch.Tensor, step: float) -> torch.Tensor:
 
 
 def refine(stream: Stream, views, target: torch.Tensor, steps: int = 200, lr: float | None = None,
-           refine_roots: bool = True, log_every: int = 0, quantise_aware: bool = False):
+           refine_roots: bool = True, log_every: int = 0, quantise_aware: bool = False, bias: bool = False):
     """Adam on the dequantised coefficients (and roots) of a stream so that
     its relaxed render approaches `target`; returns (coeff, root, losses).
 
     With quantise_aware the forward pass renders the coefficients rounded to
     the stream's quantiser step (and the roots to integers) while the
     gradient passes straight through, so that the optimum survives the
-    re-quantisation."""
+    re-quantisation.  With bias the relaxed render carries the integer
+    decode's expected rounding, so that its optimum is not offset from the
+    integer render's."""
     coeff, root = stream.dequant()
     coeff = coeff.clone().requires_grad_(True)
     root = root.clone().requires_grad_(refine_roots)
@@ -68,9 +71,9 @@ def refine(stream: Stream, views, target: torch.Tensor, steps: int = 200, lr: fl
     for it in range(steps):
         opt.zero_grad(set_to_none=True)
         if quantise_aware:
-            out = relaxed_render(_ste_round(coeff, float(q)), _ste_round(root, 1.0), stream, views)
+            out = relaxed_render(_ste_round(coeff, float(q)), _ste_round(root, 1.0), stream, views, bias)
         else:
-            out = relaxed_render(coeff, root, stream, views)
+            out = relaxed_render(coeff, root, stream, views, bias)
         loss = torch.mean((out - target) ** 2)
         loss.backward()
         opt.step()

@@ -272,6 +272,35 @@ def test_relaxed_forward_and_adjoint(H, torch_cuda, tiny_streams, tiny_cfg):
     assert np.max(np.abs(gr.cpu().numpy() - wr)) <= 1e-5 * scale
 
 
+@pytest.mark.parametrize("mc", [O.MC_QPEL, O.MC_INTEGER, O.MC_OFF])
+def test_relaxed_forward_with_bias(H, torch_cuda, tiny_lf, tiny_cfg, mc):
+    """The relaxation carrying the expected rounding (HMLFC_RELAX_BIAS) vs the
+    oracle's, at the stream's dequantised coefficients and at random ones;
+    unknown flag bits are refused."""
+    import ctypes as C
+    torch = torch_cuda
+    c = tiny_cfg
+    data = O.encode(tiny_lf, c.levels, c.block, c.search, 4, mc=mc).stream
+    ost = O.Stream(data)
+    st = H.Stream(data)
+    arr = S.views_to_array(_views_mix(c, 37, 3, [(32, 32), (21, 19)]))
+    rng = np.random.default_rng(38)
+    co0, ro0 = ost.dequant()
+    for co, ro in ((co0, ro0), (rng.standard_normal(co0.shape) * 20, rng.standard_normal(ro0.shape) * 20)):
+        want = ost.relax_render(co, ro, arr, bias=True)
+        got = H.render_views_relaxed([st], [torch.tensor(co, dtype=torch.float32, device="cuda")],
+                                     [torch.tensor(ro, dtype=torch.float32, device="cuda")], arr, bias=True)
+        torch.cuda.synchronize()
+        assert np.max(np.abs(got.cpu().numpy() - want)) <= 1e-5 * max(1.0, np.max(np.abs(want)))
+    lib = H.lib()
+    va = H._views_array(arr)
+    out = torch.zeros(H.out_size(arr), dtype=torch.float32, device="cuda")
+    cp = (C.c_void_p * 1)(int(torch.zeros(1, device="cuda").data_ptr()))
+    rc = lib.hmlfc_render_views_relaxed_ex(H._streams_array([st]), 1, cp, cp, va, len(va), 6,
+                                           C.c_void_p(int(out.data_ptr())), None)
+    assert rc == H.E_INVALID_ARG
+
+
 def test_requantize_round_trip(H, torch_cuda, tiny_streams, tiny_cfg):
     """Re-encoding a stream's own dequantised coefficients reproduces a
     stream that decodes to the same samples."""

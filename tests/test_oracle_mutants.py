@@ -61,6 +61,10 @@ MUTANTS = {
     "chroma_root_bytes": ("size_t rp = ((size_t)(i >> g->L) * g->gv[g->L] + (j >> g->L)) * g->npx + g->coff[c] +",
                           "size_t rp = ((size_t)(i >> g->L) * g->gv[g->L] + (j >> g->L)) * g->npx + g->coff[0] +",
                           ["chroma_touched"]),
+    "relax_bias_ycocg_sign": ("double t = v[0] - v[2] / 2.0 + (bias ? 0.25 : 0.0);",
+                              "double t = v[0] - v[2] / 2.0 - (bias ? 0.25 : 0.0);", ["relax_bias_ycocg"]),
+    "mc_rounding_bias_scale": ("return gcd4(fx) * gcd4(fy) / 32.0;", "return gcd4(fx) * gcd4(fy) / 16.0;",
+                               ["mc_rounding_bias"]),
     "progressive_one_level_too_deep": ("for (int l = lod; l < L; l++)", "for (int l = lod > 0 ? lod - 1 : 0; l < L; l++)",
                                        ["progressive"]),
 }
@@ -103,6 +107,10 @@ def _run(name, tiny_lf, tiny_cfg, ragged_lf):
         pins.test_chroma_420_lossless_luma_and_filter_closed_form(tiny_lf, tiny_cfg, ragged_lf, O.MC_QPEL)
     elif name == "chroma_touched":
         pins.test_chroma_420_touched_bytes_closed_form(tiny_cfg)
+    elif name == "relax_bias_ycocg":
+        pins.test_relax_bias_ycocg_closed_form(tiny_lf, tiny_cfg)
+    elif name == "mc_rounding_bias":
+        pins.test_mc_rounding_bias_equals_brute_force()
     elif name == "progressive":
         pins.test_progressive_lossless_equals_level_images(tiny_lf, tiny_cfg, ragged_lf, O.MC_QPEL)
     else:

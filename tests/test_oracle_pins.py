@@ -903,3 +903,52 @@ def test_chroma_420_render_equals_dense_render(tiny_lf, tiny_cfg):
     got = st.render_pixels(views, pix)
     idx = (views["out_offset"][pix[:, 0]] + (pix[:, 2] * 40 + pix[:, 1]) * 3)[:, None] + np.arange(3)[None, :]
     assert np.max(np.abs(got - dense[idx])) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# the relaxation carrying the expected rounding of the integer decode
+# --------------------------------------------------------------------------
+
+def test_mc_rounding_bias_equals_brute_force():
+    """floor((S + 8) / 16) - S / 16 averaged over every residue of four
+    reference values (0..15 each) equals the oracle's predictor bias at every
+    quarter-pel phase, for negative vectors too (Sec. 4.4 filter)."""
+    a = np.stack(np.meshgrid(*[np.arange(16)] * 4, indexing="ij"), -1).reshape(-1, 4)
+    for mvx in range(-5, 5):
+        for mvy in range(-5, 5):
+            fx, fy = mvx & 3, mvy & 3
+            w = np.array([(4 - fx) * (4 - fy), fx * (4 - fy), (4 - fx) * fy, fx * fy])
+            s = a @ w
+            want = float(np.mean(np.floor((s + 8) / 16.0) - s / 16.0))
+            assert O.mc_rounding_bias(mvx, mvy) == pytest.approx(want, abs=1e-12), (mvx, mvy)
+
+
+def test_relax_bias_ycocg_closed_form(tiny_lf, tiny_cfg):
+    """Without motion compensation the biased relaxation is the relaxation
+    plus (1/2, 1/4, 1/2) levels in (R, G, B): each >> 1 of the YCoCg-R
+    inverse averages v/2 - 1/4, t carries +1/4, B = t - Co/2 twice that."""
+    c = tiny_cfg
+    st = O.Stream(O.encode(tiny_lf, c.levels, c.block, c.search, 4, mc=O.MC_OFF).stream)
+    co, ro = st.dequant()
+    geo = S.lf_geometry(c.nu, c.nv, c.width, c.height)
+    views = S.views_to_array(S.random_views(21, geo, 2, [(19, 13)]))
+    d = (st.relax_render(co, ro, views, bias=True) - st.relax_render(co, ro, views)).reshape(-1, 3) * 255.0
+    assert np.max(np.abs(d - np.array([0.5, 0.25, 0.5]))) < 1e-9
+
+
+@pytest.mark.parametrize("mc", [O.MC_OFF, O.MC_QPEL])
+def test_relax_bias_removes_the_mean_offset(tiny_lf, tiny_cfg, mc):
+    """At the dequantised coefficients the integer render exceeds the plain
+    relaxation by about (1/2, 1/4, 1/2) levels on average; the biased
+    relaxation leaves no mean offset (within 0.05 level per channel)."""
+    c = tiny_cfg
+    st = O.Stream(O.encode(tiny_lf, c.levels, c.block, c.search, 4, mc=mc).stream)
+    co, ro = st.dequant()
+    geo = S.lf_geometry(c.nu, c.nv, c.width, c.height)
+    views = S.views_to_array(S.random_views(3, geo, 6, [(64, 64)]))
+    ri = O.render_dense(st.decode_all(), views)
+    plain = ((ri - st.relax_render(co, ro, views)).reshape(-1, 3) * 255.0).mean(0)
+    biased = ((ri - st.relax_render(co, ro, views, bias=True)).reshape(-1, 3) * 255.0).mean(0)
+    assert np.all(np.abs(plain - np.array([0.5, 0.25, 0.5])) < 0.05), plain
+    assert np.all(np.abs(biased) < 0.05), biased
+
