@@ -1467,7 +1467,7 @@ __device__ __forceinline__ bool item_desc(const DevStream &S, const LevelTabs &T
 // serves more pixel work.  Each thread decodes two horizontally adjacent
 // pixels, which share the descriptor reads and four of their six taps.
 template <int BS>
-__global__ void __launch_bounds__(256, 4) k_decode_blocks(const __grid_constant__ DevStream S,
+__global__ void __launch_bounds__(256, 5) k_decode_blocks(const __grid_constant__ DevStream S,
                                                       const uint4 *__restrict__ items,
                                                       const unsigned long long *__restrict__ counters,
                                                       const uint32_t *__restrict__ camslot,
