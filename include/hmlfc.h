@@ -258,21 +258,23 @@ int hmlfc_render_views_noalloc(const hmlfc_stream *const *streams, int n_streams
 
 /*
  * Batched form of hmlfc_render_views (same results): all views of all
- * streams in one pass -- one launch each of footprint marking, slot
- * assignment, a persistent block decode and a persistent render whose CTAs
- * take (view, tile) items from an atomic counter.  The call's view records
- * and stream descriptors are copied into stream-ordered scratch by kernels
- * whose parameters carry them, so the call can be captured in a CUDA graph
- * and replayed without touching host memory.  Streams must share one block
- * size (otherwise this falls back to hmlfc_render_views).
+ * streams in one pass -- one launch each of footprint marking, camera-image
+ * and item assignment, a block decode over every stream's items and a
+ * persistent blend whose CTAs take (view, tile) items from an atomic
+ * counter.  The camera images of all streams share one pool (cameras beyond
+ * it decode their rays directly).  The call's view records and stream
+ * descriptors are copied into stream-ordered scratch by kernels whose
+ * parameters carry them, so the call can be captured in a CUDA graph and
+ * replayed without touching host memory.  Streams may differ in block size
+ * and chroma mode.
  */
 int hmlfc_render_batch(const hmlfc_stream *const *streams, int n_streams, const hmlfc_view *h_views, int n_views,
                        float *d_out, void *cuda_stream);
 
 /* Tunables of hmlfc_render_batch (process-wide): rays per tile (0: 16x16,
- * 1: 32x8, 2: 8x8), decode items per pass (1-8), persistent CTAs per SM
- * (1-32), decoded-block cache bytes (0 keeps the current value; default
- * 2 GiB).  Chosen per workload by the package's autotuner. */
+ * 1: 32x8, 2: 8x8), decode items per pass (1-8; above 4 act as 4), decode
+ * CTAs launched per SM (1-32), camera-image pool bytes (0 keeps the current
+ * value; default 2 GiB).  Chosen per workload by the package's autotuner. */
 int hmlfc_set_batch_tuning(int tile_shape, int group, int ctas_per_sm, size_t cache_bytes);
 
 /*

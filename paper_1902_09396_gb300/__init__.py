@@ -19,7 +19,7 @@ from .build import LIB, build  # noqa: F401
 
 # Identifies the render kernel's code; profile figures recorded for another
 # version are not reused.
-KERNEL_VERSION = "render-cached-v14"
+KERNEL_VERSION = "render-cached-v15"
 ENCODER_VERSION = "encode-planes-v4"
 
 OK, E_INVALID_ARG, E_CORRUPT, E_OOM, E_CUDA, E_TIMEOUT, E_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6

@@ -1,8 +1,9 @@
 """Autotuner of the batched render (hmlfc_render_batch).
 
 Candidates: rays per tile (16x16, 32x8, 8x8), decode items per pass (1, 2,
-4, 8 -- how many (level-1 node, block) items a CTA stages descriptors for
-before decoding them) and persistent CTAs per SM (2, 4, 8).  Each candidate
+4 -- how many (level-2 node, block) items a CTA builds descriptors for
+before decoding them) and decode CTAs launched per SM (5: all resident,
+10, 32).  Each candidate
 renders the caller's own batch a few times under CUDA events; the fastest is
 set and remembered per workload signature (stream shapes and the histogram of
 view sizes) in a JSON file next to the built library.
@@ -19,7 +20,7 @@ import numpy as np
 from . import render_batch, set_batch_tuning
 from .build import OUT_DIR
 
-CANDIDATES = [(t, g, c) for t in (0, 1, 2) for g in (1, 2, 4, 8) for c in (2, 4, 8)]
+CANDIDATES = [(t, g, c) for t in (0, 1, 2) for g in (1, 2, 4) for c in (5, 10, 32)]
 CACHE_FILE = OUT_DIR / "autotune.json"
 
 

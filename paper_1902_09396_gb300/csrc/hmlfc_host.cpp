@@ -902,11 +902,10 @@ int hmlfc_render_batch(const hmlfc_stream *const *streams, int n_streams, const 
     if (rc != HMLFC_OK) return rc;
     if (n_views > 0 && !d_out) return fail(HMLFC_E_INVALID_ARG, "d_out is NULL");
     if (n_views == 0) return HMLFC_OK;
-    for (int k = 0; k < n_streams; k++)
-        // one kernel instantiation per call: equal block sizes only; the batched decode reads full-resolution
-        // chroma only
-        if (streams[k]->g.B != streams[0]->g.B || streams[k]->g.sub)
-            return hmlfc_render_views(streams, n_streams, h_views, n_views, d_out, cuda_stream);
+    // one kernel instantiation per call: the streams' common block size, or the generic one when they differ
+    int B = streams[0]->g.B;
+    for (int k = 1; k < n_streams; k++)
+        if (streams[k]->g.B != B) B = 0;
     const int dev = streams[0]->device;
     DeviceGuard guard(dev);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
@@ -926,7 +925,7 @@ int hmlfc_render_batch(const hmlfc_stream *const *streams, int n_streams, const 
     }
     tile_start.push_back((int)tiles);
     if (views.empty()) return HMLFC_OK;
-    int64_t n_keys = 0, n_ck = 0;
+    int64_t n_keys = 0, n_sk = 0, n_cam = 0;
     const size_t lf_bytes = batch_lf_bytes(), hdr_bytes = batch_hdr_bytes();
     auto a16 = [](size_t v) { return (v + 15) & ~(size_t)15; };
     int offs[4];
@@ -938,19 +937,21 @@ int hmlfc_render_batch(const hmlfc_stream *const *streams, int n_streams, const 
     std::vector<unsigned char> img(img_bytes, 0);
     for (int k = 0; k < n_streams; k++) {
         const Geometry &g = streams[k]->g;
-        batch_fill_lf(img.data() + offs[1] + lf_bytes * k, streams[k]->ds, n_keys, n_ck);
-        n_keys += (int64_t)g.nu * g.nv * g.nblocks;
-        n_ck += (int64_t)g.gu[1] * g.gv[1] * g.nblocks;
+        const int K = g.L < 2 ? g.L : 2;
+        const int64_t sk = (int64_t)g.gu[K] * g.gv[K] * g.nblocks;
+        batch_fill_lf(img.data() + offs[1] + lf_bytes * k, streams[k]->ds, n_keys, n_sk, n_cam);
+        n_keys += (((sk << (2 * K)) + 15) / 16) * 16;     // each light field's flags start on 16 bytes
+        n_sk += sk;
+        n_cam += (int64_t)g.nu * g.nv;
     }
-    batch_fill_hdr(img.data(), n_streams, (int)views.size(), (int)tiles, TW, TH, n_keys, n_ck);
+    batch_fill_hdr(img.data(), n_streams, (int)views.size(), (int)tiles, TW, TH, n_keys, n_sk, n_cam);
     std::memcpy(img.data() + offs[2], views.data(), sizeof(hmlfc_view) * views.size());
     std::memcpy(img.data() + offs[3], tile_start.data(), sizeof(int) * tile_start.size());
-    const int B = streams[0]->g.B;
-    const size_t blk_bytes = (size_t)B * B * 4;
-    const uint32_t capacity = (uint32_t)std::min<int64_t>({n_keys, (int64_t)(g_batch.cache_bytes / blk_bytes), kMaxSlots});
+    // the image pool: camera images of W x H RGB8 pixels (u32), offsets below 2^31 so that kNone stays apart
+    const unsigned long long capacity = std::min<unsigned long long>(g_batch.cache_bytes / 4, (unsigned long long)kMaxSlots);
     const size_t o_flags = up256(img_bytes), o_slot = up256(o_flags + (size_t)n_keys),
-                 o_items = up256(o_slot + (size_t)n_keys * 4), o_count = up256(o_items + (size_t)n_ck * 16),
-                 o_cache = up256(o_count + 16), total = up256(o_cache + (size_t)capacity * blk_bytes);
+                 o_items = up256(o_slot + (size_t)n_cam * 4), o_count = up256(o_items + (size_t)n_sk * 16),
+                 o_cache = up256(o_count + 24), total = up256(o_cache + (size_t)capacity * 4);
     void *base = nullptr;
     cudaError_t e = cudaMallocAsync(&base, total, st);
     if (e != cudaSuccess) {
@@ -958,15 +959,26 @@ int hmlfc_render_batch(const hmlfc_stream *const *streams, int n_streams, const 
         return hmlfc_render_views(streams, n_streams, h_views, n_views, d_out, cuda_stream);
     }
     uint8_t *b = static_cast<uint8_t *>(base);
+    BatchLaunch L;
+    L.total_tiles = (int)tiles;
+    L.flags = b + o_flags;
+    L.camslot = reinterpret_cast<uint32_t *>(b + o_slot);
+    L.items = reinterpret_cast<uint4 *>(b + o_items);
+    L.counters = reinterpret_cast<unsigned long long *>(b + o_count);
+    L.work = reinterpret_cast<unsigned int *>(b + o_count + 16);
+    L.cache = reinterpret_cast<uint32_t *>(b + o_cache);
+    L.capacity = capacity;
+    L.n_sk = n_sk;
+    L.n_cam = n_cam;
+    L.group = g_batch.group;
+    L.sm_count = sm_count(dev);
+    L.decode_ctas = L.sm_count * g_batch.ctas_per_sm;
+    L.d_out = d_out;
     e = launch_copy_blob(img.data(), (int)img_bytes, b, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b + o_flags, 0, (size_t)n_keys, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b + o_count, 0, 16, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b + o_count, 0, 24, st);
     if (e == cudaSuccess)
-        e = launch_batch(B, g_batch.tile_shape, b, offs, (int)tiles, b + o_flags, reinterpret_cast<uint32_t *>(b + o_slot),
-                         reinterpret_cast<uint4 *>(b + o_items), reinterpret_cast<unsigned long long *>(b + o_count),
-                         reinterpret_cast<unsigned int *>(b + o_count + 8), reinterpret_cast<uint32_t *>(b + o_cache),
-                         capacity, n_ck, g_batch.group, sm_count(dev) * g_batch.ctas_per_sm, d_out,
-                         g_phase_ev[0] ? g_phase_ev : nullptr, st);
+        e = launch_batch(B, g_batch.tile_shape, b, offs, L, g_phase_ev[0] ? g_phase_ev : nullptr, st);
     const cudaError_t ef = cudaFreeAsync(base, st);
     if (e == cudaSuccess) e = ef;
     return e == cudaSuccess ? HMLFC_OK : cuda_fail(e, "batched render");

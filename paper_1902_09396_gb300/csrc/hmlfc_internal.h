@@ -125,13 +125,30 @@ cudaError_t launch_accumulate(const unsigned long long *counters, unsigned long 
 cudaError_t launch_copy_blob(const void *src, int n, void *dst, cudaStream_t st);
 size_t batch_lf_bytes();
 size_t batch_hdr_bytes();
-void batch_fill_lf(void *dst, const DevStream &ds, int64_t key_off, int64_t ck_off);
+// key_off: the light field's first flag (a multiple of 16), sk_off its first
+// super key, cam_off its first camera in the call's flattened arrays.
+void batch_fill_lf(void *dst, const DevStream &ds, int64_t key_off, int64_t sk_off, int64_t cam_off);
 void batch_fill_hdr(void *dst, int n_lf, int n_views, int total_tiles, int tile_w, int tile_h, int64_t n_keys,
-                    int64_t n_ck);
-cudaError_t launch_batch(int B, int tile_shape, const void *image, const int *ptr_offsets, int total_tiles,
-                         uint8_t *flags, uint32_t *slotmap, uint4 *items, unsigned long long *counters,
-                         unsigned int *work, uint32_t *cache, uint32_t capacity, int64_t n_ck, int group,
-                         int persistent_ctas, float *d_out, cudaEvent_t const *phase, cudaStream_t st);
+                    int64_t n_sk, int64_t n_cam);
+// Scratch and sizes of one batched pass: flags (n_keys), camera image
+// offsets (n_cam), items (n_sk), counters {items << 32, image pixels
+// allocated}, the blend's tile counter, the image pool (capacity pixels,
+// below 2^31), items per decode pass and the decode's CTA count.
+struct BatchLaunch {
+    int total_tiles = 0;
+    uint8_t *flags = nullptr;
+    uint32_t *camslot = nullptr;
+    uint4 *items = nullptr;
+    unsigned long long *counters = nullptr;
+    unsigned int *work = nullptr;
+    uint32_t *cache = nullptr;
+    unsigned long long capacity = 0;
+    int64_t n_sk = 0, n_cam = 0;
+    int group = 2, decode_ctas = 0, sm_count = 0;
+    float *d_out = nullptr;
+};
+cudaError_t launch_batch(int B, int tile_shape, const void *image, const int *ptr_offsets, const BatchLaunch &L,
+                         cudaEvent_t const *phase, cudaStream_t st);
 // bias: the forward carries the expected rounding of the integer decode.
 cudaError_t launch_render_relaxed(const DevStream &ds, const LaunchViews &lv, int total_tiles, const float *coeff,
                                   const float *root, float *d_out, bool bias, cudaStream_t st);

@@ -1459,6 +1459,141 @@ __device__ __forceinline__ bool item_desc(const DevStream &S, const LevelTabs &T
     return true;
 }
 
+// One pixel pair of a decode item `it` ({(level-K node, block) key, camera
+// mask}, K = min(2, L)): pair pp of the block is row pp / ceil(B/2), columns
+// 2 (pp % ceil(B/2)) and + 1.  Root + levels L-1 .. K once, level 1 once per
+// active child node (K = 2), level 0 once per flagged camera, from the
+// item's descriptors dd (item_desc order); dst_of(q) is the first pixel of
+// camera q's image (nullptr: the camera has no image and is skipped).  Both
+// pixels go through one evaluation site per (node, 3 channels) step.
+template <int BS, class DstOf>
+__device__ __forceinline__ void decode_item_pair(const DevStream &S, const LevelTabs &T, const Blk<BS> &bk,
+                                                 const NDesc *__restrict__ dd, const uint4 &it, int pp,
+                                                 DstOf dst_of) {
+    const int B = bk.size();
+    const int L = S.L, K = L < 2 ? L : 2;
+    const int n_sh = (L - K) * 3;                               // shared levels L-1 .. K
+    const int n_mid = K == 2 ? 12 : 0;                          // level 1 of the 4 child nodes
+    const int hp = (B + 1) >> 1;
+    const int node = (int)(it.x / (uint32_t)S.nblocks), k = (int)(it.x - (uint32_t)node * S.nblocks);
+    const int aK = node / T.gv[K], bK = node - (node / T.gv[K]) * T.gv[K];
+    const int bx = k % S.nbx, by = k / S.nbx;
+    const int yy = pp / hp, xx = 2 * (pp - yy * hp);
+    const int bw = min(B, S.W - bx * B), bh = min(B, S.H - by * B);
+    const bool in0 = xx < bw && yy < bh, in1 = xx + 1 < bw && yy < bh;
+    const int xi = min(xx, bw - 1), yi = min(yy, bh - 1);   // pixels outside the image compute a copy
+    const int p = yi * S.W + xi;
+    const int ti = yy * S.pstride + xx;                 // even; rows and columns past the block read zeros
+    const int gx = bx * B + xi, gy = by * B + yi;
+    // sub-sampled chroma: both pixels of the pair are chroma pixel (gx >> 1, gy >> 1), at (xi >> 1,
+    // yi >> 1) of the descriptors' half-size regions, inside chroma block (bx >> 1, by >> 1)
+    const int xic = xi >> 1, yic = yi >> 1, pc = yic * S.W + xic;
+    const int tic = ((by & 1) * (B / 2) + yic) * S.pstride + (bx & 1) * (B / 2) + xic;
+    const size_t rb = ((size_t)(aK >> (L - K)) * T.gv[L] + (bK >> (L - K))) * (size_t)S.rnpx;
+    int v0[3], v1[3];
+    const int gx1 = in1 ? gx + 1 : gx;                 // the second pixel, when it is in the image
+    v0[0] = SLD(S, roots, rb + S.roff[0] + (size_t)gy * S.W + gx);
+    v1[0] = SLD(S, roots, rb + S.roff[0] + (size_t)gy * S.W + gx1);
+#pragma unroll
+    for (int c = 1; c < 3; c++) {
+        if (S.sub) {
+            v0[c] = v1[c] = SLD(S, roots, rb + S.roff[c] + (size_t)(gy >> 1) * S.cW[c] + (gx >> 1));
+        } else {
+            v0[c] = SLD(S, roots, rb + S.roff[c] + (size_t)gy * S.W + gx);
+            v1[c] = SLD(S, roots, rb + S.roff[c] + (size_t)gy * S.W + gx1);
+        }
+    }
+    const int lod = S.lod;                              // progressive decode: stop at level lod
+    const uint32_t mask = it.y;
+    const int nm = K == 2 ? 4 : 1;
+    const size_t o0 = (size_t)gy * S.W + gx;
+    // One evaluation site for every (node, 3 channels) step, so that the loop body stays small:
+    // phase 0 the shared levels L-1 .. max(K, lod) into v; phase 1 the next child node m with a
+    // flagged camera, its level 1 into w = v + SRV (K = 2, lod <= 1); phase 2 its flagged cameras
+    // with a slot, level 0 into z = w + SRV (lod = 0), each stored to its camera image.
+    int w0[3] = {0, 0, 0}, w1[3] = {0, 0, 0};
+    int l = L - 1, m = -1, phase = 0, q = 0;
+    uint32_t cams = 0;
+    for (;;) {
+        const NDesc *d = nullptr;
+        if (phase == 0) {
+            if (l >= max(K, lod)) {
+                d = dd + (l - K) * 3;
+                l--;
+            } else {
+                phase = 1;
+                continue;
+            }
+        } else if (phase == 1) {
+            if (++m >= nm) break;
+            cams = K == 2 ? mask & (0x33u << (8 * (m >> 1) + 2 * (m & 1))) : mask;
+            if (!cams) continue;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                w0[c] = v0[c];
+                w1[c] = v1[c];
+            }
+            phase = 2;
+            if (K == 2 && lod <= 1) {
+                d = dd + n_sh + m * 3;
+            } else {
+                continue;
+            }
+        } else {
+            if (!cams) {
+                phase = 1;
+                continue;
+            }
+            q = __ffs(cams) - 1;
+            cams &= cams - 1;
+            uint32_t *const img = dst_of(q);
+            if (!img) continue;
+            if (lod == 0) {
+                d = dd + n_sh + n_mid + q * 3;
+            } else {
+                uint32_t *dst = img + o0;
+                if (in0) dst[0] = ycocg_to_rgb8(w0[0], w0[1], w0[2]);
+                if (in1) dst[1] = ycocg_to_rgb8(w1[0], w1[1], w1[2]);
+                continue;
+            }
+        }
+        int s0[3], s1[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            if (c > 0 && S.sub) {
+                int unused;
+                eval_pair<BS, false>(S, d[c], c, pc, xic, yic, tic, s0[c], unused);
+                s1[c] = s0[c];
+            } else {
+                eval_pair<BS, true>(S, d[c], c, p, xi, yi, ti, s0[c], s1[c]);
+            }
+        }
+        if (phase == 0) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                v0[c] += s0[c];
+                v1[c] += s1[c];
+            }
+        } else if (d == dd + n_sh + m * 3 && K == 2) {     // the child node's level 1
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                w0[c] += s0[c];
+                w1[c] += s1[c];
+            }
+        } else {                                            // a camera's level 0
+            uint32_t *dst = dst_of(q) + o0;
+            const uint32_t c0 = ycocg_to_rgb8(w0[0] + s0[0], w0[1] + s0[1], w0[2] + s0[2]);
+            const uint32_t c1 = ycocg_to_rgb8(w1[0] + s1[0], w1[1] + s1[1], w1[2] + s1[2]);
+            if (in1 && !(reinterpret_cast<uintptr_t>(dst) & 7u)) {
+                *reinterpret_cast<uint2 *>(dst) = make_uint2(c0, c1);   // both pixels, one store
+            } else {
+                if (in0) dst[0] = c0;
+                if (in1) dst[1] = c1;
+            }
+        }
+    }
+}
+
 // Decode the flagged blocks into the camera images, one item ((level-K node,
 // block), K = min(2, L)) at a time: per pixel, the node's reconstruction
 // (root + SRV levels L-1 .. K) is evaluated once, level 1 once per active
@@ -1509,125 +1644,12 @@ __global__ void __launch_bounds__(256, 5) k_decode_blocks(const __grid_constant_
         for (int e = threadIdx.x; e < kGroup * npair; e += blockDim.x) {
             const int gi = e / npair, pp = e - gi * npair;
             if (first + gi >= n) continue;
-            const uint4 it = __ldg(items + first + gi);
-            const int node = (int)(it.x / (uint32_t)S.nblocks), k = (int)(it.x - (uint32_t)node * S.nblocks);
-            const int aK = node / T.gv[K], bK = node - (node / T.gv[K]) * T.gv[K];
-            const int bx = k % S.nbx, by = k / S.nbx;
-            const int yy = pp / hp, xx = 2 * (pp - yy * hp);
-            const int bw = min(B, S.W - bx * B), bh = min(B, S.H - by * B);
-            const bool in0 = xx < bw && yy < bh, in1 = xx + 1 < bw && yy < bh;
-            const int xi = min(xx, bw - 1), yi = min(yy, bh - 1);   // pixels outside the image compute a copy
-            const int p = yi * S.W + xi;
-            const int ti = yy * S.pstride + xx;                 // even; rows and columns past the block read zeros
-            const int gx = bx * B + xi, gy = by * B + yi;
-            // sub-sampled chroma: both pixels of the pair are chroma pixel (gx >> 1, gy >> 1), at (xi >> 1,
-            // yi >> 1) of the descriptors' half-size regions, inside chroma block (bx >> 1, by >> 1)
-            const int xic = xi >> 1, yic = yi >> 1, pc = yic * S.W + xic;
-            const int tic = ((by & 1) * (B / 2) + yic) * S.pstride + (bx & 1) * (B / 2) + xic;
-            const size_t rb = ((size_t)(aK >> (L - K)) * T.gv[L] + (bK >> (L - K))) * (size_t)S.rnpx;
-            int v0[3], v1[3];
-            const int gx1 = in1 ? gx + 1 : gx;                 // the second pixel, when it is in the image
-            v0[0] = SLD(S, roots, rb + S.roff[0] + (size_t)gy * S.W + gx);
-            v1[0] = SLD(S, roots, rb + S.roff[0] + (size_t)gy * S.W + gx1);
-#pragma unroll
-            for (int c = 1; c < 3; c++) {
-                if (S.sub) {
-                    v0[c] = v1[c] = SLD(S, roots, rb + S.roff[c] + (size_t)(gy >> 1) * S.cW[c] + (gx >> 1));
-                } else {
-                    v0[c] = SLD(S, roots, rb + S.roff[c] + (size_t)gy * S.W + gx);
-                    v1[c] = SLD(S, roots, rb + S.roff[c] + (size_t)gy * S.W + gx1);
-                }
-            }
             const NDesc *dd = s_desc + gi * kDescPer;
             const uint32_t *slots = s_slot[gi];
-            const int lod = S.lod;                              // progressive decode: stop at level lod
-            const uint32_t mask = it.y;
-            const int nm = K == 2 ? 4 : 1;
-            const size_t o0 = (size_t)gy * S.W + gx;
-            // One evaluation site for every (node, 3 channels) step, so that the loop body stays small:
-            // phase 0 the shared levels L-1 .. max(K, lod) into v; phase 1 the next child node m with a
-            // flagged camera, its level 1 into w = v + SRV (K = 2, lod <= 1); phase 2 its flagged cameras
-            // with a slot, level 0 into z = w + SRV (lod = 0), each stored to its camera image.
-            int w0[3] = {0, 0, 0}, w1[3] = {0, 0, 0};
-            int l = L - 1, m = -1, phase = 0, q = 0;
-            uint32_t cams = 0;
-            for (;;) {
-                const NDesc *d = nullptr;
-                if (phase == 0) {
-                    if (l >= max(K, lod)) {
-                        d = dd + (l - K) * 3;
-                        l--;
-                    } else {
-                        phase = 1;
-                        continue;
-                    }
-                } else if (phase == 1) {
-                    if (++m >= nm) break;
-                    cams = K == 2 ? mask & (0x33u << (8 * (m >> 1) + 2 * (m & 1))) : mask;
-                    if (!cams) continue;
-#pragma unroll
-                    for (int c = 0; c < 3; c++) {
-                        w0[c] = v0[c];
-                        w1[c] = v1[c];
-                    }
-                    phase = 2;
-                    if (K == 2 && lod <= 1) {
-                        d = dd + n_sh + m * 3;
-                    } else {
-                        continue;
-                    }
-                } else {
-                    if (!cams) {
-                        phase = 1;
-                        continue;
-                    }
-                    q = __ffs(cams) - 1;
-                    cams &= cams - 1;
-                    if (slots[q] == kNone) continue;
-                    if (lod == 0) {
-                        d = dd + n_sh + n_mid + q * 3;
-                    } else {
-                        uint32_t *dst = cache + (size_t)slots[q] * plane + o0;
-                        if (in0) dst[0] = ycocg_to_rgb8(w0[0], w0[1], w0[2]);
-                        if (in1) dst[1] = ycocg_to_rgb8(w1[0], w1[1], w1[2]);
-                        continue;
-                    }
-                }
-                int s0[3], s1[3];
-#pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    if (c > 0 && S.sub) {
-                        int unused;
-                        eval_pair<BS, false>(S, d[c], c, pc, xic, yic, tic, s0[c], unused);
-                        s1[c] = s0[c];
-                    } else {
-                        eval_pair<BS, true>(S, d[c], c, p, xi, yi, ti, s0[c], s1[c]);
-                    }
-                }
-                if (phase == 0) {
-#pragma unroll
-                    for (int c = 0; c < 3; c++) {
-                        v0[c] += s0[c];
-                        v1[c] += s1[c];
-                    }
-                } else if (d == dd + n_sh + m * 3 && K == 2) {     // the child node's level 1
-#pragma unroll
-                    for (int c = 0; c < 3; c++) {
-                        w0[c] += s0[c];
-                        w1[c] += s1[c];
-                    }
-                } else {                                            // a camera's level 0
-                    uint32_t *dst = cache + (size_t)slots[q] * plane + o0;
-                    const uint32_t c0 = ycocg_to_rgb8(w0[0] + s0[0], w0[1] + s0[1], w0[2] + s0[2]);
-                    const uint32_t c1 = ycocg_to_rgb8(w1[0] + s1[0], w1[1] + s1[1], w1[2] + s1[2]);
-                    if (in1 && !(reinterpret_cast<uintptr_t>(dst) & 7u)) {
-                        *reinterpret_cast<uint2 *>(dst) = make_uint2(c0, c1);   // both pixels, one store
-                    } else {
-                        if (in0) dst[0] = c0;
-                        if (in1) dst[1] = c1;
-                    }
-                }
-            }
+            decode_item_pair<BS>(S, T, bk, dd, __ldg(items + first + gi), pp, [&](int q) -> uint32_t * {
+                const uint32_t sl = slots[q];
+                return sl == kNone ? nullptr : cache + (size_t)sl * plane;
+            });
         }
         __syncthreads();
     }
@@ -1663,7 +1685,9 @@ __device__ __noinline__ float3 blend_direct(const DevStream &S, const hmlfc_view
 // lookup and the tile arithmetic.  kFallback: some camera may have no image
 // (the call's cache could not hold every camera of the light field); a ray
 // with such a camera decodes its samples directly.
-template <int BS, bool kFallback>
+// kOffsets: camslot holds each camera image's first pixel in `cache` (the
+// batched form's pool of images of several sizes), not its slot index.
+template <int BS, bool kFallback, bool kOffsets = false>
 __device__ __forceinline__ void blend_cached_ray(const DevStream &S, const hmlfc_view &V, int px, int py,
                                                  const uint32_t *__restrict__ camslot,
                                                  const uint32_t *__restrict__ cache, float *__restrict__ out) {
@@ -1680,8 +1704,9 @@ __device__ __forceinline__ void blend_cached_ray(const DevStream &S, const hmlfc
         const uint32_t plane = (uint32_t)(S.W * S.H);
         const uint32_t p00 = (uint32_t)(r.y0 * S.W + r.x0);
         const uint32_t dx = (uint32_t)(r.x1 - r.x0), dy = (uint32_t)((r.y1 - r.y0) * S.W);
-        const uint32_t *c0 = cache + (size_t)s00 * plane + p00, *c1 = cache + (size_t)s01 * plane + p00;
-        const uint32_t *c2 = cache + (size_t)s10 * plane + p00, *c3 = cache + (size_t)s11 * plane + p00;
+        const size_t ip = kOffsets ? 1 : plane;
+        const uint32_t *c0 = cache + (size_t)s00 * ip + p00, *c1 = cache + (size_t)s01 * ip + p00;
+        const uint32_t *c2 = cache + (size_t)s10 * ip + p00, *c3 = cache + (size_t)s11 * ip + p00;
         uint32_t val[16];
         // sample order of blend16: q = a*8 + b*4 + xs*2 + ys  ->  camera a*2+b, corner xs*2+ys
         val[0] = __ldg(c0); val[1] = __ldg(c0 + dy); val[2] = __ldg(c0 + dx); val[3] = __ldg(c0 + dx + dy);
@@ -1813,13 +1838,15 @@ cudaError_t render_dispatch_tw(const DevStream &ds, const LaunchViews &lv, int t
 struct BatchHdr {
     int n_lf, n_views, total_tiles, tile_w, tile_h;
     int pad[3];
-    int64_t n_keys, n_ck;
+    int64_t n_keys, n_sk, n_cam;
 };
 
+// One light field of a batch: its stream and the first of its flags
+// (super-key layout, a multiple of 16), super keys ((level-K node, block)
+// pairs, K = min(2, L)) and cameras in the call's flattened arrays.
 struct BatchLF {
     DevStream S;
-    int64_t key_off;   // first (camera, block) key of this light field
-    int64_t ck_off;    // first (level-1 node, block) key
+    int64_t key_off, sk_off, cam_off;
 };
 
 struct BatchPtrs {     // device pointers into the scratch image
@@ -1849,39 +1876,76 @@ __device__ __forceinline__ int find_view_dev(const int *__restrict__ tile_start,
     return lo;
 }
 
-// One thread per tile: flag the (camera, block) pairs of its footprint.
+// The light field of a flattened index (first index of each in off_of(lf)).
+template <class OffOf>
+__device__ __forceinline__ int find_lf(int n_lf, int64_t g, OffOf off_of) {
+    int lf = 0;
+    while (lf + 1 < n_lf && g >= off_of(lf + 1)) lf++;
+    return lf;
+}
+
+// Marking of every light field's (camera, block) pairs, as k_mark: eight
+// tiles per warp, one per group of 4 lanes, each with its own view and light
+// field; the corner rays bound a tile's footprint (w > 0), otherwise the
+// whole warp marks the tile ray by ray.
 template <int BS, int TW, int TH>
-__global__ void __launch_bounds__(128) k_mark_batch(const BatchPtrs P, uint8_t *__restrict__ flags) {
-    const int tile = blockIdx.x * blockDim.x + threadIdx.x;
-    if (tile >= P.hdr->total_tiles) return;
-    const int vi = find_view_dev(P.tile_start, P.hdr->n_views, tile);
-    const hmlfc_view V = P.views[vi];
+__global__ void __launch_bounds__(256) k_mark_batch(const BatchPtrs P, uint8_t *__restrict__ flags) {
+    const int lane = threadIdx.x & 31, q = lane & 3;
+    const int total = P.hdr->total_tiles;
+    const int tile = (int)((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 8) + (lane >> 2);
+    const bool valid = tile < total;
+    const int tc = valid ? tile : total - 1;
+    const int vi = find_view_dev(P.tile_start, P.hdr->n_views, tc);
+    const hmlfc_view &V = P.views[vi];
     const BatchLF &F = P.lf[V.lf];
     const DevStream &S = F.S;
     const int tiles_x = (V.width + TW - 1) / TW;
-    const int local = tile - __ldg(P.tile_start + vi);
+    const int local = tc - __ldg(P.tile_start + vi);
     const int x0 = (local % tiles_x) * TW, y0 = (local / tiles_x) * TH;
     const int x1 = min(x0 + TW, V.width) - 1, y1 = min(y0 + TH, V.height) - 1;
     const Blk<BS> bk(S.B);
-    const int nu = S.nu, nv = S.nv, W = S.W, Hh = S.H, nbx = S.nbx, nblocks = S.nblocks;
-    float lo[4] = {1e30f, 1e30f, 1e30f, 1e30f}, hi[4] = {-1e30f, -1e30f, -1e30f, -1e30f};
-    bool ok = true;
+    const float X = (float)((q & 1) ? x1 : x0) + 0.5f, Y = (float)((q & 2) ? y1 : y0) + 0.5f;
+    const float *h = V.H_uv, *g = V.H_st;
+    const float wu = h[6] * X + h[7] * Y + h[8], ws = g[6] * X + g[7] * Y + g[8];
+    float lo[4] = {__fdividef(h[0] * X + h[1] * Y + h[2], wu), __fdividef(h[3] * X + h[4] * Y + h[5], wu),
+                   __fdividef(g[0] * X + g[1] * Y + g[2], ws), __fdividef(g[3] * X + g[4] * Y + g[5], ws)};
+    float hi[4] = {lo[0], lo[1], lo[2], lo[3]};
+    bool ok = wu > 0.f && ws > 0.f;
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-        const float X = (float)((q & 1) ? x1 : x0) + 0.5f, Y = (float)((q & 2) ? y1 : y0) + 0.5f;
-        const float *h = V.H_uv, *g = V.H_st;
-        const float wu = h[6] * X + h[7] * Y + h[8], ws = g[6] * X + g[7] * Y + g[8];
-        ok &= wu > 0.f && ws > 0.f;
-        const float c[4] = {__fdividef(h[0] * X + h[1] * Y + h[2], wu), __fdividef(h[3] * X + h[4] * Y + h[5], wu),
-                            __fdividef(g[0] * X + g[1] * Y + g[2], ws), __fdividef(g[3] * X + g[4] * Y + g[5], ws)};
+    for (int k = 0; k < 4; k++) ok = ok && lo[k] == lo[k];   // NaN
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            lo[k] = fminf(lo[k], c[k]);
-            hi[k] = fmaxf(hi[k], c[k]);
+            lo[k] = fminf(lo[k], __shfl_xor_sync(0xFFFFFFFFu, lo[k], o));
+            hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xFFFFFFFFu, hi[k], o));
+        }
+        const int ok_other = __shfl_xor_sync(0xFFFFFFFFu, (int)ok, o);   // every lane takes part
+        ok = ok && ok_other != 0;
+    }
+    for (unsigned bad = __ballot_sync(0xFFFFFFFFu, valid && !ok) & 0x11111111u; bad; bad &= bad - 1u) {
+        const int src = __ffs(bad) - 1;                    // the tile's group leader
+        const int bvi = __shfl_sync(0xFFFFFFFFu, vi, src);
+        const int bx0 = __shfl_sync(0xFFFFFFFFu, x0, src), by0 = __shfl_sync(0xFFFFFFFFu, y0, src);
+        const int bx1 = __shfl_sync(0xFFFFFFFFu, x1, src), by1 = __shfl_sync(0xFFFFFFFFu, y1, src);
+        const hmlfc_view &BV = P.views[bvi];
+        const BatchLF &BF = P.lf[BV.lf];
+        const DevStream &BSt = BF.S;
+        const Blk<BS> bbk(BSt.B);
+        const int tw = bx1 - bx0 + 1, n = tw * (by1 - by0 + 1);
+        for (int e = lane; e < n; e += 32) {
+            const int py = by0 + e / tw, px = bx0 + e % tw;
+            Ray r;
+            ray_setup(BV, BSt.nu, BSt.nv, BSt.W, BSt.H, px, py, r);
+            const int ci[2] = {r.i0, r.i1}, cj[2] = {r.j0, r.j1};
+            const int kb[4] = {bbk.div(r.y0) * BSt.nbx + bbk.div(r.x0), bbk.div(r.y0) * BSt.nbx + bbk.div(r.x1),
+                               bbk.div(r.y1) * BSt.nbx + bbk.div(r.x0), bbk.div(r.y1) * BSt.nbx + bbk.div(r.x1)};
+            for (int k = 0; k < 16; k++)
+                flags[BF.key_off + flag_index<true>(BSt, ci[k >> 3], cj[(k >> 2) & 1], kb[k & 3])] = 1;
         }
     }
-    uint8_t *fl = flags + F.key_off;
-    const int n[4] = {nu, nv, W, Hh};
+    if (!valid || !ok) return;                             // no warp-wide operation follows
+    const int n[4] = {S.nu, S.nv, S.W, S.H};
     int bl[4], bh[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
@@ -1891,112 +1955,100 @@ __global__ void __launch_bounds__(128) k_mark_batch(const BatchPtrs P, uint8_t *
         axis_nb(hi[k] + e, n[k], b0, b1);
         bl[k] = a0;
         bh[k] = b1;
-        if (!(lo[k] == lo[k]) || !(hi[k] == hi[k])) ok = false;
     }
-    if (!ok) {
-        for (int py = y0; py <= y1; py++)
-            for (int px = x0; px <= x1; px++) {
-                Ray r;
-                ray_setup(V, nu, nv, W, Hh, px, py, r);
-                const int ci[2] = {(r.i0 >> S.lod) << S.lod, (r.i1 >> S.lod) << S.lod};
-                const int cj[2] = {(r.j0 >> S.lod) << S.lod, (r.j1 >> S.lod) << S.lod};
-                const int kb[4] = {bk.div(r.y0) * nbx + bk.div(r.x0), bk.div(r.y0) * nbx + bk.div(r.x1),
-                                   bk.div(r.y1) * nbx + bk.div(r.x0), bk.div(r.y1) * nbx + bk.div(r.x1)};
-                for (int q = 0; q < 16; q++) fl[((size_t)ci[q >> 3] * nv + cj[(q >> 2) & 1]) * nblocks + kb[q & 3]] = 1;
+    const int bx0 = bk.div(bl[2]), by0 = bk.div(bl[3]);
+    const int nbx = bk.div(bh[2]) - bx0 + 1, by1 = bk.div(bh[3]);
+    const size_t stride = (size_t)1 << (2 * (S.L < 2 ? S.L : 2));
+    uint8_t *fl = flags + F.key_off;
+    int e = 0;
+    for (int i = bl[0]; i <= bh[0]; i++)
+        for (int j = bl[1]; j <= bh[1]; j++)
+            for (int by = by0; by <= by1; by++, e++) {
+                if ((e & 3) != q) continue;
+                uint8_t *f = fl + flag_index<true>(S, i, j, by * S.nbx + bx0);
+                for (int bx = 0; bx < nbx; bx++) f[bx * stride] = 1;
             }
-        return;
-    }
-    const int bx0 = bk.div(bl[2]), bx1 = bk.div(bh[2]), by0 = bk.div(bl[3]), by1 = bk.div(bh[3]);
-    const int step = 1 << S.lod;            // progressive decode: one representative camera per level-lod node
-    for (int i = (bl[0] >> S.lod) << S.lod; i <= bh[0]; i += step)
-        for (int j = (bl[1] >> S.lod) << S.lod; j <= bh[1]; j += step) {
-            uint8_t *f = fl + ((size_t)i * nv + j) * nblocks;
-            for (int by = by0; by <= by1; by++)
-                for (int bx = bx0; bx <= bx1; bx++) f[by * nbx + bx] = 1;
-        }
 }
 
-// One thread per (light field, level-1 node, block): slots of its flagged
-// cameras and one decode item {cluster key, camera mask, first slot, lf}.
+// Camera images and decode items of every light field.  The first
+// item_blocks blocks: one thread per super key of the call; a super key with
+// a flagged camera becomes the item {super key in its light field, camera
+// mask, light field, 0}.  The rest: one warp per camera; a camera with a
+// flagged block gets the offset (in pixels) of its W x H image in the call's
+// image pool, or kNone beyond the pool's `capacity` pixels (its rays decode
+// directly).
 __global__ void __launch_bounds__(256) k_assign_batch(const BatchPtrs P, const uint8_t *__restrict__ flags,
-                                                      uint32_t *__restrict__ slotmap, uint4 *__restrict__ items,
-                                                      unsigned long long *__restrict__ counters, uint32_t capacity) {
-    __shared__ uint32_t s_warp[8][2];
-    __shared__ uint32_t s_base[2];
-    const int64_t gck = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    uint32_t mask = 0;
-    int64_t keys[4] = {-1, -1, -1, -1};
-    int lf = 0;
-    int64_t ck = 0;
-    if (gck < P.hdr->n_ck) {
-        while (lf + 1 < P.hdr->n_lf && gck >= P.lf[lf + 1].ck_off) lf++;
+                                                      uint32_t *__restrict__ camslot, uint4 *__restrict__ items,
+                                                      unsigned long long *__restrict__ counters,
+                                                      unsigned long long capacity, int item_blocks) {
+    const int n_lf = P.hdr->n_lf;
+    if ((int)blockIdx.x >= item_blocks) {           // camera images: one warp per camera
+        const int64_t gcam = ((int64_t)blockIdx.x - item_blocks) * 8 + (threadIdx.x >> 5);
+        const int lane = threadIdx.x & 31;
+        if (gcam >= P.hdr->n_cam) return;
+        const int lf = find_lf(n_lf, gcam, [&](int k) { return P.lf[k].cam_off; });
         const BatchLF &F = P.lf[lf];
         const DevStream &S = F.S;
-        ck = gck - F.ck_off;
-        const int node = (int)(ck / S.nblocks), k = (int)(ck - (int64_t)node * S.nblocks);
-        const int gv1 = S.gv[1];
-        const int a1 = node / gv1, b1 = node - (node / gv1) * gv1;
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int i = 2 * a1 + (q >> 1), j = 2 * b1 + (q & 1);
-            if (i < S.nu && j < S.nv) {
-                keys[q] = F.key_off + ((int64_t)i * S.nv + j) * S.nblocks + k;
-                if (flags[keys[q]]) mask |= 1u << q;
+        const int cam = (int)(gcam - F.cam_off);
+        const int i = cam / S.nv, j = cam - (cam / S.nv) * S.nv;
+        const int K = S.L < 2 ? S.L : 2;
+        const uint8_t *f = flags + F.key_off + flag_index<true>(S, i, j, 0);   // block k at f[k << 2K]
+        uint32_t any = 0;
+        for (int k = lane; k < S.nblocks; k += 32) any |= __ldg(f + ((size_t)k << (2 * K)));
+        any = __any_sync(0xFFFFFFFFu, any != 0);
+        if (lane == 0) {
+            uint32_t slot = kNone;
+            if (any) {
+                const unsigned long long px = (unsigned long long)S.W * S.H;
+                const unsigned long long o = atomicAdd(counters + 1, px);
+                if (o + px <= capacity) slot = (uint32_t)o;
             }
+            camslot[gcam] = slot;
+        }
+        return;
+    }
+    __shared__ uint32_t s_warp[8];
+    __shared__ uint32_t s_base;
+    const int64_t gsk = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    uint32_t mask = 0;
+    int lf = 0;
+    int64_t sk = 0;
+    if (gsk < P.hdr->n_sk) {
+        lf = find_lf(n_lf, gsk, [&](int k) { return P.lf[k].sk_off; });
+        const BatchLF &F = P.lf[lf];
+        const int K = F.S.L < 2 ? F.S.L : 2, ncg = 1 << (2 * K);
+        sk = gsk - F.sk_off;
+        const uint8_t *f = flags + F.key_off + ((size_t)sk << (2 * K));   // the super key's camera flags
+        if (K == 2) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(f));
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int c = 0; c < 16; c++) mask |= ((w[c >> 2] >> (8 * (c & 3))) & 0xFFu) ? 1u << c : 0u;
+        } else {
+            for (int c = 0; c < ncg; c++) mask |= f[c] ? 1u << c : 0u;
         }
     }
-    const uint32_t nslot = __popc(mask), nitem = mask ? 1u : 0u;
+    const uint32_t nitem = mask ? 1u : 0u;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t is = nslot, ii = nitem;
+    uint32_t ii = nitem;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t vs = __shfl_up_sync(0xFFFFFFFFu, is, o), vi = __shfl_up_sync(0xFFFFFFFFu, ii, o);
-        if (lane >= o) {
-            is += vs;
-            ii += vi;
-        }
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, ii, o);
+        if (lane >= o) ii += v;
     }
-    if (lane == 31) {
-        s_warp[warp][0] = is;
-        s_warp[warp][1] = ii;
-    }
+    if (lane == 31) s_warp[warp] = ii;
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint32_t as = 0, ai = 0;
+        uint32_t a = 0;
         for (int w = 0; w < 8; w++) {
-            const uint32_t vs = s_warp[w][0], vi = s_warp[w][1];
-            s_warp[w][0] = as;
-            s_warp[w][1] = ai;
-            as += vs;
-            ai += vi;
+            const uint32_t v = s_warp[w];
+            s_warp[w] = a;
+            a += v;
         }
-        const unsigned long long old = atomicAdd(counters, ((unsigned long long)ai << 32) | as);
-        s_base[0] = (uint32_t)(old & 0xFFFFFFFFull);
-        s_base[1] = (uint32_t)(old >> 32);
+        s_base = (uint32_t)(atomicAdd(counters, (unsigned long long)a << 32) >> 32);
     }
     __syncthreads();
-    if (gck >= P.hdr->n_ck) return;
-    const uint32_t slot0 = s_base[0] + s_warp[warp][0] + is - nslot;
-    const uint32_t item = s_base[1] + s_warp[warp][1] + ii - nitem;
-    uint32_t slot = slot0;
-    const bool fits = slot0 + nslot <= capacity;
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        if (keys[q] < 0) continue;
-        if ((mask >> q) & 1u) {
-            slotmap[keys[q]] = fits ? slot : kNone;
-            slot++;
-        } else {
-            slotmap[keys[q]] = kNone;
-        }
-    }
-    if (mask) items[item] = make_uint4((uint32_t)ck, fits ? mask : 0u, slot0, (uint32_t)lf);
-}
-
-__device__ __forceinline__ void copy_words(void *dst, const void *src, int bytes) {
-    const int n = bytes / 4;
-    for (int t = threadIdx.x; t < n; t += blockDim.x)
-        reinterpret_cast<uint32_t *>(dst)[t] = __ldg(reinterpret_cast<const uint32_t *>(src) + t);
+    if (mask) items[s_base + s_warp[warp] + ii - nitem] = make_uint4((uint32_t)sk, mask, (uint32_t)lf, 0u);
 }
 
 // One pixel pair (pair pp: row pp / ceil(B/2), columns 2 (pp % ceil(B/2)) and
@@ -2066,156 +2118,117 @@ __device__ __forceinline__ void decode_pair_l1(const DevStream &S, const LevelTa
     }
 }
 
-// Persistent decode of every light field's items, G items per pass.
+__device__ __forceinline__ void copy_words(void *dst, const void *src, int bytes) {
+    const int n = bytes / 4;
+    for (int t = threadIdx.x; t < n; t += blockDim.x)
+        reinterpret_cast<uint32_t *>(dst)[t] = __ldg(reinterpret_cast<const uint32_t *>(src) + t);
+}
+
+// Block decode of every light field's items, as k_decode_blocks: G items per
+// pass (G <= 4), each with its light field's stream and level tables copied
+// to shared memory, its descriptors built by the whole CTA, then its pixel
+// pairs decoded into its cameras' images (pool offsets in camslot).
 template <int BS>
-__global__ void __launch_bounds__(256) k_decode_batch(const BatchPtrs P, const uint4 *__restrict__ items,
-                                                     const unsigned long long *__restrict__ counters,
-                                                     uint32_t *__restrict__ cache, int G) {
-    constexpr int kMaxGroup = 8;
-    constexpr int kDescPer = (kMaxLevels - 1) * 3 + 12;
+__global__ void __launch_bounds__(256, 5) k_decode_batch(const BatchPtrs P, const uint4 *__restrict__ items,
+                                                        const unsigned long long *__restrict__ counters,
+                                                        const uint32_t *__restrict__ camslot,
+                                                        uint32_t *__restrict__ cache, int G) {
+    constexpr int kMaxGroup = 4;
+    constexpr int kDescPer = (kMaxLevels - 2) * 3 + 4 * 3 + 16 * 3;
     __shared__ __align__(16) DevStream s_S[kMaxGroup];
     __shared__ LevelTabs s_T[kMaxGroup];
-    __shared__ Desc s_desc[kMaxGroup * kDescPer];
+    __shared__ __align__(16) NDesc s_desc[kMaxGroup * kDescPer];
+    __shared__ uint32_t s_img[kMaxGroup][16];
     __shared__ uint4 s_it[kMaxGroup];
     const uint32_t n = (uint32_t)(__ldg(counters) >> 32);
     G = max(1, min(G, kMaxGroup));
     for (uint32_t first = blockIdx.x * G; first < n; first += gridDim.x * G) {
-        __syncthreads();
+        __syncthreads();                                        // the previous pass is done with the slices
         for (int gi = 0; gi < G; gi++) {
-            const uint32_t it_idx = first + gi;
-            const uint4 it = it_idx < n ? __ldg(items + it_idx) : make_uint4(0u, 0u, 0u, 0u);
+            if (first + gi >= n) break;
+            const uint4 it = __ldg(items + first + gi);
             if (threadIdx.x == 0) s_it[gi] = it;
-            if (it_idx < n) copy_words(&s_S[gi], &P.lf[it.w].S, (int)sizeof(DevStream));
+            copy_words(&s_S[gi], &P.lf[it.z].S, (int)sizeof(DevStream));
         }
         __syncthreads();
         for (int gi = 0; gi < G; gi++)
             if (first + gi < n) load_tabs(s_S[gi], s_T[gi]);
         __syncthreads();
-        for (int d = threadIdx.x; d < G * kDescPer; d += blockDim.x) {
-            const int gi = d / kDescPer, e = d - gi * kDescPer;
+        for (int d = threadIdx.x; d < G * (kDescPer + 16); d += blockDim.x) {
+            const int gi = d / (kDescPer + 16), e = d - gi * (kDescPer + 16);
             if (first + gi >= n) continue;
-            const uint4 it = s_it[gi];
-            if (!it.y) continue;
             const DevStream &S = s_S[gi];
             const LevelTabs &T = s_T[gi];
-            const int L = S.L;
-            if (e >= (L - 1) * 3 + 12) continue;
-            const Blk<BS> bk(S.B);
-            const int node = (int)(it.x / (uint32_t)S.nblocks), k = (int)(it.x - (uint32_t)node * S.nblocks);
-            const int a1 = node / T.gv[1], b1 = node - (node / T.gv[1]) * T.gv[1];
-            int l, a, b, c;
-            if (e < (L - 1) * 3) {
-                l = 1 + e / 3;
-                c = e - 3 * (l - 1);
-                a = a1 >> (l - 1);
-                b = b1 >> (l - 1);
-            } else {
-                const int q = (e - (L - 1) * 3) / 3;
-                c = (e - (L - 1) * 3) - 3 * q;
-                l = 0;
-                a = 2 * a1 + (q >> 1);
-                b = 2 * b1 + (q & 1);
-                if (!((it.y >> q) & 1u)) continue;
+            const uint4 it = s_it[gi];
+            const int L = S.L, K = L < 2 ? L : 2, cpa = 1 << K;
+            const int nd = (L - K) * 3 + (K == 2 ? 12 : 0) + cpa * cpa * 3;
+            if (e >= kDescPer) {                                // pool offsets of the item's cameras
+                const int q = e - kDescPer;
+                const int node = (int)(it.x / (uint32_t)S.nblocks);
+                const int aK = node / T.gv[K], bK = node - (node / T.gv[K]) * T.gv[K];
+                const int i = aK * cpa + q / cpa, j = bK * cpa + q % cpa;
+                s_img[gi][q] = (q < cpa * cpa && ((it.y >> q) & 1u))
+                                   ? __ldg(camslot + P.lf[it.z].cam_off + (int64_t)i * S.nv + j) : kNone;
+                continue;
             }
-            s_desc[d] = make_desc(S, T, bk, l, a, b, c, k % S.nbx, k / S.nbx);
+            if (e >= nd) continue;
+            const Blk<BS> bk(S.B);
+            NDesc D;
+            if (item_desc(S, T, bk, it, e, D)) s_desc[gi * kDescPer + e] = D;
         }
         __syncthreads();
-        const int Bc = BS > 0 ? BS : s_S[0].B;                  // one block size per call
-        const int npair = Bc * ((Bc + 1) >> 1);
+        // two horizontally adjacent pixels per thread; an item's block size may differ from another's (BS = 0)
+        int npair = 0;
+        for (int gi = 0; gi < G && first + gi < n; gi++) {
+            const int B = s_S[gi].B;
+            npair = max(npair, B * ((B + 1) >> 1));
+        }
         for (int e = threadIdx.x; e < G * npair; e += blockDim.x) {
             const int gi = e / npair, pp = e - gi * npair;
             if (first + gi >= n) continue;
-            const uint4 it = s_it[gi];
-            if (!it.y) continue;
-            const Blk<BS> bk(s_S[gi].B);
-            decode_pair_l1(s_S[gi], s_T[gi], bk, s_desc + gi * kDescPer, it.x, it.y, pp,
-                           [&](int q) { return it.z + __popc(it.y & ((1u << q) - 1u)); }, cache);
+            const DevStream &S = s_S[gi];
+            const Blk<BS> bk(S.B);
+            if (pp >= bk.size() * ((bk.size() + 1) >> 1)) continue;
+            const uint32_t *img = s_img[gi];
+            decode_item_pair<BS>(S, s_T[gi], bk, s_desc + gi * kDescPer, s_it[gi], pp, [&](int q) -> uint32_t * {
+                const uint32_t o = img[q];
+                return o == kNone ? nullptr : cache + o;
+            });
         }
     }
 }
 
-// Persistent render: CTAs take (view, tile) items from an atomic counter.
-template <int BS, int TW, int TH>
-__global__ void __launch_bounds__(TW *TH) k_render_batch(const BatchPtrs P, const uint32_t *__restrict__ slotmap,
-                                                        const uint32_t *__restrict__ cache,
-                                                        unsigned int *__restrict__ work, float *__restrict__ out) {
-    __shared__ __align__(16) DevStream s_S;
-    __shared__ LevelTabs s_T;
-    __shared__ hmlfc_view s_V;
-    __shared__ int s_tile, s_local;
-    __shared__ int s_lf;
-    __shared__ long long s_key_off;
-    if (threadIdx.x == 0) s_lf = -1;
+// Blend of every light field's views: persistent CTAs take (view, tile)
+// items in order from a counter; each tile as k_render_cached, RPT rays per
+// thread, from the cameras' images at their pool offsets (a camera without
+// an image sends its rays to the direct decode).
+template <int BS, int TW, int TH, int RPT>
+__global__ void __launch_bounds__(TW *TH / RPT, 16) k_render_batch(const BatchPtrs P, const uint32_t *__restrict__ camslot,
+                                                              const uint32_t *__restrict__ cache,
+                                                              unsigned int *__restrict__ work, float *__restrict__ out) {
+    __shared__ int s_tile;
     const int total = P.hdr->total_tiles, n_views = P.hdr->n_views;
     for (;;) {
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(work, 1u);
         __syncthreads();
-        if (threadIdx.x == 0) {
-            const int tile = (int)atomicAdd(work, 1u);
-            s_tile = tile;
-            if (tile < total) {
-                const int vi = find_view_dev(P.tile_start, n_views, tile);
-                s_V = P.views[vi];
-                s_local = tile - __ldg(P.tile_start + vi);
-            }
-        }
-        __syncthreads();
-        if (s_tile >= total) break;
-        const int lf = s_V.lf;
-        if (lf != s_lf) {                       // uniform: the whole CTA reloads the descriptor
-            __syncthreads();
-            copy_words(&s_S, &P.lf[lf].S, (int)sizeof(DevStream));
-            __syncthreads();
-            load_tabs(s_S, s_T);
-            if (threadIdx.x == 0) {
-                s_lf = lf;
-                s_key_off = P.lf[lf].key_off;
-            }
-            __syncthreads();
-        }
-        const DevStream &S = s_S;
-        const hmlfc_view &V = s_V;
+        const int tile = s_tile;
+        __syncthreads();                                        // every thread has read it before the next write
+        if (tile >= total) break;
+        int vi = 0;
+        if ((threadIdx.x & 31) == 0) vi = find_view_dev(P.tile_start, n_views, tile);
+        vi = __shfl_sync(0xFFFFFFFFu, vi, 0);
+        const hmlfc_view &V = P.views[vi];
+        const BatchLF &F = P.lf[V.lf];
         const int tiles_x = (V.width + TW - 1) / TW;
-        const int px = (s_local % tiles_x) * TW + (int)threadIdx.x % TW;
-        const int py = (s_local / tiles_x) * TH + (int)threadIdx.x / TW;
-        if (px >= V.width || py >= V.height) continue;
-        const Blk<BS> bk(S.B);
-        const int B = bk.size();
-        Ray r;
-        ray_setup(V, S.nu, S.nv, S.W, S.H, px, py, r);
-        const uint32_t nv = (uint32_t)S.nv, nbl = (uint32_t)S.nblocks;
-        const uint32_t *sm = slotmap + s_key_off;
-        const uint32_t cam[4] = {(uint32_t)r.i0 * nv + r.j0, (uint32_t)r.i0 * nv + r.j1, (uint32_t)r.i1 * nv + r.j0,
-                                 (uint32_t)r.i1 * nv + r.j1};
-        const int bx[2] = {bk.div(r.x0), bk.div(r.x1)}, by[2] = {bk.div(r.y0), bk.div(r.y1)};
-        const uint32_t blk[4] = {(uint32_t)(by[0] * S.nbx + bx[0]), (uint32_t)(by[1] * S.nbx + bx[0]),
-                                 (uint32_t)(by[0] * S.nbx + bx[1]), (uint32_t)(by[1] * S.nbx + bx[1])};
-        const uint32_t off[4] = {(uint32_t)((r.y0 - by[0] * B) * B + (r.x0 - bx[0] * B)),
-                                 (uint32_t)((r.y1 - by[1] * B) * B + (r.x0 - bx[0] * B)),
-                                 (uint32_t)((r.y0 - by[0] * B) * B + (r.x1 - bx[1] * B)),
-                                 (uint32_t)((r.y1 - by[1] * B) * B + (r.x1 - bx[1] * B))};
-        uint32_t slot[16];
-        bool all = true;
+        const int local = tile - __ldg(P.tile_start + vi);
+        const int ty = local / tiles_x;
+        const int px = (local - ty * tiles_x) * TW + (int)threadIdx.x % TW;
+        const int py = ty * TH + (int)threadIdx.x / TW;
+        if (px >= V.width) continue;
 #pragma unroll
-        for (int q = 0; q < 16; q++) {
-            slot[q] = __ldg(sm + (size_t)cam[q >> 2] * nbl + blk[q & 3]);
-            all &= slot[q] != kNone;
-        }
-        float o[3];
-        if (all) {
-            uint32_t val[16];
-#pragma unroll
-            for (int q = 0; q < 16; q++) val[q] = __ldg(cache + (size_t)slot[q] * (uint32_t)(B * B) + off[q & 3]);
-            blend16(r, [&](int a, int b, int xs, int ys, int, int, int, int) { return val[a * 8 + b * 4 + xs * 2 + ys]; },
-                    o);
-        } else {
-            blend16(r, [&](int, int, int, int, int i, int j, int x, int y) { return sample_direct(S, s_T, bk, i, j, x, y); },
-                    o);
-        }
-        // write-streaming stores: the output must not evict the decode's working set from L2
-        float *dst = out + V.out_offset + ((size_t)py * V.width + px) * 3;
-        __stcs(dst, o[0]);
-        __stcs(dst + 1, o[1]);
-        __stcs(dst + 2, o[2]);
+        for (int k = 0; k < RPT; k++)
+            if (py + k * (TH / RPT) < V.height)
+                blend_cached_ray<BS, true, true>(F.S, V, px, py + k * (TH / RPT), camslot + F.cam_off, cache, out);
     }
 }
 
@@ -2447,17 +2460,18 @@ cudaError_t launch_copy_blob(const void *src, int n, void *dst, cudaStream_t st)
 size_t batch_lf_bytes() { return sizeof(BatchLF); }
 size_t batch_hdr_bytes() { return sizeof(BatchHdr); }
 
-void batch_fill_lf(void *dst, const DevStream &ds, int64_t key_off, int64_t ck_off) {
+void batch_fill_lf(void *dst, const DevStream &ds, int64_t key_off, int64_t sk_off, int64_t cam_off) {
     BatchLF f;
     memset(&f, 0, sizeof f);
     f.S = ds;
     f.key_off = key_off;
-    f.ck_off = ck_off;
+    f.sk_off = sk_off;
+    f.cam_off = cam_off;
     memcpy(dst, &f, sizeof f);
 }
 
 void batch_fill_hdr(void *dst, int n_lf, int n_views, int total_tiles, int tile_w, int tile_h, int64_t n_keys,
-                    int64_t n_ck) {
+                    int64_t n_sk, int64_t n_cam) {
     BatchHdr h;
     memset(&h, 0, sizeof h);
     h.n_lf = n_lf;
@@ -2466,57 +2480,50 @@ void batch_fill_hdr(void *dst, int n_lf, int n_views, int total_tiles, int tile_
     h.tile_w = tile_w;
     h.tile_h = tile_h;
     h.n_keys = n_keys;
-    h.n_ck = n_ck;
+    h.n_sk = n_sk;
+    h.n_cam = n_cam;
     memcpy(dst, &h, sizeof h);
 }
 
 namespace {
 
-template <int BS, int TW, int TH>
-cudaError_t batch_kernels(const BatchPtrs &P, int total_tiles, uint8_t *flags, uint32_t *slotmap, uint4 *items,
-                          unsigned long long *counters, unsigned int *work, uint32_t *cache, uint32_t capacity,
-                          int64_t n_ck, int group, int persistent_ctas, float *d_out, cudaEvent_t const *phase,
-                          cudaStream_t st) {
+constexpr int kBatchRenderCtasPerSm = 16;   // the blend's resident CTAs of 64 threads (64 registers)
+
+template <int BS, int TW, int TH, int RPT>
+cudaError_t batch_kernels(const BatchPtrs &P, const BatchLaunch &L, cudaEvent_t const *phase, cudaStream_t st) {
     if (phase && phase[0]) cudaEventRecord(phase[0], st);
-    k_mark_batch<BS, TW, TH><<<(total_tiles + 127) / 128, 128, 0, st>>>(P, flags);
+    k_mark_batch<BS, TW, TH><<<(unsigned)((L.total_tiles + 63) / 64), 256, 0, st>>>(P, L.flags);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_assign_batch<<<(unsigned)((n_ck + 255) / 256), 256, 0, st>>>(P, flags, slotmap, items, counters, capacity);
+    const int item_blocks = (int)((L.n_sk + 255) / 256), cam_blocks = (int)((L.n_cam + 7) / 8);
+    k_assign_batch<<<(unsigned)(item_blocks + cam_blocks), 256, 0, st>>>(P, L.flags, L.camslot, L.items, L.counters,
+                                                                       L.capacity, item_blocks);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (phase && phase[1]) cudaEventRecord(phase[1], st);
-    k_decode_batch<BS><<<persistent_ctas, 256, 0, st>>>(P, items, counters, cache, group);
+    k_decode_batch<BS><<<L.decode_ctas, 256, 0, st>>>(P, L.items, L.counters, L.camslot, L.cache, L.group);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (phase && phase[2]) cudaEventRecord(phase[2], st);
-    k_render_batch<BS, TW, TH><<<persistent_ctas, TW * TH, 0, st>>>(P, slotmap, cache, work, d_out);
+    k_render_batch<BS, TW, TH, RPT><<<L.sm_count * kBatchRenderCtasPerSm, TW * TH / RPT, 0, st>>>(
+        P, L.camslot, L.cache, L.work, L.d_out);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (phase && phase[3]) cudaEventRecord(phase[3], st);
     return cudaSuccess;
 }
 
 template <int BS>
-cudaError_t batch_tiles(int tile_shape, const BatchPtrs &P, int total_tiles, uint8_t *flags, uint32_t *slotmap,
-                        uint4 *items, unsigned long long *counters, unsigned int *work, uint32_t *cache,
-                        uint32_t capacity, int64_t n_ck, int group, int persistent_ctas, float *d_out,
-                        cudaEvent_t const *phase, cudaStream_t st) {
+cudaError_t batch_tiles(int tile_shape, const BatchPtrs &P, const BatchLaunch &L, cudaEvent_t const *phase,
+                        cudaStream_t st) {
     switch (tile_shape) {
-        case 1:
-            return batch_kernels<BS, 32, 8>(P, total_tiles, flags, slotmap, items, counters, work, cache, capacity,
-                                            n_ck, group, persistent_ctas, d_out, phase, st);
-        case 2:
-            return batch_kernels<BS, 8, 8>(P, total_tiles, flags, slotmap, items, counters, work, cache, capacity,
-                                           n_ck, group, persistent_ctas, d_out, phase, st);
-        default:
-            return batch_kernels<BS, 16, 16>(P, total_tiles, flags, slotmap, items, counters, work, cache, capacity,
-                                             n_ck, group, persistent_ctas, d_out, phase, st);
+        case 1: return batch_kernels<BS, 32, 8, 4>(P, L, phase, st);
+        case 2: return batch_kernels<BS, 8, 8, 1>(P, L, phase, st);
+        default: return batch_kernels<BS, 16, 16, 4>(P, L, phase, st);
     }
 }
 
 }  // namespace
 
-cudaError_t launch_batch(int B, int tile_shape, const void *image, const int *ptr_offsets, int total_tiles,
-                         uint8_t *flags, uint32_t *slotmap, uint4 *items, unsigned long long *counters,
-                         unsigned int *work, uint32_t *cache, uint32_t capacity, int64_t n_ck, int group,
-                         int persistent_ctas, float *d_out, cudaEvent_t const *phase, cudaStream_t st) {
+cudaError_t launch_batch(int B, int tile_shape, const void *image, const int *ptr_offsets, const BatchLaunch &L,
+                         cudaEvent_t const *phase, cudaStream_t st) {
     BatchPtrs P;
     const unsigned char *base = static_cast<const unsigned char *>(image);
     P.hdr = reinterpret_cast<const BatchHdr *>(base + ptr_offsets[0]);
@@ -2524,8 +2531,7 @@ cudaError_t launch_batch(int B, int tile_shape, const void *image, const int *pt
     P.views = reinterpret_cast<const hmlfc_view *>(base + ptr_offsets[2]);
     P.tile_start = reinterpret_cast<const int *>(base + ptr_offsets[3]);
     cudaError_t e = cudaSuccess;
-    HMLFC_DISPATCH_B(B, (e = batch_tiles<BS>(tile_shape, P, total_tiles, flags, slotmap, items, counters, work, cache,
-                                             capacity, n_ck, group, persistent_ctas, d_out, phase, st)));
+    HMLFC_DISPATCH_B(B, (e = batch_tiles<BS>(tile_shape, P, L, phase, st)));
     return e;
 }
 

@@ -333,12 +333,45 @@ def test_render_batch_matches_render_views(H, torch_cuda, tiny_streams, tiny_cfg
                 got = H.render_batch([s1, s2], arr)
                 torch_cuda.cuda.synchronize()
                 assert np.array_equal(got.cpu().numpy().astype(np.float64), want)
-        H.set_batch_tuning(0, 4, 4, 6 * 8 * 8 * 4)      # room for six blocks only
-        got = H.render_batch([s1, s2], arr)
-        torch_cuda.cuda.synchronize()
-        assert np.array_equal(got.cpu().numpy().astype(np.float64), want)
+        # an image pool with room for no camera image, then for three (the other cameras' rays decode directly)
+        for pool in (6 * 8 * 8 * 4, 3 * 64 * 64 * 4):
+            H.set_batch_tuning(0, 4, 4, pool)
+            got = H.render_batch([s1, s2], arr)
+            torch_cuda.cuda.synchronize()
+            assert np.array_equal(got.cpu().numpy().astype(np.float64), want)
     finally:
         H.set_batch_tuning(0, 4, 8, 2 << 30)
+
+
+def test_render_batch_mixed_block_sizes_and_chroma(H, torch_cuda, tiny_streams, tiny_cfg, ragged_lf):
+    """One batched pass over streams of block sizes 8 and 4 and a 4:2:0
+    stream gives the bits of hmlfc_render_views, and stays within the bound
+    of the oracle's FP64 render."""
+    c = tiny_cfg
+    datas = [tiny_streams[c.qstep].stream, O.encode(ragged_lf, 2, 4, 2, 4, mc=O.MC_INTEGER).stream,
+             O.encode(ragged_lf, 3, 8, 4, 2, t_ref=20, t_pred=30, sub=1).stream]
+    streams = [H.Stream(d) for d in datas]
+    geo1 = S.lf_geometry(c.nu, c.nv, c.width, c.height)
+    geo2 = S.lf_geometry(5, 3, 37, 29)
+    views = (S.random_views(61, geo1, 3, [(64, 64), (33, 17)]) + S.random_views(62, geo2, 3, [(40, 31)], lf=1) +
+             S.random_views(63, geo2, 3, [(29, 44)], lf=2))
+    arr = S.views_to_array([views[k] for k in (0, 3, 6, 1, 4, 7, 2, 5, 8)])
+    want = _render_gpu(H, torch_cuda, streams, arr)
+    for tile in (0, 1, 2):
+        try:
+            H.set_batch_tuning(tile, 2, 4)
+            got = H.render_batch(streams, arr)
+            torch_cuda.cuda.synchronize()
+        finally:
+            H.set_batch_tuning(0, 4, 8, 2 << 30)
+        assert np.array_equal(got.cpu().numpy().astype(np.float64), want)
+    for lf, d in enumerate(datas):
+        sel = arr[arr["lf"] == lf].copy()
+        sel["lf"] = 0
+        ref = O.render_dense(O.Stream(d).decode_all(), sel)     # each view at its own out_offset
+        for v in sel:
+            o, n = int(v["out_offset"]), int(v["width"] * v["height"] * 3)
+            assert np.max(np.abs(want[o:o + n] - ref[o:o + n])) <= RENDER_TOL
 
 
 def test_render_batch_graph_replay(H, torch_cuda, tiny_streams, tiny_cfg):
