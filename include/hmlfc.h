@@ -446,8 +446,11 @@ int hmlfc_touched_bytes_union_lod(const hmlfc_stream *const *streams, int n_stre
 int hmlfc_set_render_path(int path);
 
 /* Scratch budget of one cached render call, in bytes: the block index plus
- * the decoded camera images (W * H * 4 bytes each).  Default 1 GiB; 0
- * disables the cache. */
+ * the decoded camera images (W * H * 4 bytes each).  A call allocates an
+ * image for every camera of the stream, or as many as the budget holds
+ * (cameras beyond it decode their rays directly, much more slowly).
+ * Default 8 GiB (a 32x32 grid of 1024^2 cameras takes 4 GiB); 0 disables
+ * the cache. */
 int hmlfc_set_block_cache_bytes(size_t bytes);
 
 /*

@@ -19,7 +19,7 @@ from .build import LIB, build  # noqa: F401
 
 # Identifies the render kernel's code; profile figures recorded for another
 # version are not reused.
-KERNEL_VERSION = "render-cached-v15"
+KERNEL_VERSION = "render-cached-v16"
 ENCODER_VERSION = "encode-planes-v4"
 
 OK, E_INVALID_ARG, E_CORRUPT, E_OOM, E_CUDA, E_TIMEOUT, E_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
@@ -329,7 +329,7 @@ def set_encode_events(events):
     _check(lib().hmlfc_set_encode_events(arr, len(events)))
 
 
-DEFAULT_CACHE_BYTES = 1 << 30     # the library's default scratch budget of one cached render call
+DEFAULT_CACHE_BYTES = 8 << 30     # the library's default scratch budget of one cached render call
 
 
 def set_block_cache_bytes(n: int):

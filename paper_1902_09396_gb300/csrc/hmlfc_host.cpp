@@ -31,7 +31,7 @@ struct NvtxRange {
 
 thread_local std::string g_err;
 int g_render_path = 0;                      // 0 cached blocks, 1 direct per ray, 2 per-tile staging
-size_t g_cache_bytes = (size_t)1 << 30;     // scratch of one cached render call: index and camera images
+size_t g_cache_bytes = (size_t)8 << 30;     // cap on the scratch of one cached render call: index and camera images
 cudaEvent_t g_phase_ev[4] = {nullptr, nullptr, nullptr, nullptr};   // optional phase markers of the cached render
 
 struct BatchTuning {
@@ -987,7 +987,6 @@ int hmlfc_render_batch(const hmlfc_stream *const *streams, int n_streams, const 
 int hmlfc_server_create(const hmlfc_stream *s, size_t cache_bytes, void *cuda_stream, hmlfc_server **out) {
     if (!s || !out) return fail(HMLFC_E_INVALID_ARG, "NULL argument");
     *out = nullptr;
-    if (s->g.sub) return fail(HMLFC_E_UNSUPPORTED, "the serving form decodes full-resolution chroma only");
     const Geometry &g = s->g;
     DeviceGuard guard(s->device);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);

@@ -568,65 +568,6 @@ __device__ __forceinline__ int srv_desc(const DevStream &S, const Blk<BS> &bk, c
     return ((D.d0.z >> 20) & 1u) ? r - pred : r + pred;
 }
 
-// SRVs of one node-channel at two horizontally adjacent pixels (x, y) and
-// (x + 1, y) of a block, from its staged descriptor.  Both share the motion
-// vector, so their six distinct taps (columns x0, x0 + 1, x0 + 2 of rows y0
-// and y0 + 1) are read once.  idx1 / toff1 of the second pixel must be in
-// range even where that pixel is outside the block (its value is then
-// discarded); `inb` says whether its taps lie in the block's tap window.
-template <int BS>
-__device__ __forceinline__ void srv_desc2(const DevStream &S, const Blk<BS> &bk, const Desc &D, bool ref,
-                                          const PixGeom &g, int idx1, int toff1, bool inb, int &o0, int &o1) {
-    const int B = bk.size();
-    if (ref) {
-        const int16_t *t = S.tiles + (size_t)D.d1.x * (B * B);
-        o0 = __ldg(t + g.toff);
-        o1 = __ldg(t + toff1);
-        return;
-    }
-    int r0 = 0, r1 = 0;
-    if (D.d0.x != kNone) {
-        const int m = (int)(int16_t)(D.d0.y & 0xFFFFu);
-        const uint32_t *w = S.recs + D.d0.x + 1;
-        const uint32_t mode = (D.d0.y >> 21) & 3u, b = (D.d0.y >> 16) & 31u;
-        r0 = S.q * (m + (int)bise_get_small(w, mode, b, (uint32_t)g.idx));
-        r1 = S.q * (m + (int)bise_get_small(w, mode, b, (uint32_t)idx1));
-    }
-    if (!S.mc) {
-        o0 = r0;
-        o1 = r1;
-        return;
-    }
-    const int mvx = (int)(D.d0.z & 1023u) - 512, mvy = (int)((D.d0.z >> 10) & 1023u) - 512;
-    const int X = 4 * g.x + mvx, Y = 4 * g.y + mvy;
-    const int x0 = X >> 2, y0 = Y >> 2, fx = X & 3, fy = Y & 3;
-    const int c0 = clampi(x0, 0, S.W - 1), c1 = clampi(x0 + 1, 0, S.W - 1);
-    const int c2 = inb ? clampi(x0 + 2, 0, S.W - 1) : c1;
-    const int ya = clampi(y0, 0, S.H - 1), yb = clampi(y0 + 1, 0, S.H - 1);
-    const int cx = (int)(D.d0.w & 0xFFFFu), cy = (int)(D.d0.w >> 16);
-    // the six taps are 2 rows x 3 columns: tile row / column and in-tile offsets once each
-    const int tya = bk.div(ya), tyb = bk.div(yb);
-    const int tx0 = bk.div(c0), tx1 = bk.div(c1), tx2 = bk.div(c2);
-    const uint32_t la = tya == cy ? D.d1.x : D.d1.z, ra = tya == cy ? D.d1.y : D.d1.w;   // row a: left / right tile
-    const uint32_t lb = tyb == cy ? D.d1.x : D.d1.z, rb = tyb == cy ? D.d1.y : D.d1.w;
-    const int oya = (ya - tya * B) * B, oyb = (yb - tyb * B) * B;
-    const int ox0 = c0 - tx0 * B, ox1 = c1 - tx1 * B, ox2 = c2 - tx2 * B;
-    const bool l0 = tx0 == cx, l1 = tx1 == cx, l2 = tx2 == cx;
-    const int16_t *T = S.tiles;
-    const size_t B2s = (size_t)B * B;
-    const int a0 = __ldg(T + (l0 ? la : ra) * B2s + (oya + ox0));
-    const int a1 = __ldg(T + (l1 ? la : ra) * B2s + (oya + ox1));
-    const int a2 = __ldg(T + (l2 ? la : ra) * B2s + (oya + ox2));
-    const int b0 = __ldg(T + (l0 ? lb : rb) * B2s + (oyb + ox0));
-    const int b1 = __ldg(T + (l1 ? lb : rb) * B2s + (oyb + ox1));
-    const int b2 = __ldg(T + (l2 ? lb : rb) * B2s + (oyb + ox2));
-    const int w00 = (4 - fx) * (4 - fy), w10 = fx * (4 - fy), w01 = (4 - fx) * fy, w11 = fx * fy;
-    const int p0 = (w00 * a0 + w10 * a1 + w01 * b0 + w11 * b1 + 8) >> 4;
-    const int p1 = (w00 * a1 + w10 * a2 + w01 * b1 + w11 * b2 + 8) >> 4;
-    const bool neg = (D.d0.z >> 20) & 1u;
-    o0 = neg ? r0 - p0 : r0 + p0;
-    o1 = neg ? r1 - p1 : r1 + p1;
-}
 
 template <int BS>
 __device__ __forceinline__ const Desc &desc_at(const Desc *desc, const Footprint &F, int l, int a, int b, int c,
@@ -1428,8 +1369,8 @@ __device__ __forceinline__ void eval_pair(const DevStream &S, const NDesc &D, in
 // that the item does not decode.
 template <int BS>
 __device__ __forceinline__ bool item_desc(const DevStream &S, const LevelTabs &T, const Blk<BS> &bk, const uint4 &it,
-                                          int e, NDesc &D) {
-    const int L = S.L, K = L < 2 ? L : 2, cpa = 1 << K;
+                                          int e, NDesc &D, int K) {
+    const int L = S.L, cpa = 1 << K;
     const int n_sh = (L - K) * 3, n_mid = K == 2 ? 12 : 0;
     const int node = (int)(it.x / (uint32_t)S.nblocks), k = (int)(it.x - (uint32_t)node * S.nblocks);
     const int aK = node / T.gv[K], bK = node - (node / T.gv[K]) * T.gv[K];
@@ -1466,12 +1407,12 @@ __device__ __forceinline__ bool item_desc(const DevStream &S, const LevelTabs &T
 // item's descriptors dd (item_desc order); dst_of(q) is the first pixel of
 // camera q's image (nullptr: the camera has no image and is skipped).  Both
 // pixels go through one evaluation site per (node, 3 channels) step.
-template <int BS, class DstOf>
+template <int BS, bool kTile = false, class DstOf>
 __device__ __forceinline__ void decode_item_pair(const DevStream &S, const LevelTabs &T, const Blk<BS> &bk,
                                                  const NDesc *__restrict__ dd, const uint4 &it, int pp,
-                                                 DstOf dst_of) {
+                                                 DstOf dst_of, int K) {
     const int B = bk.size();
-    const int L = S.L, K = L < 2 ? L : 2;
+    const int L = S.L;
     const int n_sh = (L - K) * 3;                               // shared levels L-1 .. K
     const int n_mid = K == 2 ? 12 : 0;                          // level 1 of the 4 child nodes
     const int hp = (B + 1) >> 1;
@@ -1506,7 +1447,8 @@ __device__ __forceinline__ void decode_item_pair(const DevStream &S, const Level
     const int lod = S.lod;                              // progressive decode: stop at level lod
     const uint32_t mask = it.y;
     const int nm = K == 2 ? 4 : 1;
-    const size_t o0 = (size_t)gy * S.W + gx;
+    // kTile: a camera's block is a B x B slot (the serving form's resident cache), else a W x H image
+    const size_t o0 = kTile ? (size_t)yy * B + xx : (size_t)gy * S.W + gx;
     // One evaluation site for every (node, 3 channels) step, so that the loop body stays small:
     // phase 0 the shared levels L-1 .. max(K, lod) into v; phase 1 the next child node m with a
     // flagged camera, its level 1 into w = v + SRV (K = 2, lod <= 1); phase 2 its flagged cameras
@@ -1636,7 +1578,7 @@ __global__ void __launch_bounds__(256, 5) k_decode_blocks(const __grid_constant_
                 continue;
             }
             NDesc D;
-            if (item_desc(S, T, bk, it, e, D)) s_desc[gi * kDescPer + e] = D;
+            if (item_desc(S, T, bk, it, e, D, L < 2 ? L : 2)) s_desc[gi * kDescPer + e] = D;
         }
         __syncthreads();
         // two horizontally adjacent pixels per thread: (xx, yy) and (xx + 1, yy)
@@ -1649,7 +1591,7 @@ __global__ void __launch_bounds__(256, 5) k_decode_blocks(const __grid_constant_
             decode_item_pair<BS>(S, T, bk, dd, __ldg(items + first + gi), pp, [&](int q) -> uint32_t * {
                 const uint32_t sl = slots[q];
                 return sl == kNone ? nullptr : cache + (size_t)sl * plane;
-            });
+            }, K);
         }
         __syncthreads();
     }
@@ -2051,73 +1993,6 @@ __global__ void __launch_bounds__(256) k_assign_batch(const BatchPtrs P, const u
     if (mask) items[s_base + s_warp[warp] + ii - nitem] = make_uint4((uint32_t)sk, mask, (uint32_t)lf, 0u);
 }
 
-// One pixel pair (pair pp: row pp / ceil(B/2), columns 2 (pp % ceil(B/2)) and
-// + 1) of a cluster item (level-1 node, block) with a mask over its 2 x 2
-// cameras: root + levels L-1 .. 1 once, level 0 per marked camera, both
-// pixels through one evaluation site (as k_decode_blocks); slot_of(q) is
-// camera q's cache slot.
-template <int BS, class SlotOf>
-__device__ __forceinline__ void decode_pair_l1(const DevStream &S, const LevelTabs &T, const Blk<BS> &bk,
-                                               const Desc *dd, uint32_t key, uint32_t mask, int pp, SlotOf slot_of,
-                                               uint32_t *__restrict__ cache) {
-    const int B = bk.size(), B2 = B * B, L = S.L, hp = (B + 1) >> 1;
-    const size_t plane = (size_t)S.W * S.H;
-    const int node = (int)(key / (uint32_t)S.nblocks), k = (int)(key - (uint32_t)node * S.nblocks);
-    const int a1 = node / T.gv[1], b1 = node - (node / T.gv[1]) * T.gv[1];
-    const int bx = k % S.nbx, by = k / S.nbx;
-    const int yy = pp / hp, xx = 2 * (pp - yy * hp);
-    const int bw = min(B, S.W - bx * B), bh = min(B, S.H - by * B);
-    const bool in0 = xx < bw && yy < bh, in1 = xx + 1 < bw && yy < bh, tile1 = xx + 1 < B;
-    PixGeom g;
-    g.x = bx * B + min(xx, bw - 1);
-    g.y = by * B + min(yy, bh - 1);
-    g.blk = 0;
-    g.idx = (g.y - by * B) * bw + (g.x - bx * B);
-    g.toff = (g.y - by * B) * B + (g.x - bx * B);
-    const int idx1 = in1 ? g.idx + 1 : g.idx, toff1 = in1 ? g.toff + 1 : g.toff, x1 = in1 ? g.x + 1 : g.x;
-    const size_t rb = ((size_t)(a1 >> (L - 1)) * T.gv[L] + (b1 >> (L - 1))) * 3 * plane + (size_t)g.y * S.W;
-    int v0[3], v1[3];
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        v0[c] = SLD(S, roots, rb + c * plane + g.x);
-        v1[c] = SLD(S, roots, rb + c * plane + x1);
-    }
-    const size_t o0 = (size_t)yy * B + xx;
-    int l = L - 1;
-    uint32_t cams = mask;
-    for (;;) {
-        const Desc *d;
-        bool ref;
-        int q = -1;
-        if (l >= 1) {
-            d = dd + (l - 1) * 3;
-            ref = is_ref(a1 >> (l - 1), b1 >> (l - 1));
-            l--;
-        } else if (cams) {
-            q = __ffs(cams) - 1;
-            cams &= cams - 1;
-            d = dd + (L - 1) * 3 + q * 3;
-            ref = is_ref(2 * a1 + (q >> 1), 2 * b1 + (q & 1));
-        } else {
-            break;
-        }
-        int s0[3], s1[3];
-#pragma unroll
-        for (int c = 0; c < 3; c++) srv_desc2(S, bk, d[c], ref, g, idx1, toff1, in1, s0[c], s1[c]);
-        if (q < 0) {
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                v0[c] += s0[c];
-                v1[c] += s1[c];
-            }
-        } else {
-            uint32_t *dst = cache + (size_t)slot_of(q) * B2 + o0;
-            dst[0] = in0 ? ycocg_to_rgb8(v0[0] + s0[0], v0[1] + s0[1], v0[2] + s0[2]) : 0u;
-            if (tile1) dst[1] = in1 ? ycocg_to_rgb8(v1[0] + s1[0], v1[1] + s1[1], v1[2] + s1[2]) : 0u;
-        }
-    }
-}
-
 __device__ __forceinline__ void copy_words(void *dst, const void *src, int bytes) {
     const int n = bytes / 4;
     for (int t = threadIdx.x; t < n; t += blockDim.x)
@@ -2174,7 +2049,7 @@ __global__ void __launch_bounds__(256, 5) k_decode_batch(const BatchPtrs P, cons
             if (e >= nd) continue;
             const Blk<BS> bk(S.B);
             NDesc D;
-            if (item_desc(S, T, bk, it, e, D)) s_desc[gi * kDescPer + e] = D;
+            if (item_desc(S, T, bk, it, e, D, L < 2 ? L : 2)) s_desc[gi * kDescPer + e] = D;
         }
         __syncthreads();
         // two horizontally adjacent pixels per thread; an item's block size may differ from another's (BS = 0)
@@ -2193,7 +2068,7 @@ __global__ void __launch_bounds__(256, 5) k_decode_batch(const BatchPtrs P, cons
             decode_item_pair<BS>(S, s_T[gi], bk, s_desc + gi * kDescPer, s_it[gi], pp, [&](int q) -> uint32_t * {
                 const uint32_t o = img[q];
                 return o == kNone ? nullptr : cache + o;
-            });
+            }, S.L < 2 ? S.L : 2);
         }
     }
 }
@@ -2295,57 +2170,48 @@ __global__ void __launch_bounds__(256) k_resident_misses(const __grid_constant__
     items[2 * (size_t)item + 1] = make_uint4(slots[0], slots[1], slots[2], slots[3]);
 }
 
-// Decode the claimed blocks (as k_decode_blocks, with one slot per camera).
+// Decode the claimed blocks (as k_decode_blocks) into their B x B slots:
+// items are (level-1 node, block) pairs with a mask over the node's 2 x 2
+// cameras and one slot per camera, decoded by the same pixel-pair
+// evaluation over the dense reference planes and residual tiles.
 template <int BS>
-__global__ void __launch_bounds__(256) k_decode_resident(const __grid_constant__ DevStream S,
-                                                        const uint4 *__restrict__ items,
-                                                        const unsigned long long *__restrict__ counters,
-                                                        uint32_t *__restrict__ cache) {
+__global__ void __launch_bounds__(256, 5) k_decode_resident(const __grid_constant__ DevStream S,
+                                                           const uint4 *__restrict__ items,
+                                                           const unsigned long long *__restrict__ counters,
+                                                           uint32_t *__restrict__ cache) {
     constexpr int kGroup = 4;
     constexpr int kDescPer = (kMaxLevels - 1) * 3 + 4 * 3;
     __shared__ LevelTabs T;
-    __shared__ Desc s_desc[kGroup * kDescPer];
+    __shared__ __align__(16) NDesc s_desc[kGroup * kDescPer];
+    __shared__ uint4 s_it[kGroup][2];
     load_tabs(S, T);
     const Blk<BS> bk(S.B);
-    const int B = bk.size();
-    const int L = S.L;
+    const int B = bk.size(), B2 = B * B;
+    const int L = S.L, K = L < 1 ? L : 1;
     const uint32_t n = (uint32_t)(__ldg(counters) >> 32);
-    const int nd = (L - 1) * 3 + 12;
-    __syncthreads();
+    const int nd = (L - K) * 3 + 4 * 3;
     for (uint32_t first = blockIdx.x * kGroup; first < n; first += gridDim.x * kGroup) {
+        __syncthreads();                                        // the previous pass is done with the slices
+        if (threadIdx.x < 2 * kGroup && first + (threadIdx.x >> 1) < n)
+            s_it[threadIdx.x >> 1][threadIdx.x & 1] = __ldg(items + 2 * (size_t)first + threadIdx.x);
+        __syncthreads();
         for (int d = threadIdx.x; d < kGroup * nd; d += blockDim.x) {
             const int gi = d / nd, e = d - gi * nd;
             if (first + gi >= n) continue;
-            const uint4 it = __ldg(items + 2 * (size_t)(first + gi));
-            const int node = (int)(it.x / (uint32_t)S.nblocks), k = (int)(it.x - (uint32_t)node * S.nblocks);
-            const int a1 = node / T.gv[1], b1 = node - (node / T.gv[1]) * T.gv[1];
-            int l, a, b, c;
-            if (e < (L - 1) * 3) {
-                l = 1 + e / 3;
-                c = e - 3 * (l - 1);
-                a = a1 >> (l - 1);
-                b = b1 >> (l - 1);
-            } else {
-                const int q = (e - (L - 1) * 3) / 3;
-                c = (e - (L - 1) * 3) - 3 * q;
-                l = 0;
-                a = 2 * a1 + (q >> 1);
-                b = 2 * b1 + (q & 1);
-                if (!((it.y >> q) & 1u)) continue;
-            }
-            s_desc[d] = make_desc(S, T, bk, l, a, b, c, k % S.nbx, k / S.nbx);
+            NDesc D;
+            if (item_desc(S, T, bk, s_it[gi][0], e, D, K)) s_desc[gi * kDescPer + e] = D;
         }
         __syncthreads();
         const int npair = B * ((B + 1) >> 1);
         for (int e = threadIdx.x; e < kGroup * npair; e += blockDim.x) {
             const int gi = e / npair, pp = e - gi * npair;
             if (first + gi >= n) continue;
-            const uint4 it = __ldg(items + 2 * (size_t)(first + gi));
-            const uint4 sl = __ldg(items + 2 * (size_t)(first + gi) + 1);
-            decode_pair_l1(S, T, bk, s_desc + gi * nd, it.x, it.y, pp,
-                           [&](int q) { return q == 0 ? sl.x : q == 1 ? sl.y : q == 2 ? sl.z : sl.w; }, cache);
+            const uint4 sl = s_it[gi][1];
+            decode_item_pair<BS, true>(S, T, bk, s_desc + gi * kDescPer, s_it[gi][0], pp, [&](int q) -> uint32_t * {
+                const uint32_t slot = q == 0 ? sl.x : q == 1 ? sl.y : q == 2 ? sl.z : sl.w;
+                return slot == kNone ? nullptr : cache + (size_t)slot * B2;
+            }, K);
         }
-        __syncthreads();
     }
 }
 

@@ -69,12 +69,12 @@ for lf, data, L in cases:
     for level in range(1, L + 1):
         H.render_views([st], views, level=level)
         status(f"render level {level}")
+    cache = ResidentCache(st, 1 << 20)
+    out = torch.zeros(H.out_size(views), dtype=torch.float32, device="cuda")
+    cache.render(views, out)
+    assert np.array_equal(out.cpu().numpy(), outs[0]), "serve"
+    status("serve")
     if not st.info["chroma"]:
-        cache = ResidentCache(st, 1 << 20)
-        out = torch.zeros(H.out_size(views), dtype=torch.float32, device="cuda")
-        cache.render(views, out)
-        assert np.array_equal(out.cpu().numpy(), outs[0]), "serve"
-        status("serve")
         co_, ro_ = st.dequant()
         H.render_views_relaxed([st], [co_], [ro_], views)
         status("relaxed render")

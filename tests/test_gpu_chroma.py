@@ -1,9 +1,9 @@
 """Chroma sub-sampled 4:2:0 streams (Sec. 4.5) through the C ABI: decoded
 samples bit-exact against the oracle, rendered views within 1e-3 of its FP64
 render, every render path the same bits, progressive levels, the touched-bytes
-counter, the allocation-free entry point, and the calls that decode full
-resolution chroma only refusing the mode (or, for the batched form, handing
-it to hmlfc_render_views)."""
+counter, the allocation-free entry point, the serving form's resident
+cache, and the calls that decode full-resolution chroma only refusing the
+mode."""
 import ctypes as C
 
 import numpy as np
@@ -133,18 +133,35 @@ def test_chroma_420_noalloc_equals_render_views(H, tiny_lf, tiny_cfg):
     assert torch.equal(got, want)
 
 
+def test_chroma_420_served_from_the_resident_cache(H, tiny_lf, tiny_cfg, ragged_lf):
+    """The serving form's resident cache renders 4:2:0 streams with the bits
+    of hmlfc_render_views, on consecutive calls (hits) and with a cache
+    smaller than one call (evictions and direct decode)."""
+    import torch
+    from paper_1902_09396_gb300.serve import ResidentCache
+    for data, lf, L in _fields(tiny_lf, tiny_cfg, ragged_lf)[:2]:
+        st = H.Stream(data)
+        nu, nv, Hh, W = lf.shape[:4]
+        geo = S.lf_geometry(nu, nv, W, Hh)
+        for cache_bytes in (1 << 22, 6 * 8 * 8 * 4):
+            cache = ResidentCache(st, cache_bytes)
+            for seed in (71, 72):
+                views = S.views_to_array(S.random_views(seed, geo, 3, [(40, 36), (17, 9)]))
+                want = H.render_views([st], views)
+                out = torch.zeros(H.out_size(views), dtype=torch.float32, device="cuda")
+                cache.render(views, out)
+                torch.cuda.synchronize()
+                assert torch.equal(out, want)
+
+
 def test_chroma_420_refused_where_full_chroma_only(H, tiny_lf, tiny_cfg):
-    """The serving form, the relaxation (forward, adjoint, starting point),
-    the re-quantiser and the device encoder decode or code full-resolution
-    chroma only: each refuses a 4:2:0 stream with HMLFC_E_UNSUPPORTED."""
+    """The relaxation (forward, adjoint, starting point), the re-quantiser and
+    the device encoder decode or code full-resolution chroma only: each
+    refuses a 4:2:0 stream with HMLFC_E_UNSUPPORTED."""
     import torch
     c = tiny_cfg
     data = O.encode(tiny_lf, c.levels, c.block, c.search, c.qstep, sub=1).stream
     st = H.Stream(data)
-    from paper_1902_09396_gb300.serve import ResidentCache
-    with pytest.raises(H.HmlfcError) as e:
-        ResidentCache(st, 1 << 20)
-    assert e.value.code == H.E_UNSUPPORTED
     lib = H.lib()
     d = torch.zeros(1 << 20, dtype=torch.float32, device="cuda")
     lib.hmlfc_dequant.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
