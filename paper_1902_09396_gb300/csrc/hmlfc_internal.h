@@ -19,7 +19,7 @@ constexpr uint32_t kVersion = 1u;
 constexpr int kHeaderWords = 32;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr int64_t kMaxSlots = 0x7FFFFFFF;   // cache slots stay below 2^31, so kNone is the only value with bit 31 set
-constexpr int kDecodeCtasPerSm = 32;        // persistent CTAs per SM of the cached block decode (from launch-shape sweeps)
+constexpr int kDecodeCtasPerSm = 32;        // CTAs per SM launched for the cached block decode (5 resident; from sweeps)
 
 // Everything a kernel needs to decode samples of one stream.  Passed by value
 // as a kernel parameter (it lives in the constant bank while the kernel runs).
