@@ -4,13 +4,13 @@ hmlfc_render_views_noalloc serves callers that cannot allocate device memory
 when they render: a frame loop with a hard deadline that must not wait on
 the allocator or fail on fragmentation midway, code under a caching
 allocator that has to account for every byte, and code capturing work into
-a CUDA graph in a capture mode that forbids cudaMalloc.  Its decoded-block
-cache lives in a fixed device array that every call shares and finds as the
-previous call left it, so it is checked on two calls in a row, with
-different streams and views, against hmlfc_render_views: the results must
-be the same bits.  A larger field whose reached blocks overflow the array
-exercises the per-ray decode of the blocks beyond it, and a stream whose
-block index alone does not fit must be rejected.  This file is collected
+a CUDA graph in a capture mode that forbids cudaMalloc.  Its index and
+decoded camera images live in a fixed device array that every call shares
+and finds as the previous call left it, so it is checked on two calls in a
+row, with different streams and views, against hmlfc_render_views: the
+results must be the same bits.  A larger field whose reached cameras
+overflow the array exercises the direct decode of their rays, and a stream
+whose index alone does not fit must be rejected.  This file is collected
 last so that a run stopping at its first failure has already run every
 other test.
 """
