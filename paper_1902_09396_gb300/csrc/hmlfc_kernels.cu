@@ -1773,8 +1773,9 @@ cudaError_t render_dispatch_tw(const DevStream &ds, const LaunchViews &lv, int t
 // A call's light-field descriptors, views and tile prefix live in device
 // scratch (written by k_copy_blob from kernel parameters, so a captured
 // graph keeps no pointer to host memory).  One launch each of mark, assign,
-// decode (persistent) and render (persistent, atomic work queue over
-// (view, tile) items) covers every light field of the call.
+// decode (CTAs looping over the items of every light field) and render
+// (persistent, atomic work queue over (view, tile) items) covers every light
+// field of the call; the camera images of all light fields share one pool.
 
 // Host-built image at the start of the batch scratch.
 struct BatchHdr {
